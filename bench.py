@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Benchmark: one outer iteration of the bilayer minimum-mode kernel on the
+2048 x 2048 triangular lattice (4,194,304 spins, 3 exchange shells, Neel DMI,
+anisotropy, Zeeman; FP32 spin fields; biskyrmion Q = 2 start).
+
+A step = moto_mmf_step (energy + Riemannian gradient; k = 8 block Lanczos,
+block 8 x 12 steps = 96 HVPs with FP64-accumulated CGS2 reorthogonalisation and
+FP64 Rayleigh-Ritz; reflected force F - 2 (F.v1) v1; saddle test; L-BFGS
+direction; Rodrigues retraction) followed by the topological charge.
+
+metric: spin-HVP throughput of the whole step, N * (HVPs per step) / step time.
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same step on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import inputs  # noqa: E402
+
+L = 2048
+K_MODES, BLOCK, STEPS = 8, 8, 12
+HVP_PER_STEP = BLOCK * STEPS
+METRIC = "spin-HVP Gspin/s"
+UNIT = "Gspin-HVP/s"
+WORKLOAD = "roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12)"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def config(extra=None):
+    c = {"workload": WORKLOAD, "lattice": f"{L}x{L}", "spins": L * L, "shells": 3, "k": K_MODES,
+         "block": BLOCK, "krylov_steps": STEPS, "hvps_per_step": HVP_PER_STEP,
+         "l2": "inputs larger than L2 (96 Krylov fields x 50 MB each per step)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def start_block(n, seed):
+    return np.stack([inputs.gaussian_field(seed, L, L, offset=j * 3 * L * L) for j in range(n)])
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------
+def oracle_sample(m, v_block, n_hvp):
+    """Energy + Riemannian gradient and n_hvp tangent HVPs of the oracle on the
+    full 2048 x 2048 lattice; returns seconds."""
+    from oracle import spin
+    from oracle.model import model_from_workload
+    M = model_from_workload(inputs.WORKLOADS[4])
+    t0 = time.perf_counter()
+    g, s = spin.riemann_grad(M, m)
+    for j in range(n_hvp):
+        spin.hvp(M, m, s, v_block[j % len(v_block)])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(m, n_hvp=8):
+    from oracle import spin
+    v = [spin.project(m, x) for x in start_block(2, 4242)]
+    t = oracle_sample(m, v, n_hvp)
+    value = L * L * n_hvp / t / 1e9
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"energy+gradient and {n_hvp} tangent HVPs of the numpy FP64 oracle on the full "
+                      f"2048x2048 lattice ({t:.1f} s); numpy elementwise ops run on one host core"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    m = inputs.workload4_state()
+    from oracle import spin
+    v = [spin.project(m, x) for x in start_block(2, 4242)]
+    n_hvp = 2
+    for _ in range(args.warmup):
+        oracle_sample(m, v, n_hvp)
+    ts = [oracle_sample(m, v, n_hvp) for _ in range(args.steps)]
+    t = sum(ts)
+    value = L * L * n_hvp * args.steps / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config({"sample": "per step: energy+gradient and 2 HVPs (FP64 numpy oracle)"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: energy+gradient and 2 tangent HVPs on the full lattice"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2509_26269_gb300 as mo
+    from paper_2509_26269_gb300 import Context
+
+    p = inputs.WORKLOADS[4]
+    ctx = Context(L, L, J=p["J"], D=p["D"], K=p["K"], muB=p["muB"], dtype=torch.float32,
+                  k=K_MODES, block=BLOCK, krylov_steps=STEPS)
+    walker = rank
+    m_host = inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, walker))
+    m0 = torch.from_numpy(m_host).to(device="cuda", dtype=torch.float32)
+    V0 = torch.from_numpy(start_block(BLOCK, inputs.workload_seed(4, walker) + 17)).to("cuda", torch.float32)
+    m = m0.clone()
+    V = V0.clone()
+    params = ctx.params
+    out = torch.empty(6, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    Q = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def step():
+        mo.moto_mmf_step(ctx.handle, m, params, V, out, status)
+        mo.moto_topo_charge(ctx.handle, m, Q)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("NVIDIA_SMI_INDEX", local)))
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t[0])
+    value = world * L * L * HVP_PER_STEP / (ms * 1e-3) / 1e9
+
+    # ---- per-kernel-class times inside one real step (CUDA events) ----------
+    mo.moto_profile_begin(ctx.handle, 4096)
+    step()
+    prof = mo.moto_profile_end(ctx.handle)
+    torch.cuda.synchronize()
+    launches = sum(v[0] for v in prof.values()) + 1  # + the charge kernel
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_l, dom_ms, dom_bytes = prof[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
+    hvp = prof["hvp"]
+    hvp_gbs = hvp[2] / (hvp[1] * 1e-3) / 1e9 if hvp[1] > 0 else 0.0
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    pin_m = torch.from_numpy(m_host.astype(np.float32)).pin_memory()
+    res_host = torch.empty(7, dtype=torch.float64).pin_memory()
+    m.copy_(m0)
+    V.copy_(V0)
+    mo.moto_lbfgs_reset(ctx.handle)
+
+    def e2e_step():
+        m.copy_(pin_m, non_blocking=True)
+        mo.moto_mmf_step(ctx.handle, m, params, V, out, status)
+        mo.moto_topo_charge(ctx.handle, m, Q)
+        res_host[:6].copy_(out, non_blocking=True)
+        res_host[6:].copy_(Q, non_blocking=True)
+
+    for _ in range(max(args.warmup, 0)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_e2e = float(t[0])
+    e2e = {"value": world * L * L * HVP_PER_STEP / (ms_e2e * 1e-3) / 1e9, "unit": UNIT,
+           "h2d_bytes_per_step": int(pin_m.numel() * 4), "d2h_bytes_per_step": int(res_host.numel() * 8)}
+
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline(m_host) if (world == 1 and not args.no_cpu_baseline) else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single"}),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "launches_in_step": n_l, "ms_in_step": dom_ms},
+            "kernel_classes": {k: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] * 1e-3) / 1e9 if v[1] else 0.0)}
+                               for k, v in prof.items()},
+            "hvp_gbs": hvp_gbs,
+            "hvp_gspin_s": (L * L * HVP_PER_STEP) / (hvp[1] * 1e-3) / 1e9 if hvp[1] else 0.0,
+            "e2e": e2e,
+            "gpu_launches": launches * args.steps,
+            "clocks": ck,
+            "cpu_baseline": cpu,
+            "trace": {"E": float(out[0]), "fmax": float(out[1]), "lam1": float(out[2]), "lam2": float(out[3]),
+                      "Q": float(Q[0])},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * moto.h -- C ABI of the GB300 (sm_103a) minimum-mode kernel for atomistic
+ * spin systems on a periodic 2D triangular lattice (arXiv 2509.26269, "MOTO":
+ * bilayer minimum-mode following with HVP-driven Krylov eigensolvers).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.  A spin field or a tangent vector field is a contiguous device array
+ *   of 3*N elements, N = L1*L2, component-major (structure of arrays):
+ *   x[c*N + i2*L1 + i1] is component c (0 = x, 1 = y, 2 = z) of site (i1, i2),
+ *   the site at i1*a1 + i2*a2 with a1 = (1, 0), a2 = (1/2, sqrt(3)/2).  The
+ *   element type is float (MOTO_F32) or double (MOTO_F64), fixed when the
+ *   context is created.  Scalars produced on the device (energies, eigenvalues,
+ *   forces) are always double.  Base addresses must be 16-byte aligned.
+ * Ownership.  Every pointer argument is caller-owned memory; the library never
+ *   frees or retains it past the call's stream work.  "dev" pointers are device
+ *   memory, all others host memory.  The context owns its scratch (Krylov
+ *   basis, L-BFGS history, reduction partials), sized once in moto_create; no
+ *   other call allocates device memory.
+ * Streams.  Calls enqueue work on the given stream (a cudaStream_t passed as
+ *   void*; NULL = legacy default stream) and return without synchronising,
+ *   except where stated (moto_ascend, moto_descend read a status word back).
+ *   A context is not thread-safe and must not be used on two streams at once.
+ * Errors.  Every call returns an int: MOTO_OK (0), a positive informational
+ *   code, or a negative error.  Argument errors are detected on the host before
+ *   any launch.  Errors detected on the device (non-finite values, a Krylov
+ *   breakdown, a timeout of a bounded wait) are written to the context's
+ *   device status word and returned by moto_status(); they never trap.
+ * Units.  Energies and model parameters in meV, forces (torques) in meV/rad,
+ *   eigenvalues in meV (per rad^2), angles in rad.
+ */
+#ifndef MOTO_H
+#define MOTO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct moto_ctx moto_ctx;
+
+enum {
+  MOTO_F32 = 0,
+  MOTO_F64 = 1
+};
+
+enum {
+  MOTO_OK = 0,
+  MOTO_NOT_CONVERGED = 1,   /* an iteration hit its cap; results are the last iterate */
+  MOTO_ERR_ARG = -1,        /* invalid argument (checked on the host) */
+  MOTO_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  MOTO_ERR_NUMERIC = -3,    /* Krylov breakdown or a non-SPD small Gram matrix */
+  MOTO_ERR_NONFINITE = -4,  /* NaN/Inf met on the device */
+  MOTO_ERR_TIMEOUT = -5,    /* a bounded device-side wait gave up */
+  MOTO_ERR_NOMEM = -6       /* moto_create could not allocate its scratch */
+};
+
+enum {
+  MOTO_SOLVER_LANCZOS = 0,  /* block Lanczos, block size params.block (1 = Lanczos) */
+  MOTO_SOLVER_LOBPCG = 1
+};
+
+#define MOTO_MAX_K 8        /* modes per solve */
+#define MOTO_MAX_BASIS 96   /* Krylov basis vectors (block * steps) */
+#define MOTO_MAX_MEM 8      /* L-BFGS pairs */
+
+/* Spin Hamiltonian of Eq. param-hamiltonian (Methods, "Spin Hamiltonian and
+ * manifold gradient"), read with ordered-pair sums (each bond counted twice):
+ *   E = - sum_i sum_s J[s] sum_{d in shell s} m_i . m_{i+d}
+ *       - D sum_i sum_{d in shell 1} (z x d_hat) . (m_i x m_{i+d})
+ *       - muB sum_i m_iz - K sum_i m_iz^2
+ * Shells (index-space offsets): 1: +-(1,0), +-(0,1), +-(-1,1);
+ * 2: +-(1,1), +-(-1,2), +-(-2,1); 3: +-(2,0), +-(0,2), +-(-2,2). */
+typedef struct {
+  int L1, L2;        /* lattice sides, each >= 5 */
+  int n_shells;      /* 1..3 exchange shells */
+  double J[3];       /* exchange per shell, meV */
+  double D;          /* Neel DMI on shell 1, meV */
+  double K;          /* uniaxial anisotropy along z, meV */
+  double muB;        /* Zeeman energy mu*B along +z, meV */
+} moto_model;
+
+/* Parameters of the inner (eigensolver) and outer (ascent, descent) layers.
+ * moto_default_params fills the values used throughout the tests. */
+typedef struct {
+  int k;              /* eigenpairs wanted, 1..MOTO_MAX_K                       (1) */
+  int solver;         /* MOTO_SOLVER_*                                         (LANCZOS) */
+  int block;          /* block size of block Lanczos, k..MOTO_MAX_K            (1) */
+  int krylov_steps;   /* Lanczos steps (block steps); block*steps <= MAX_BASIS (60) */
+  int max_iter;       /* LOBPCG iteration cap                                  (200) */
+  double tol;         /* LOBPCG: stop when all |H x - theta x| <= tol*|theta|max (1e-6) */
+  int lbfgs_mem;      /* L-BFGS pairs, 1..MOTO_MAX_MEM                         (5) */
+  double theta_max;   /* largest per-spin rotation of one step, rad             (0.2) */
+  double gamma0;      /* steepest-descent scale without history, rad^2/meV      (0.02) */
+  double tau_F;       /* force tolerance, meV/rad                               (1e-3) */
+  double eta_theta;   /* largest per-spin rotation of a descent seed, rad       (0.1) */
+  int max_steps;      /* ascent step cap                                       (300) */
+  int descent_max_steps; /* descent step cap per side                          (5000) */
+} moto_params;
+
+/* Fills *p with the defaults listed above. */
+void moto_default_params(moto_params* p);
+
+/* Creates a context for one lattice: validates the model (L1, L2 >= 5,
+ * 1 <= n_shells <= 3) and params (k, block, steps, mem limits), then
+ * allocates the scratch every later call uses.  dtype is MOTO_F32 or
+ * MOTO_F64.  On success *out receives the context.  Must be called with the
+ * target device current. */
+int moto_create(const moto_model* model, int dtype, const moto_params* params, moto_ctx** out);
+
+/* Releases the context and its scratch (synchronises the device first). */
+void moto_destroy(moto_ctx* ctx);
+
+/* Energy and Riemannian gradient (Methods, "Gradient, HVP, and Hessian via
+ * the autograd engine": F = -grad E understood as tangent-projected).
+ * m_dev: unit spins (3N).  Writes, each optional (NULL to skip):
+ *   g_dev  (3N): g_i = grad_i E - s_i m_i, the Riemannian gradient (F = -g);
+ *   s_dev  (N):  s_i = m_i . grad_i E (needed by moto_hvp);
+ *   out_dev (2 doubles): [E, max_i |g_i|].
+ * E here is summed in double from per-site shares computed in the context
+ * precision; moto_energy gives the FP64-arithmetic energy. */
+int moto_energy_grad(moto_ctx* ctx, const void* m_dev, void* g_dev, void* s_dev,
+                     double* out_dev, void* stream);
+
+/* E(m) of Eq. param-hamiltonian evaluated in double arithmetic whatever the
+ * context precision (final saddle and minimum energies).  E_dev: 1 double. */
+int moto_energy(moto_ctx* ctx, const void* m_dev, double* E_dev, void* stream);
+
+/* Tangent Hessian-vector products (Methods, "HVP operator mode"):
+ *   (H v)_i = P_i [ (hess E v)_i - s_i v_i ],   P_i = I - m_i m_i^T,
+ * for nvec tangent vectors v_j stored at v_dev + j*ldv (element stride ldv >=
+ * 3N), results at hv_dev + j*ldhv.  s_dev from moto_energy_grad at the same m.
+ * For tangent v this is the Riemannian Hessian on the product of spheres. */
+int moto_hvp(moto_ctx* ctx, const void* m_dev, const void* s_dev, const void* v_dev,
+             size_t ldv, void* hv_dev, size_t ldhv, int nvec, void* stream);
+
+/* Inner layer of the bilayer MMF kernel (Results, "Bilayer MMF"): the k
+ * smallest eigenpairs of the tangent Hessian at m by HVP-driven block
+ * Lanczos or LOBPCG (params->solver).
+ *   v0_dev:  start vectors, params->block (Lanczos) or params->k (LOBPCG)
+ *            fields of 3N elements, consecutive; projected on the tangent
+ *            planes before use.
+ *   V_dev:   out, k Ritz vectors (3N each, consecutive), tangent, unit norm,
+ *            entry of largest magnitude positive (lowest index on ties).
+ *   lam_dev: out, MOTO_MAX_BASIS doubles: Ritz values ascending (unused
+ *            entries set to +inf).
+ *   info_dev: out, 2 ints: [iterations or steps done, device status].
+ * s_dev may be NULL, in which case it is recomputed from m. */
+int moto_lowest_modes(moto_ctx* ctx, const void* m_dev, const void* s_dev,
+                      const moto_params* params, const void* v0_dev, void* V_dev,
+                      double* lam_dev, int* info_dev, void* stream);
+
+/* Topological charge Q = -(1/4pi) sum over the 2N elementary triangles of the
+ * Berg-Luescher solid angle (up triangles (i, i+a1, i+a2), down triangles
+ * (i+a1, i+a1+a2, i+a2)).  Q_dev: 1 double. */
+int moto_topo_charge(moto_ctx* ctx, const void* m_dev, double* Q_dev, void* stream);
+
+/* Clears the L-BFGS history of the context (start of an ascent or descent). */
+int moto_lbfgs_reset(moto_ctx* ctx, void* stream);
+
+/* One step of the outer layer (Results, "Bilayer MMF"; Algorithm 1 of
+ * Supplementary Note 1): g at m, the k lowest modes warm-started from V_dev,
+ * F_mmf = F - 2 (F . v1) v1 with F = -g, the saddle test
+ * max_i |F_mmf,i| <= tau_F and lambda_1 < 0 < lambda_2, and unless the test
+ * passed, an L-BFGS step on -F_mmf capped at theta_max per spin and applied
+ * by a per-spin Rodrigues rotation.
+ *   m_dev:   in/out spins.  V_dev: in/out modes (k fields), also the start
+ *            of the inner solve (the first block column when block > k is
+ *            filled from v0 of the context's last solve).
+ *   out_dev: out, 6 doubles [E, max|F_mmf,i|, lambda_1, lambda_2, max|g_i|, F.v1]
+ *            at the m the step started from.
+ *   status_dev: out, 1 int: 1 if the saddle test passed (m unchanged), else 0.
+ * The L-BFGS history persists in the context between calls. */
+int moto_mmf_step(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V_dev,
+                  double* out_dev, int* status_dev, void* stream);
+
+/* Runs moto_mmf_step until the saddle test passes or params->max_steps steps
+ * were taken, reading the status word back every `check_every` steps
+ * (synchronises the stream).  trace_dev (optional, 6 doubles per step,
+ * max_steps+1 rows) receives each step's out vector.  *steps_out: steps
+ * taken.  Returns MOTO_OK at a saddle, MOTO_NOT_CONVERGED at the cap. */
+int moto_ascend(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V_dev,
+                double* trace_dev, int check_every, int* steps_out, void* stream);
+
+/* Two-sided descent (Results, "Deterministic bidirectional saddle descent";
+ * Algorithm 1): seeds m_saddle +- eta v1 with eta = eta_theta / max_i |v1_i|
+ * (retracted), each relaxed by L-BFGS on g until max_i |g_i| <= tau_F or
+ * descent_max_steps.  Writes m_plus_dev, m_minus_dev (3N each) and
+ * out_dev (6 doubles): [E+, Q+, E-, Q-, steps+, steps-] with E in double
+ * arithmetic.  Synchronises the stream.  Returns MOTO_OK if both sides
+ * converged, MOTO_NOT_CONVERGED otherwise. */
+int moto_descend(moto_ctx* ctx, const void* m_saddle_dev, const void* v1_dev,
+                 const moto_params* params, void* m_plus_dev, void* m_minus_dev,
+                 double* out_dev, void* stream);
+
+/* Device status word of the context (synchronises the stream): MOTO_OK or
+ * the first device-detected error since the last moto_clear_status. */
+int moto_status(moto_ctx* ctx, void* stream);
+int moto_clear_status(moto_ctx* ctx, void* stream);
+
+/* Human-readable text of a return code (static storage). */
+const char* moto_status_string(int code);
+
+/* Launch profiler (tracing).  moto_profile_begin starts recording a CUDA
+ * event pair around each of the next `capacity` launches that the context's
+ * solver sequences enqueue, tagged with a kernel class
+ *   0 HVP, 1 Gram (skinny X^T Y), 2 field combination, 3 energy/gradient
+ *   stencil, 4 single-block FP64 steps, 5 other field kernels
+ * and the algorithmic bytes of the launch (every field read or written once).
+ * moto_profile_end synchronises, writes per class (nkinds entries each,
+ * NULL to skip) the number of launches, the summed event time in ms and the
+ * summed algorithmic bytes, and releases the events.  Launches beyond
+ * `capacity` are not recorded.  Not for use during stream capture. */
+int moto_profile_begin(moto_ctx* ctx, int capacity);
+int moto_profile_end(moto_ctx* ctx, int nkinds, int* launches, double* ms, double* bytes);
+
+/* Bytes of device scratch owned by the context. */
+size_t moto_workspace_bytes(const moto_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOTO_H */

@@ -53,8 +53,12 @@ def finish_ritz(m: np.ndarray, v: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Lanczos
 # ----------------------------------------------------------------------------
-def lanczos(op, q0: np.ndarray, nsteps: int, breakdown: float = 1e-12):
+def lanczos(op, q0: np.ndarray, nsteps: int, breakdown: float = 1e-12, proj=None):
     """Lanczos with full CGS2 reorthogonalisation.
+
+    ``proj`` (optional) maps a vector onto the subspace the operator lives on;
+    it is applied after the three-term recurrence, since a small beta would
+    otherwise magnify rounding-level components outside that subspace.
 
     Returns (theta, Y, Q): Ritz values ascending, eigenvectors of T (columns),
     and the orthonormal Krylov basis as an (nq, n) matrix."""
@@ -70,6 +74,8 @@ def lanczos(op, q0: np.ndarray, nsteps: int, breakdown: float = 1e-12):
         w = w - a * Q[j]
         if j > 0:
             w = w - beta[j - 1] * Q[j - 1]
+        if proj is not None:
+            w = proj(w.reshape(q0.shape)).ravel()
         for _ in range(2):
             c = Q[: j + 1] @ w
             w = w - Q[: j + 1].T @ c
@@ -91,7 +97,7 @@ def lanczos_modes(model, m, s, q0, nsteps: int, k: int = 1):
     Returns (lam, V): the nsteps-bounded Ritz values (all of them, ascending) and
     the first k finished Ritz vectors."""
     op = lambda v: spin.hvp(model, m, s, v)
-    theta, Y, Q = lanczos(op, spin.project(m, q0), nsteps)
+    theta, Y, Q = lanczos(op, spin.project(m, q0), nsteps, proj=lambda v: spin.project(m, v))
     V = []
     for i in range(k):
         v = (Q.T @ Y[:, i]).reshape(m.shape)
@@ -102,25 +108,36 @@ def lanczos_modes(model, m, s, q0, nsteps: int, k: int = 1):
 # ----------------------------------------------------------------------------
 # block Lanczos
 # ----------------------------------------------------------------------------
+def _chol_factor(W: np.ndarray):
+    """Lower Cholesky factor of W W^T (rows of W are vectors), or None."""
+    try:
+        return np.linalg.cholesky(W @ W.T)
+    except np.linalg.LinAlgError:
+        return None
+
+
+def _dependent(L, G) -> bool:
+    """A column whose new direction is below 1e-6 of its own length."""
+    return bool(np.any(np.diag(L) <= 1e-6 * np.sqrt(np.clip(np.diag(G), 0.0, None))))
+
+
 def cholqr2(W: np.ndarray):
-    """Cholesky QR applied twice: W = Q R with Q^T Q = I.  W is (b, n) with rows
-    as vectors.  Returns (Q, R) or None when W is numerically rank deficient."""
+    """Cholesky QR applied twice: W = Q R with Q Q^T = I (rows are vectors).
+    Returns (Q, R), or None when W is numerically rank deficient (a factor
+    fails or a column keeps less than 1e-6 of its length)."""
     R = np.eye(W.shape[0])
     Qm = W
     for _ in range(2):
         G = Qm @ Qm.T
-        try:
-            Lc = np.linalg.cholesky(G)
-        except np.linalg.LinAlgError:
-            return None
-        if np.min(np.diag(Lc)) <= 1e-12 * np.max(np.diag(Lc)):
+        Lc = _chol_factor(Qm)
+        if Lc is None or _dependent(Lc, G):
             return None
         Qm = np.linalg.solve(Lc, Qm)          # L^{-1} W  (rows)
         R = Lc.T @ R
     return Qm, R
 
 
-def block_lanczos(op_block, X0: np.ndarray, nsteps: int):
+def block_lanczos(op_block, X0: np.ndarray, nsteps: int, breakdown: float = 1e-12, proj=None):
     """Block Lanczos with full CGS2 reorthogonalisation of each new block.
 
     op_block maps a (b, n) block to H applied row-wise.  Returns (theta, Y, Q)
@@ -133,6 +150,7 @@ def block_lanczos(op_block, X0: np.ndarray, nsteps: int):
     T = np.zeros((b * nsteps, b * nsteps))
     Rprev = None
     nb_used = 0
+    tnorm = 0.0
     for j in range(nsteps):
         Qj = blocks[j]
         W = op_block(Qj)
@@ -143,16 +161,30 @@ def block_lanczos(op_block, X0: np.ndarray, nsteps: int):
         W = W - A.T @ Qj                       # W - Q_j A (rows)
         if j > 0:
             W = W - Rprev @ blocks[j - 1]      # W - Q_{j-1} R_j^T (rows)
+        if proj is not None:
+            W = proj(W)
         Qall = np.concatenate(blocks, axis=0)
         for _ in range(2):
             C = W @ Qall.T
             W = W - C @ Qall
         if j == nsteps - 1:
             break
-        qr = cholqr2(W)
-        if qr is None:
+        # Cholesky QR of the new block; breakdown when its smallest diagonal
+        # is below rel * |T| (|T| estimated by the largest row sum seen, as for
+        # beta_j <= 1e-12 |T| in the plain Lanczos above)
+        L1 = _chol_factor(W)
+        if L1 is None:
             break
-        Qn, Rn = qr
+        rows = np.abs(A).sum(axis=1) + (np.abs(Rprev).sum(axis=1) if Rprev is not None else 0.0)
+        tnorm = max(tnorm, float(np.max(rows)) + float(np.max(np.diag(L1))))
+        if np.min(np.diag(L1)) <= breakdown * tnorm:
+            break
+        Q1 = np.linalg.solve(L1, W)
+        L2 = _chol_factor(Q1)
+        if L2 is None or _dependent(L2, Q1 @ Q1.T):
+            break
+        Qn = np.linalg.solve(L2, Q1)
+        Rn = L2.T @ L1.T
         T[(j + 1) * b:(j + 2) * b, j * b:(j + 1) * b] = Rn
         T[j * b:(j + 1) * b, (j + 1) * b:(j + 2) * b] = Rn.T
         blocks.append(Qn)
@@ -165,8 +197,9 @@ def block_lanczos(op_block, X0: np.ndarray, nsteps: int):
 def block_lanczos_modes(model, m, s, X0_list, nsteps: int, k: int):
     shape = m.shape
     op_block = lambda B: np.stack([spin.hvp(model, m, s, r.reshape(shape)).ravel() for r in B])
+    proj = lambda B: np.stack([spin.project(m, r.reshape(shape)).ravel() for r in B])
     X0 = np.stack([spin.project(m, x).ravel() for x in X0_list])
-    theta, Y, Q = block_lanczos(op_block, X0, nsteps)
+    theta, Y, Q = block_lanczos(op_block, X0, nsteps, proj=proj)
     V = [finish_ritz(m, (Q.T @ Y[:, i]).reshape(shape)) for i in range(k)]
     return theta, V
 

@@ -1,0 +1,236 @@
+"""Python binding of ``libmoto.so``, the GB300 (sm_103a) minimum-mode kernel
+for atomistic spin systems (arXiv 2509.26269).
+
+Every entry point of ``include/moto.h`` is exposed under the same name; the
+functions only marshal arguments (torch CUDA tensors or raw device pointers
+as ints) into the C ABI.  All computation runs in the library's CUDA kernels;
+there is no CPU path: importing this package fails if ``libmoto.so`` has not
+been built (``python paper_2509_26269_gb300/build.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmoto.so")
+
+MOTO_F32, MOTO_F64 = 0, 1
+MOTO_OK, MOTO_NOT_CONVERGED = 0, 1
+MOTO_ERR_ARG, MOTO_ERR_CUDA, MOTO_ERR_NUMERIC = -1, -2, -3
+MOTO_ERR_NONFINITE, MOTO_ERR_TIMEOUT, MOTO_ERR_NOMEM = -4, -5, -6
+MOTO_SOLVER_LANCZOS, MOTO_SOLVER_LOBPCG = 0, 1
+MOTO_MAX_K, MOTO_MAX_BASIS, MOTO_MAX_MEM = 8, 96, 8
+
+
+class moto_model(ctypes.Structure):
+    _fields_ = [
+        ("L1", ctypes.c_int), ("L2", ctypes.c_int), ("n_shells", ctypes.c_int),
+        ("J", ctypes.c_double * 3), ("D", ctypes.c_double), ("K", ctypes.c_double), ("muB", ctypes.c_double),
+    ]
+
+
+class moto_params(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int), ("solver", ctypes.c_int), ("block", ctypes.c_int), ("krylov_steps", ctypes.c_int),
+        ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("lbfgs_mem", ctypes.c_int),
+        ("theta_max", ctypes.c_double), ("gamma0", ctypes.c_double), ("tau_F", ctypes.c_double),
+        ("eta_theta", ctypes.c_double), ("max_steps", ctypes.c_int), ("descent_max_steps", ctypes.c_int),
+    ]
+
+
+class MotoError(RuntimeError):
+    pass
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python paper_2509_26269_gb300/build.py` "
+            "(this package has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, Z = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
+    sig = {
+        "moto_default_params": (None, [ctypes.POINTER(moto_params)]),
+        "moto_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params), ctypes.POINTER(P)]),
+        "moto_destroy": (None, [P]),
+        "moto_energy_grad": (I, [P, P, P, P, P, P]),
+        "moto_energy": (I, [P, P, P, P]),
+        "moto_hvp": (I, [P, P, P, P, Z, P, Z, I, P]),
+        "moto_lowest_modes": (I, [P, P, P, ctypes.POINTER(moto_params), P, P, P, P, P]),
+        "moto_topo_charge": (I, [P, P, P, P]),
+        "moto_lbfgs_reset": (I, [P, P]),
+        "moto_mmf_step": (I, [P, P, ctypes.POINTER(moto_params), P, P, P, P]),
+        "moto_ascend": (I, [P, P, ctypes.POINTER(moto_params), P, P, I, ctypes.POINTER(I), P]),
+        "moto_descend": (I, [P, P, P, ctypes.POINTER(moto_params), P, P, P, P]),
+        "moto_status": (I, [P, P]),
+        "moto_clear_status": (I, [P, P]),
+        "moto_status_string": (ctypes.c_char_p, [I]),
+        "moto_workspace_bytes": (Z, [P]),
+        "moto_profile_begin": (I, [P, I]),
+        "moto_profile_end": (I, [P, I, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = (
+    "moto_default_params", "moto_create", "moto_destroy", "moto_energy_grad", "moto_energy", "moto_hvp",
+    "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
+    "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
+    "moto_profile_end",
+)
+PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec")
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _ptr(x):
+    """Device address of a torch CUDA tensor (checked contiguous), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda:
+        raise MotoError("expected a CUDA tensor")
+    if not x.is_contiguous():
+        raise MotoError("expected a contiguous tensor")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc, what, ok=(MOTO_OK,)):
+    if rc not in ok:
+        raise MotoError(f"{what}: {_lib.moto_status_string(rc).decode()} ({rc})")
+    return rc
+
+
+def make_model(L1, L2, J=(1.0,), D=0.0, K=0.0, muB=0.0) -> moto_model:
+    mm = moto_model()
+    mm.L1, mm.L2, mm.n_shells = int(L1), int(L2), len(J)
+    for i in range(3):
+        mm.J[i] = float(J[i]) if i < len(J) else 0.0
+    mm.D, mm.K, mm.muB = float(D), float(K), float(muB)
+    return mm
+
+
+def make_params(**kw) -> moto_params:
+    p = moto_params()
+    _lib.moto_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise MotoError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, same names
+# ---------------------------------------------------------------------------
+def moto_default_params() -> moto_params:
+    return make_params()
+
+
+def moto_create(model: moto_model, dtype: int, params: moto_params | None = None) -> int:
+    h = ctypes.c_void_p()
+    p = params if params is not None else make_params()
+    _check(_lib.moto_create(ctypes.byref(model), int(dtype), ctypes.byref(p), ctypes.byref(h)), "moto_create")
+    return h.value
+
+
+def moto_destroy(ctx: int) -> None:
+    _lib.moto_destroy(ctx)
+
+
+def moto_energy_grad(ctx, m, g=None, s=None, out=None, stream=None):
+    _check(_lib.moto_energy_grad(ctx, _ptr(m), _ptr(g), _ptr(s), _ptr(out), _stream(stream)), "moto_energy_grad")
+
+
+def moto_energy(ctx, m, E, stream=None):
+    _check(_lib.moto_energy(ctx, _ptr(m), _ptr(E), _stream(stream)), "moto_energy")
+
+
+def moto_hvp(ctx, m, s, v, ldv, hv, ldhv, nvec=1, stream=None):
+    _check(_lib.moto_hvp(ctx, _ptr(m), _ptr(s), _ptr(v), int(ldv), _ptr(hv), int(ldhv), int(nvec),
+                         _stream(stream)), "moto_hvp")
+
+
+def moto_lowest_modes(ctx, m, s, params, v0, V, lam, info=None, stream=None):
+    _check(_lib.moto_lowest_modes(ctx, _ptr(m), _ptr(s), ctypes.byref(params), _ptr(v0), _ptr(V), _ptr(lam),
+                                  _ptr(info), _stream(stream)), "moto_lowest_modes")
+
+
+def moto_topo_charge(ctx, m, Q, stream=None):
+    _check(_lib.moto_topo_charge(ctx, _ptr(m), _ptr(Q), _stream(stream)), "moto_topo_charge")
+
+
+def moto_lbfgs_reset(ctx, stream=None):
+    _check(_lib.moto_lbfgs_reset(ctx, _stream(stream)), "moto_lbfgs_reset")
+
+
+def moto_mmf_step(ctx, m, params, V, out=None, status=None, stream=None):
+    _check(_lib.moto_mmf_step(ctx, _ptr(m), ctypes.byref(params), _ptr(V), _ptr(out), _ptr(status),
+                              _stream(stream)), "moto_mmf_step")
+
+
+def moto_ascend(ctx, m, params, V, trace=None, check_every=10, stream=None):
+    """Returns (code, steps); code is MOTO_OK at a saddle, MOTO_NOT_CONVERGED at the cap."""
+    steps = ctypes.c_int(0)
+    rc = _lib.moto_ascend(ctx, _ptr(m), ctypes.byref(params), _ptr(V), _ptr(trace), int(check_every),
+                          ctypes.byref(steps), _stream(stream))
+    _check(rc, "moto_ascend", ok=(MOTO_OK, MOTO_NOT_CONVERGED))
+    return rc, steps.value
+
+
+def moto_descend(ctx, m_saddle, v1, params, m_plus, m_minus, out, stream=None):
+    rc = _lib.moto_descend(ctx, _ptr(m_saddle), _ptr(v1), ctypes.byref(params), _ptr(m_plus), _ptr(m_minus),
+                           _ptr(out), _stream(stream))
+    _check(rc, "moto_descend", ok=(MOTO_OK, MOTO_NOT_CONVERGED))
+    return rc
+
+
+def moto_status(ctx, stream=None) -> int:
+    return _lib.moto_status(ctx, _stream(stream))
+
+
+def moto_clear_status(ctx, stream=None):
+    _check(_lib.moto_clear_status(ctx, _stream(stream)), "moto_clear_status")
+
+
+def moto_status_string(code: int) -> str:
+    return _lib.moto_status_string(int(code)).decode()
+
+
+def moto_workspace_bytes(ctx) -> int:
+    return int(_lib.moto_workspace_bytes(ctx))
+
+
+def moto_profile_begin(ctx, capacity=8192):
+    _check(_lib.moto_profile_begin(ctx, int(capacity)), "moto_profile_begin")
+
+
+def moto_profile_end(ctx):
+    """Returns {kind: (launches, ms, algorithmic bytes)} for the recorded launches."""
+    n = len(PROFILE_KINDS)
+    launches = (ctypes.c_int * n)()
+    ms = (ctypes.c_double * n)()
+    nbytes = (ctypes.c_double * n)()
+    _check(_lib.moto_profile_end(ctx, n, ctypes.cast(launches, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p),
+                                 ctypes.cast(nbytes, ctypes.c_void_p)), "moto_profile_end")
+    return {k: (launches[i], ms[i], nbytes[i]) for i, k in enumerate(PROFILE_KINDS)}
+
+
+from .context import Context  # noqa: E402,F401

@@ -1,0 +1,867 @@
+// C ABI of the minimum-mode kernel: context and workspace management and the
+// host-side sequencing of the device steps.  Control stays on the device
+// (gate bits, step counters, convergence flags); the host only enqueues
+// launches, except moto_ascend / moto_descend / moto_status which read a
+// status word back.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <tuple>
+
+#include "internal.h"
+
+using namespace moto;
+
+struct moto_ctx {
+  ModelDev md;
+  int dtype;
+  size_t esize;
+  moto_params p;  // sizing parameters given at creation
+  int N;
+  size_t n3;  // 3N
+  size_t ld;  // element stride of internal vector fields
+  // device scratch
+  void* basis;  // MOTO_MAX_BASIS fields
+  void* W;      // MOTO_MAX_K fields
+  void* Wt;     // MOTO_MAX_K fields
+  void* g;      // gradient
+  void* s;      // s_i (N)
+  void* ring;   // L-BFGS: 2(mem+1) pair slots, G, G_prev, d, 2 staging
+  void* lob;    // LOBPCG blocks: 2 sets x [X, W, P, AX, AW, AP] (12 x MOTO_MAX_K fields)
+  double* dsm;  // small dense area
+  double* part;
+  unsigned* counter;
+  DevState* st;
+  size_t part_len;
+  size_t bytes;
+  // launch profiler (moto_profile_*): events around each launch of the
+  // Krylov / optimiser sequences, tagged with a kernel class and the
+  // algorithmic bytes that launch moves
+  int prof_on, prof_n, prof_cap;
+  cudaEvent_t* prof_ev;
+  int* prof_kind;
+  double* prof_bytes;
+  cudaStream_t prof_stream;
+};
+
+namespace {
+struct ProfScope {
+  moto_ctx* c;
+  bool on;
+  ProfScope(moto_ctx* c_, int kind, double bytes, cudaStream_t st) : c(c_), on(false) {
+    if (c->prof_on && c->prof_n < c->prof_cap) {
+      on = true;
+      c->prof_kind[c->prof_n] = kind;
+      c->prof_bytes[c->prof_n] = bytes;
+      cudaEventRecord(c->prof_ev[2 * c->prof_n], st);
+      c->prof_stream = st;
+    }
+  }
+  ~ProfScope() {
+    if (on) {
+      cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->prof_stream);
+      c->prof_n += 1;
+    }
+  }
+};
+}  // namespace
+#define MOTO_CAT2(a, b) a##b
+#define MOTO_CAT(a, b) MOTO_CAT2(a, b)
+#define PROF(kind, bytes) ProfScope MOTO_CAT(prof_scope_, __LINE__)(c, (kind), (double)(bytes), st)
+
+// kernel classes of the profiler
+enum { kPkHvp = 0, kPkGram = 1, kPkCombine = 2, kPkStencil = 3, kPkSmall = 4, kPkVec = 5, kPkCount = 6 };
+
+namespace {
+// Profiled launch wrappers: same arguments as the launchers, plus the context.
+// Bytes are the algorithmic traffic of the launch (each field read or written
+// once).
+template <typename T>
+void P_gram(moto_ctx* c, const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+            double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkGram, (double)((X == Y) ? nx : nx + ny) * n * sizeof(T));
+  launch_gram<T>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
+}
+template <typename T>
+void P_combine(moto_ctx* c, const T* X, size_t ldx, int nx, const int* nx_dev, const double* C, int ny, const T* Y,
+               size_t ldy, double beta, double sigma, T* out, size_t ldo, const T* m, int N, const int* gate, int mask,
+               cudaStream_t st) {
+  const double f = 3.0 * N * sizeof(T);
+  PROF(kPkCombine, f * (nx + ny + (beta != 0.0 ? ny : 0) + (m ? 1 : 0)));
+  launch_combine<T>(X, ldx, nx, nx_dev, C, ny, Y, ldy, beta, sigma, out, ldo, m, N, gate, mask, st);
+}
+template <typename T>
+void P_hvp(moto_ctx* c, const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
+           int nvec, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkHvp, (4.0 + 6.0 * nvec) * md.N * sizeof(T));
+  launch_hvp<T>(md, m, s, V, ldv, HV, ldhv, nvec, gate, mask, st);
+}
+template <typename T>
+void P_energy_grad(moto_ctx* c, const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
+                   double* out, int* status, bool fp64, cudaStream_t st) {
+  PROF(kPkStencil, (3.0 + (g ? 3.0 : 0.0) + (s ? 1.0 : 0.0)) * md.N * sizeof(T));
+  launch_energy_grad<T>(md, m, g, s, part, counter, out, status, fp64, st);
+}
+template <typename T>
+void P_project(moto_ctx* c, const T* m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N, const int* gate,
+               int mask, cudaStream_t st) {
+  PROF(kPkVec, (3.0 + 6.0 * nvec) * N * sizeof(T));
+  launch_project<T>(m, in, ldi, out, ldo, nvec, N, gate, mask, st);
+}
+template <typename T>
+void P_finish(moto_ctx* c, const T* m, T* V, size_t ldv, int k, int N, double* part, unsigned* counter, double* scal,
+              const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, (3.0 + 12.0 * k) * N * sizeof(T));
+  launch_finish<T>(m, V, ldv, k, N, part, counter, scal, gate, mask, st);
+}
+template <typename T>
+void P_mmf_force(moto_ctx* c, const T* g, const T* v1, const double* dot, double reflect, T* G, int N, double* part,
+                 unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, (v1 ? 9.0 : 6.0) * N * sizeof(T));
+  launch_mmf_force<T>(g, v1, dot, reflect, G, N, part, counter, fmax_out, gate, mask, st);
+}
+template <typename T>
+void P_lbfgs_pair(moto_ctx* c, const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
+                  const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, 24.0 * N * sizeof(T));
+  launch_lbfgs_pair<T>(m, d_prev, G_prev, G, ring, ld, stage, dst, N, gate, mask, st);
+}
+template <typename T>
+void P_lbfgs_direction(moto_ctx* c, const T* basis, size_t ld, int nb, const double* coef, const T* m, T* d, int N,
+                       double theta_max, double* part, unsigned* counter, DevState* dst, const int* gate, int mask,
+                       cudaStream_t st) {
+  PROF(kPkVec, (3.0 * nb + 6.0) * N * sizeof(T));
+  launch_lbfgs_direction<T>(basis, ld, nb, coef, m, d, N, theta_max, part, counter, dst, gate, mask, st);
+}
+template <typename T>
+void P_retract(moto_ctx* c, T* m, T* d, const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, 12.0 * N * sizeof(T));
+  launch_retract<T>(m, d, dst, N, gate, mask, st);
+}
+#define SMALL_WRAP(name)                                                 \
+  template <typename... A>                                               \
+  void P_##name(moto_ctx* c, A... args) {                                \
+    cudaStream_t st = std::get<sizeof...(A) - 1>(std::make_tuple(args...)); \
+    PROF(kPkSmall, 0.0);                                                 \
+    launch_##name(args...);                                              \
+  }
+SMALL_WRAP(lanczos_coeffs)
+SMALL_WRAP(cholqr)
+SMALL_WRAP(small_eig)
+SMALL_WRAP(lob_rr)
+SMALL_WRAP(lob_check)
+SMALL_WRAP(diag)
+SMALL_WRAP(lbfgs_solve)
+SMALL_WRAP(saddle_test)
+#undef SMALL_WRAP
+}  // namespace
+
+namespace {
+
+// small dense layout (doubles)
+constexpr size_t kT = 0;                                           // T: MAX_BASIS^2
+constexpr size_t kTheta = kT + MOTO_MAX_BASIS * MOTO_MAX_BASIS;    // MAX_BASIS
+constexpr size_t kY = kTheta + MOTO_MAX_BASIS;                     // MAX_BASIS * MAX_K
+constexpr size_t kC = kY + MOTO_MAX_BASIS * MOTO_MAX_K;            // MAX_BASIS * MAX_K
+constexpr size_t kC3 = kC + MOTO_MAX_BASIS * MOTO_MAX_K;           // 2K * K
+constexpr size_t kA = kC3 + 2 * MOTO_MAX_K * MOTO_MAX_K;           // K*K
+constexpr size_t kG = kA + MOTO_MAX_K * MOTO_MAX_K;                // K*K
+constexpr size_t kRinv = kG + MOTO_MAX_K * MOTO_MAX_K;             // K*K
+constexpr size_t kRacc = kRinv + MOTO_MAX_K * MOTO_MAX_K;          // K*K
+constexpr size_t kEG = kRacc + MOTO_MAX_K * MOTO_MAX_K;            // 2: [E, gmax]
+constexpr size_t kFmax = kEG + 2;                                  // 1
+constexpr size_t kScal = kFmax + 1;                                // MAX_K
+constexpr size_t kLbM = kScal + MOTO_MAX_K;                        // (2(mem+1)+1)^2
+constexpr size_t kLbMsz = (2 * MOTO_MAX_MEM + 3) * (2 * MOTO_MAX_MEM + 3);
+constexpr size_t kLbNew = kLbM + kLbMsz;                           // 3 * (2(mem+1)+1)
+constexpr size_t kLbCoef = kLbNew + 3 * (2 * MOTO_MAX_MEM + 3);    // 2(mem+1)+1
+constexpr size_t kTmp = kLbCoef + (2 * MOTO_MAX_MEM + 3);          // 8 scratch doubles
+constexpr size_t kLobG = kTmp + 8;                                 // 3K x 3K (LOBPCG Gram)
+constexpr size_t kLobM = kLobG + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 3K
+constexpr size_t kLobC = kLobM + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 2K coefficient blocks
+constexpr size_t kLobAux = kLobC + 6 * MOTO_MAX_K * MOTO_MAX_K;    // 64 aux
+constexpr size_t kDsmSize = kLobAux + 64 * MOTO_MAX_K;
+
+constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
+
+#define CK(x)                                 \
+  do {                                        \
+    cudaError_t e_ = (x);                     \
+    if (e_ != cudaSuccess) return MOTO_ERR_CUDA; \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
+
+template <typename T>
+T* F(void* base, size_t ld, int j) {
+  return static_cast<T*>(base) + (size_t)j * ld;
+}
+
+__global__ void state_kernel(DevState* st, int op) {
+  if (threadIdx.x != 0) return;
+  switch (op) {
+    case 0:  // begin Krylov solve
+      st->gate &= ~kGateKrylov;
+      st->steps = 0;
+      st->nT = 0;
+      st->tnorm = 0.0;
+      st->iters = 0;
+      break;
+    case 1:  // reset optimiser (ascent or descent start)
+      st->gate = 0;
+      st->pad[1] = 0;
+      st->lb_head = 0;
+      st->lb_count = 0;
+      st->lb_have_prev = 0;
+      st->converged = 0;
+      st->iters = 0;
+      break;
+    case 2:  // clear status
+      st->status = 0;
+      break;
+    case 3:  // begin LOBPCG
+      st->gate &= ~kGateKrylov;
+      st->steps = 0;
+      st->iters = 0;
+      st->hnorm = 0.0;
+      st->pad[0] = 0;
+      break;
+  }
+}
+
+__global__ void info_kernel(const DevState* st, int* info) {
+  if (threadIdx.x != 0) return;
+  info[0] = st->steps + st->iters;  // block steps (Lanczos) or iterations (LOBPCG)
+  info[1] = st->status;
+}
+
+__global__ void count_step_kernel(DevState* st) {
+  if (threadIdx.x == 0 && !(st->gate & kGateDone)) st->iters += 1;
+}
+
+int check_params(const moto_params* p) {
+  if (!p) return MOTO_ERR_ARG;
+  if (p->k < 1 || p->k > MOTO_MAX_K) return MOTO_ERR_ARG;
+  if (p->solver != MOTO_SOLVER_LANCZOS && p->solver != MOTO_SOLVER_LOBPCG) return MOTO_ERR_ARG;
+  if (p->solver == MOTO_SOLVER_LANCZOS) {
+    if (p->block < p->k || p->block > MOTO_MAX_K) return MOTO_ERR_ARG;
+    if (p->krylov_steps < 1 || p->block * p->krylov_steps > MOTO_MAX_BASIS) return MOTO_ERR_ARG;
+    if (p->block * p->krylov_steps < 2) return MOTO_ERR_ARG;
+  } else {
+    if (p->max_iter < 0) return MOTO_ERR_ARG;
+  }
+  if (p->lbfgs_mem < 1 || p->lbfgs_mem > MOTO_MAX_MEM) return MOTO_ERR_ARG;
+  if (!(p->theta_max > 0.0) || !(p->gamma0 > 0.0) || !(p->tau_F >= 0.0) || !(p->eta_theta > 0.0))
+    return MOTO_ERR_ARG;
+  if (p->max_steps < 0 || p->descent_max_steps < 0) return MOTO_ERR_ARG;
+  return MOTO_OK;
+}
+
+// ----------------------------------------------------------------------------
+// block Lanczos (block size b, `steps` block steps), Ritz vectors of the
+// nout lowest Ritz values into V
+// ----------------------------------------------------------------------------
+template <typename T>
+void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0, int b, int steps, T* V, size_t ldv,
+                   int nout, double* lam, cudaStream_t st) {
+  const int N = c->N;
+  const size_t n3 = c->n3, ld = c->ld;
+  T* Q = static_cast<T*>(c->basis);
+  T* W = static_cast<T*>(c->W);
+  T* Wt = static_cast<T*>(c->Wt);
+  double* D = c->dsm;
+  int* gate = &c->st->gate;
+  const int mk = kGateKrylov | kGateDone;
+  const double rel = (c->dtype == MOTO_F64) ? 1e-12 : 1e-6;
+  state_kernel<<<1, 32, 0, st>>>(c->st, 0);
+  // start block: project, Cholesky QR twice
+  P_project<T>(c, m, v0, ld0, W, ld, b, N, gate, kGateDone, st);
+  P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+  P_cholqr(c, D + kG, b, 0, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+  P_combine<T>(c, W, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Wt, ld, nullptr, N, gate, mk, st);
+  P_gram<T>(c, Wt, ld, b, Wt, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+  P_cholqr(c, D + kG, b, 1, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+  P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q, ld, nullptr, N, gate, mk, st);
+  for (int j = 0; j < steps; ++j) {
+    T* Qj = Q + (size_t)j * b * ld;
+    P_hvp<T>(c, c->md, m, s, Qj, ld, W, ld, b, gate, mk, st);
+    P_gram<T>(c, Qj, ld, b, W, ld, b, n3, D + kA, c->part, c->counter, gate, mk, st);
+    P_lanczos_coeffs(c, D + kA, b, j, D + kT, kLd, D + kC3, c->st, st);
+    const T* X3 = (j > 0) ? Q + (size_t)(j - 1) * b * ld : Qj;
+    // three-term recurrence, re-projected on the tangent planes: rounding-level
+    // normal components would otherwise grow by |alpha| / beta every step
+    P_combine<T>(c, X3, ld, (j > 0 ? 2 : 1) * b, nullptr, D + kC3, b, W, ld, 1.0, -1.0, W, ld, m, N, gate, mk,
+                      st);
+    const int nq = (j + 1) * b;
+    for (int pass = 0; pass < 2; ++pass) {
+      P_gram<T>(c, Q, ld, nq, W, ld, b, n3, D + kC, c->part, c->counter, gate, mk, st);
+      P_combine<T>(c, Q, ld, nq, nullptr, D + kC, b, W, ld, 1.0, -1.0, W, ld, nullptr, N, gate, mk, st);
+    }
+    if (j == steps - 1) break;
+    P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+    P_combine<T>(c, W, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Wt, ld, nullptr, N, gate, mk, st);
+    P_gram<T>(c, Wt, ld, b, Wt, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_cholqr(c, D + kG, b, 1, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+    P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q + (size_t)(j + 1) * b * ld, ld,
+                      nullptr, N, gate, mk, st);
+  }
+  P_small_eig(c, D + kT, kLd, lam, D + kY, nout, c->st, st);
+  P_combine<T>(c, Q, ld, b * steps, &c->st->nT, D + kY, nout, nullptr, 0, 0.0, 1.0, V, ldv, nullptr, N,
+                    gate, kGateDone, st);
+  P_finish<T>(c, m, V, ldv, nout, N, c->part, c->counter, D + kScal, gate, kGateDone, st);
+  (void)n3;
+}
+
+
+// ----------------------------------------------------------------------------
+// LOBPCG (block size k).  Two sets of blocks, each [X, W, P, AX, AW, AP] of k
+// fields; the set holding the current X is tracked on the device (st->pad[0])
+// so that a convergence stop in any iteration leaves the right block behind.
+// ----------------------------------------------------------------------------
+__global__ void fill_inf_kernel(double* lam, int from) {
+  for (int i = from + threadIdx.x; i < MOTO_MAX_BASIS; i += blockDim.x) lam[i] = 1.0 / 0.0;
+}
+
+__global__ void lob_swap_kernel(DevState* st, int mask) {
+  if (threadIdx.x == 0 && !(st->gate & mask)) st->pad[0] ^= 1;
+}
+
+template <typename T>
+__global__ void copy_current_kernel(const T* set0, const T* set1, size_t n, const DevState* st, T* out, size_t ld,
+                                    int k, size_t ldo) {
+  if (st->gate & kGateDone) return;
+  const T* src = st->pad[0] ? set1 : set0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < k; ++c) out[(size_t)c * ldo + e] = src[(size_t)c * ld + e];
+}
+
+template <typename T>
+void lobpcg(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0, int k, int max_iter, double tol, T* V,
+            size_t ldv, double* lam, cudaStream_t st) {
+  const int N = c->N;
+  const size_t n3 = c->n3, ld = c->ld;
+  double* D = c->dsm;
+  int* gate = &c->st->gate;
+  const int mk = kGateKrylov | kGateDone;
+  const double drop = (c->dtype == MOTO_F64) ? 1e-12 : 1e-8;
+  T* base = static_cast<T*>(c->lob);
+  T* Wt = static_cast<T*>(c->Wt);
+  auto SET = [&](int a) { return base + (size_t)a * 6 * MOTO_MAX_K * ld; };
+  auto blk = [&](T* S, int j) { return S + (size_t)j * k * ld; };  // 0 X, 1 W, 2 P, 3 AX, 4 AW, 5 AP
+  double* Gb = D + kLobG;
+  double* Mb = D + kLobM;
+  double* Cx = D + kLobC;
+  double* Cp = Cx + 3 * k * k;
+  state_kernel<<<1, 32, 0, st>>>(c->st, 3);
+  fill_inf_kernel<<<1, 128, 0, st>>>(lam, k);
+  // initial Rayleigh-Ritz on span(P v0)
+  T* A = SET(0);
+  T* B = SET(1);
+  P_project<T>(c, m, v0, ld0, blk(A, 0), ld, k, N, gate, kGateDone, st);
+  P_hvp<T>(c, c->md, m, s, blk(A, 0), ld, blk(A, 3), ld, k, gate, mk, st);
+  P_gram<T>(c, blk(A, 0), ld, k, blk(A, 0), ld, k, n3, Gb, c->part, c->counter, gate, mk, st);
+  P_gram<T>(c, blk(A, 0), ld, k, blk(A, 3), ld, k, n3, Mb, c->part, c->counter, gate, mk, st);
+  P_lob_rr(c, Gb, Mb, k, 1, drop, Cx, Cp, lam, c->st, st);
+  P_combine<T>(c, blk(A, 0), ld, k, nullptr, Cx, k, nullptr, 0, 0.0, 1.0, blk(B, 0), ld, nullptr, N, gate, mk, st);
+  P_combine<T>(c, blk(A, 3), ld, k, nullptr, Cx, k, nullptr, 0, 0.0, 1.0, blk(B, 3), ld, nullptr, N, gate, mk, st);
+  lob_swap_kernel<<<1, 32, 0, st>>>(c->st, mk);
+  int a = 1;
+  bool haveP = false;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  for (int it = 1; it <= max_iter; ++it) {
+    A = SET(a);
+    B = SET(1 - a);
+    // residuals R = AX - X theta, projected
+    P_diag(c, lam, k, 0, D + kC3, c->st, mk, st);
+    P_combine<T>(c, blk(A, 0), ld, k, nullptr, D + kC3, k, blk(A, 3), ld, 1.0, -1.0, blk(A, 1), ld, m, N, gate, mk,
+                      st);
+    P_gram<T>(c, blk(A, 1), ld, k, blk(A, 1), ld, k, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_lob_check(c, D + kG, k, tol, lam, c->st, st);
+    // W <- orthonormal basis of (I - X X^T) R
+    P_gram<T>(c, blk(A, 0), ld, k, blk(A, 1), ld, k, n3, D + kC, c->part, c->counter, gate, mk, st);
+    P_combine<T>(c, blk(A, 0), ld, k, nullptr, D + kC, k, blk(A, 1), ld, 1.0, -1.0, blk(A, 1), ld, nullptr, N, gate,
+                      mk, st);
+    P_gram<T>(c, blk(A, 1), ld, k, blk(A, 1), ld, k, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_cholqr(c, D + kG, k, 0, -2, D + kRinv, D + kRacc, D + kT, kLd, c->st, 0.0, st);
+    P_combine<T>(c, blk(A, 1), ld, k, nullptr, D + kRinv, k, nullptr, 0, 0.0, 1.0, Wt, ld, nullptr, N, gate, mk, st);
+    P_gram<T>(c, Wt, ld, k, Wt, ld, k, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_cholqr(c, D + kG, k, 1, -2, D + kRinv, D + kRacc, D + kT, kLd, c->st, 0.0, st);
+    P_combine<T>(c, Wt, ld, k, nullptr, D + kRinv, k, nullptr, 0, 0.0, 1.0, blk(A, 1), ld, nullptr, N, gate, mk, st);
+    P_hvp<T>(c, c->md, m, s, blk(A, 1), ld, blk(A, 4), ld, k, gate, mk, st);
+    if (haveP) {
+      P_gram<T>(c, blk(A, 2), ld, k, blk(A, 2), ld, k, n3, D + kG, c->part, c->counter, gate, mk, st);
+      P_diag(c, D + kG, k, 1, D + kC3, c->st, mk, st);
+      P_combine<T>(c, blk(A, 2), ld, k, nullptr, D + kC3, k, nullptr, 0, 0.0, 1.0, blk(A, 2), ld, nullptr, N, gate,
+                        mk, st);
+      P_combine<T>(c, blk(A, 5), ld, k, nullptr, D + kC3, k, nullptr, 0, 0.0, 1.0, blk(A, 5), ld, nullptr, N, gate,
+                        mk, st);
+    }
+    const int nb = haveP ? 3 : 2;
+    const int nS = nb * k;
+    for (int jb = 0; jb < nb; ++jb) {
+      P_gram<T>(c, A, ld, nS, blk(A, jb), ld, k, n3, Gb + (size_t)jb * nS * k, c->part, c->counter, gate, mk, st);
+      P_gram<T>(c, A, ld, nS, blk(A, 3 + jb), ld, k, n3, Mb + (size_t)jb * nS * k, c->part, c->counter, gate, mk,
+                     st);
+    }
+    P_lob_rr(c, Gb, Mb, k, nb, drop, Cx, Cp, lam, c->st, st);
+    P_combine<T>(c, A, ld, nS, nullptr, Cx, k, nullptr, 0, 0.0, 1.0, blk(B, 0), ld, nullptr, N, gate, mk, st);
+    P_combine<T>(c, blk(A, 3), ld, nS, nullptr, Cx, k, nullptr, 0, 0.0, 1.0, blk(B, 3), ld, nullptr, N, gate, mk,
+                      st);
+    P_combine<T>(c, A, ld, nS, nullptr, Cp, k, nullptr, 0, 0.0, 1.0, blk(B, 2), ld, nullptr, N, gate, mk, st);
+    P_combine<T>(c, blk(A, 3), ld, nS, nullptr, Cp, k, nullptr, 0, 0.0, 1.0, blk(B, 5), ld, nullptr, N, gate, mk,
+                      st);
+    lob_swap_kernel<<<1, 32, 0, st>>>(c->st, mk);
+    haveP = true;
+    a = 1 - a;
+    if (cap == cudaStreamCaptureStatusNone && it % 10 == 0) {
+      DevState h;
+      if (cudaMemcpyAsync(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+          cudaStreamSynchronize(st) == cudaSuccess && (h.gate & mk))
+        break;
+    }
+  }
+  copy_current_kernel<T><<<(unsigned)std::min<size_t>((n3 + 255) / 256, 4096), 256, 0, st>>>(
+      blk(SET(0), 0), blk(SET(1), 0), n3, c->st, V, ld, k, ldv);
+  P_finish<T>(c, m, V, ldv, k, N, c->part, c->counter, D + kScal, gate, kGateDone, st);
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+void moto_default_params(moto_params* p) {
+  if (!p) return;
+  p->k = 1;
+  p->solver = MOTO_SOLVER_LANCZOS;
+  p->block = 1;
+  p->krylov_steps = 60;
+  p->max_iter = 200;
+  p->tol = 1e-6;
+  p->lbfgs_mem = 5;
+  p->theta_max = 0.2;
+  p->gamma0 = 0.02;
+  p->tau_F = 1e-3;
+  p->eta_theta = 0.1;
+  p->max_steps = 300;
+  p->descent_max_steps = 5000;
+}
+
+const char* moto_status_string(int code) {
+  switch (code) {
+    case MOTO_OK: return "ok";
+    case MOTO_NOT_CONVERGED: return "not converged (iteration cap reached)";
+    case MOTO_ERR_ARG: return "invalid argument";
+    case MOTO_ERR_CUDA: return "CUDA runtime error";
+    case MOTO_ERR_NUMERIC: return "numerical breakdown (Krylov or small Gram matrix)";
+    case MOTO_ERR_NONFINITE: return "non-finite value met on the device";
+    case MOTO_ERR_TIMEOUT: return "bounded device wait timed out";
+    case MOTO_ERR_NOMEM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+int moto_create(const moto_model* model, int dtype, const moto_params* params, moto_ctx** out) {
+  if (!model || !out || !params) return MOTO_ERR_ARG;
+  *out = nullptr;
+  if (model->L1 < 5 || model->L2 < 5) return MOTO_ERR_ARG;
+  if (model->n_shells < 1 || model->n_shells > 3) return MOTO_ERR_ARG;
+  if (dtype != MOTO_F32 && dtype != MOTO_F64) return MOTO_ERR_ARG;
+  if ((long long)model->L1 * model->L2 > (1LL << 30)) return MOTO_ERR_ARG;
+  int rc = check_params(params);
+  if (rc) return rc;
+  moto_ctx* c = new moto_ctx();
+  memset(c, 0, sizeof(*c));
+  c->md.L1 = model->L1;
+  c->md.L2 = model->L2;
+  c->md.N = model->L1 * model->L2;
+  c->md.n_shells = model->n_shells;
+  for (int i = 0; i < 3; ++i) c->md.J[i] = i < model->n_shells ? model->J[i] : 0.0;
+  c->md.D = model->D;
+  c->md.K = model->K;
+  c->md.muB = model->muB;
+  c->dtype = dtype;
+  c->esize = dtype == MOTO_F64 ? 8 : 4;
+  c->p = *params;
+  c->N = c->md.N;
+  c->n3 = 3 * (size_t)c->N;
+  c->ld = (c->n3 + 63) / 64 * 64;
+  const size_t vb = c->ld * c->esize;
+  const int R = MOTO_MAX_MEM + 1;
+  size_t tb = (size_t)tile_blocks(c->md);
+  size_t part = std::max<size_t>(2 * tb, (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K);
+  part = std::max<size_t>(part, (size_t)kSMs * 8 * MOTO_MAX_K * 4);
+  part = std::max<size_t>(part, (size_t)kStreamBlocks * 9 * MOTO_MAX_K * MOTO_MAX_K * 2);
+  c->part_len = part;
+  struct A {
+    void** p;
+    size_t n;
+  } allocs[] = {
+      {&c->basis, vb * MOTO_MAX_BASIS},
+      {&c->W, vb * MOTO_MAX_K},
+      {&c->Wt, vb * MOTO_MAX_K},
+      {&c->g, vb},
+      {&c->s, c->ld * c->esize},
+      {&c->ring, vb * (2 * R + 5)},
+      {&c->lob, vb * 12 * MOTO_MAX_K},  // two sets of [X, W, P, AX, AW, AP]
+      {(void**)&c->dsm, kDsmSize * sizeof(double)},
+      {(void**)&c->part, part * sizeof(double)},
+      {(void**)&c->counter, 64 * sizeof(unsigned)},
+      {(void**)&c->st, sizeof(DevState)},
+  };
+  for (auto& a : allocs) {
+    if (cudaMalloc(a.p, a.n) != cudaSuccess) {
+      moto_destroy(c);
+      return MOTO_ERR_NOMEM;
+    }
+    c->bytes += a.n;
+    cudaMemset(*a.p, 0, a.n);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    moto_destroy(c);
+    return MOTO_ERR_CUDA;
+  }
+  *out = c;
+  return MOTO_OK;
+}
+
+void moto_destroy(moto_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  void* ptrs[] = {c->basis, c->W, c->Wt, c->g, c->s, c->ring, c->lob, c->dsm, c->part, c->counter, c->st};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+size_t moto_workspace_bytes(const moto_ctx* c) { return c ? c->bytes : 0; }
+
+int moto_status(moto_ctx* c, void* stream) {
+  if (!c) return MOTO_ERR_ARG;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  if (h.status & kStatusNonfinite) return MOTO_ERR_NONFINITE;
+  if (h.status & (kStatusBreakdown | kStatusNotSPD)) return MOTO_ERR_NUMERIC;
+  return MOTO_OK;
+}
+
+int moto_clear_status(moto_ctx* c, void* stream) {
+  if (!c) return MOTO_ERR_ARG;
+  state_kernel<<<1, 32, 0, S(stream)>>>(c->st, 2);
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_energy_grad(moto_ctx* c, const void* m, void* g, void* s, double* out, void* stream) {
+  if (!c || !m) return MOTO_ERR_ARG;
+  if (c->dtype == MOTO_F32)
+    P_energy_grad<float>(c, c->md, (const float*)m, (float*)g, (float*)s, c->part, c->counter, out,
+                              &c->st->status, false, S(stream));
+  else
+    P_energy_grad<double>(c, c->md, (const double*)m, (double*)g, (double*)s, c->part, c->counter, out,
+                               &c->st->status, false, S(stream));
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_energy(moto_ctx* c, const void* m, double* E, void* stream) {
+  if (!c || !m || !E) return MOTO_ERR_ARG;
+  double* tmp = c->dsm + kTmp;
+  if (c->dtype == MOTO_F32)
+    P_energy_grad<float>(c, c->md, (const float*)m, nullptr, nullptr, c->part, c->counter, tmp, &c->st->status,
+                              true, S(stream));
+  else
+    P_energy_grad<double>(c, c->md, (const double*)m, nullptr, nullptr, c->part, c->counter, tmp,
+                               &c->st->status, true, S(stream));
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(E, tmp, sizeof(double), cudaMemcpyDeviceToDevice, S(stream)));
+  return MOTO_OK;
+}
+
+int moto_hvp(moto_ctx* c, const void* m, const void* s, const void* v, size_t ldv, void* hv, size_t ldhv, int nvec,
+             void* stream) {
+  if (!c || !m || !s || !v || !hv || nvec < 1) return MOTO_ERR_ARG;
+  if ((nvec > 1) && (ldv < c->n3 || ldhv < c->n3)) return MOTO_ERR_ARG;
+  if (c->dtype == MOTO_F32)
+    P_hvp<float>(c, c->md, (const float*)m, (const float*)s, (const float*)v, ldv, (float*)hv, ldhv, nvec,
+                      nullptr, 0, S(stream));
+  else
+    P_hvp<double>(c, c->md, (const double*)m, (const double*)s, (const double*)v, ldv, (double*)hv, ldhv, nvec,
+                       nullptr, 0, S(stream));
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_topo_charge(moto_ctx* c, const void* m, double* Q, void* stream) {
+  if (!c || !m || !Q) return MOTO_ERR_ARG;
+  if (c->dtype == MOTO_F32)
+    launch_topo<float>(c->md, (const float*)m, c->part, c->counter, Q, S(stream));
+  else
+    launch_topo<double>(c->md, (const double*)m, c->part, c->counter, Q, S(stream));
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// inner layer, outer layer
+// ============================================================================
+namespace {
+
+__global__ void store_iters_kernel(const DevState* st, double* out) {
+  if (threadIdx.x == 0) out[0] = (double)st->pad[1];
+}
+
+template <typename T>
+void lowest_modes_impl(moto_ctx* c, const T* m, const T* s, const moto_params* p, const T* v0, size_t ld0, T* V,
+                       size_t ldv, int nout, double* lam, cudaStream_t st) {
+  if (p->solver == MOTO_SOLVER_LANCZOS) {
+    block_lanczos<T>(c, m, s, v0, ld0, p->block, p->krylov_steps, V, ldv, nout, lam, st);
+  } else {
+    lobpcg<T>(c, m, s, v0, ld0, p->k, p->max_iter, p->tol, V, ldv, lam, st);
+  }
+}
+
+// One outer step.  ascent: reflected force and min-mode solve; otherwise plain
+// descent on g.  update == false evaluates the stopping test only.
+template <typename T>
+void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* status, bool ascent, bool update,
+              cudaStream_t st) {
+  const int N = c->N;
+  const size_t ld = c->ld, n3 = c->n3;
+  T* g = static_cast<T*>(c->g);
+  T* s = static_cast<T*>(c->s);
+  const int R = p->lbfgs_mem + 1, nb = 2 * R + 1;
+  T* ring = static_cast<T*>(c->ring);
+  T* Gcur = ring + (size_t)(2 * R) * ld;
+  T* Gprev = Gcur + ld;
+  T* d = Gprev + ld;
+  T* stage = d + ld;
+  double* D = c->dsm;
+  int* gate = &c->st->gate;
+  const int md = kGateDone;
+  P_energy_grad<T>(c, c->md, m, g, s, c->part, c->counter, D + kEG, &c->st->status, false, st);
+  double* lam = D + kTheta;
+  if (ascent) {
+    const int nv = std::max(p->k, p->solver == MOTO_SOLVER_LANCZOS ? p->block : p->k);
+    lowest_modes_impl<T>(c, m, s, p, V, n3, V, n3, nv, lam, st);
+    P_gram<T>(c, g, ld, 1, V, n3, 1, n3, &c->st->dot, c->part, c->counter, gate, md, st);
+    P_mmf_force<T>(c, g, V, &c->st->dot, 1.0, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
+  } else {
+    P_mmf_force<T>(c, g, nullptr, &c->st->dot, 0.0, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
+  }
+  P_saddle_test(c, D + kEG, D + kFmax, lam, p->tau_F, out6, status, c->st, ascent ? 1 : 0, st);
+  if (!update) return;
+  P_lbfgs_pair<T>(c, m, d, Gprev, Gcur, ring, ld, stage, c->st, N, gate, md, st);
+  P_gram<T>(c, ring, ld, nb, stage, ld, 2, n3, D + kLbNew, c->part, c->counter, gate, md, st);
+  P_gram<T>(c, ring, ld, nb, Gcur, ld, 1, n3, D + kLbNew + 2 * nb, c->part, c->counter, gate, md, st);
+  P_lbfgs_solve(c, D + kLbM, p->lbfgs_mem, D + kLbNew, p->gamma0, D + kLbCoef, c->st, st);
+  P_lbfgs_direction<T>(c, ring, ld, nb, D + kLbCoef, m, d, N, p->theta_max, c->part, c->counter, c->st, gate, md,
+                            st);
+  P_retract<T>(c, m, d, c->st, N, gate, md, st);
+  cudaMemcpyAsync(Gprev, Gcur, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+}
+
+int read_state(moto_ctx* c, DevState* h, cudaStream_t st) {
+  if (cudaMemcpyAsync(h, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MOTO_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return MOTO_ERR_CUDA;
+  return MOTO_OK;
+}
+
+int status_code(const DevState& h) {
+  if (h.status & kStatusNonfinite) return MOTO_ERR_NONFINITE;
+  if (h.status & (kStatusBreakdown | kStatusNotSPD)) return MOTO_ERR_NUMERIC;
+  return MOTO_OK;
+}
+
+template <typename T>
+int run_opt(moto_ctx* c, T* m, const moto_params* p, T* V, double* trace, int check_every, int max_steps,
+            bool ascent, int* steps_out, cudaStream_t st) {
+  if (check_every < 1) check_every = 1;
+  state_kernel<<<1, 32, 0, st>>>(c->st, 1);
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  for (int t = 0; t <= max_steps; ++t) {
+    double* o = trace ? trace + 6 * (size_t)t : c->dsm + kTmp;
+    opt_step<T>(c, m, p, V, o, nullptr, ascent, t < max_steps, st);
+    if (cudaGetLastError() != cudaSuccess) return MOTO_ERR_CUDA;
+    if ((t + 1) % check_every == 0 || t == max_steps) {
+      int rc = read_state(c, &h, st);
+      if (rc) return rc;
+      if (h.converged || status_code(h)) break;
+    }
+  }
+  if (steps_out) *steps_out = h.pad[1];
+  int sc = status_code(h);
+  if (sc) return sc;
+  return h.converged ? MOTO_OK : MOTO_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+int moto_lowest_modes(moto_ctx* c, const void* m, const void* s, const moto_params* p, const void* v0, void* V,
+                      double* lam, int* info, void* stream) {
+  if (!c || !m || !p || !v0 || !V || !lam) return MOTO_ERR_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  cudaStream_t st = S(stream);
+  if (c->dtype == MOTO_F32) {
+    const float* sp = (const float*)s;
+    if (!sp) {
+      P_energy_grad<float>(c, c->md, (const float*)m, (float*)c->g, (float*)c->s, c->part, c->counter,
+                                c->dsm + kEG, &c->st->status, false, st);
+      sp = (const float*)c->s;
+    }
+    lowest_modes_impl<float>(c, (const float*)m, sp, p, (const float*)v0, c->n3, (float*)V, c->n3, p->k, lam, st);
+  } else {
+    const double* sp = (const double*)s;
+    if (!sp) {
+      P_energy_grad<double>(c, c->md, (const double*)m, (double*)c->g, (double*)c->s, c->part, c->counter,
+                                 c->dsm + kEG, &c->st->status, false, st);
+      sp = (const double*)c->s;
+    }
+    lowest_modes_impl<double>(c, (const double*)m, sp, p, (const double*)v0, c->n3, (double*)V, c->n3, p->k, lam,
+                              st);
+  }
+  if (info) info_kernel<<<1, 32, 0, st>>>(c->st, info);
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_lbfgs_reset(moto_ctx* c, void* stream) {
+  if (!c) return MOTO_ERR_ARG;
+  state_kernel<<<1, 32, 0, S(stream)>>>(c->st, 1);
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_mmf_step(moto_ctx* c, void* m, const moto_params* p, void* V, double* out, int* status, void* stream) {
+  if (!c || !m || !p || !V) return MOTO_ERR_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->lbfgs_mem != c->p.lbfgs_mem) return MOTO_ERR_ARG;
+  if (c->dtype == MOTO_F32)
+    opt_step<float>(c, (float*)m, p, (float*)V, out, status, true, true, S(stream));
+  else
+    opt_step<double>(c, (double*)m, p, (double*)V, out, status, true, true, S(stream));
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_ascend(moto_ctx* c, void* m, const moto_params* p, void* V, double* trace, int check_every,
+                int* steps_out, void* stream) {
+  if (!c || !m || !p || !V) return MOTO_ERR_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->lbfgs_mem != c->p.lbfgs_mem) return MOTO_ERR_ARG;
+  if (c->dtype == MOTO_F32)
+    return run_opt<float>(c, (float*)m, p, (float*)V, trace, check_every, p->max_steps, true, steps_out, S(stream));
+  return run_opt<double>(c, (double*)m, p, (double*)V, trace, check_every, p->max_steps, true, steps_out, S(stream));
+}
+
+int moto_descend(moto_ctx* c, const void* m_saddle, const void* v1, const moto_params* p, void* m_plus,
+                 void* m_minus, double* out, void* stream) {
+  if (!c || !m_saddle || !v1 || !p || !m_plus || !m_minus || !out) return MOTO_ERR_ARG;
+  int rc = check_params(p);
+  if (rc) return rc;
+  if (p->lbfgs_mem != c->p.lbfgs_mem) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  int result = MOTO_OK;
+  for (int side = 0; side < 2; ++side) {
+    void* mo = side == 0 ? m_plus : m_minus;
+    const double sign = side == 0 ? 1.0 : -1.0;
+    int steps = 0;
+    if (c->dtype == MOTO_F32) {
+      launch_descent_seed<float>((const float*)m_saddle, (const float*)v1, p->eta_theta, sign, (float*)mo, c->N,
+                                 c->part, c->counter, c->dsm + kTmp, st);
+      rc = run_opt<float>(c, (float*)mo, p, nullptr, nullptr, 25, p->descent_max_steps, false, &steps, st);
+    } else {
+      launch_descent_seed<double>((const double*)m_saddle, (const double*)v1, p->eta_theta, sign, (double*)mo,
+                                  c->N, c->part, c->counter, c->dsm + kTmp, st);
+      rc = run_opt<double>(c, (double*)mo, p, nullptr, nullptr, 25, p->descent_max_steps, false, &steps, st);
+    }
+    if (rc < 0) return rc;
+    if (rc == MOTO_NOT_CONVERGED) result = MOTO_NOT_CONVERGED;
+    int e = moto_energy(c, mo, out + 2 * side, stream);
+    if (e) return e;
+    e = moto_topo_charge(c, mo, out + 2 * side + 1, stream);
+    if (e) return e;
+    store_iters_kernel<<<1, 32, 0, st>>>(c->st, out + 4 + side);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return result;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// launch profiler
+// ============================================================================
+extern "C" {
+
+int moto_profile_begin(moto_ctx* c, int capacity) {
+  if (!c || capacity < 1) return MOTO_ERR_ARG;
+  if (c->prof_ev) return MOTO_ERR_ARG;
+  c->prof_ev = new cudaEvent_t[2 * (size_t)capacity];
+  c->prof_kind = new int[capacity];
+  c->prof_bytes = new double[capacity];
+  for (int i = 0; i < 2 * capacity; ++i) {
+    if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) {
+      for (int j = 0; j < i; ++j) cudaEventDestroy(c->prof_ev[j]);
+      delete[] c->prof_ev;
+      delete[] c->prof_kind;
+      delete[] c->prof_bytes;
+      c->prof_ev = nullptr;
+      return MOTO_ERR_CUDA;
+    }
+  }
+  c->prof_cap = capacity;
+  c->prof_n = 0;
+  c->prof_on = 1;
+  return MOTO_OK;
+}
+
+int moto_profile_end(moto_ctx* c, int nkinds, int* launches, double* ms, double* bytes) {
+  if (!c || !c->prof_ev) return MOTO_ERR_ARG;
+  c->prof_on = 0;
+  int rc = MOTO_OK;
+  if (c->prof_n > 0 && cudaEventSynchronize(c->prof_ev[2 * c->prof_n - 1]) != cudaSuccess) rc = MOTO_ERR_CUDA;
+  for (int k = 0; k < nkinds; ++k) {
+    if (launches) launches[k] = 0;
+    if (ms) ms[k] = 0.0;
+    if (bytes) bytes[k] = 0.0;
+  }
+  for (int i = 0; rc == MOTO_OK && i < c->prof_n; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) != cudaSuccess) {
+      rc = MOTO_ERR_CUDA;
+      break;
+    }
+    const int k = c->prof_kind[i];
+    if (k < nkinds) {
+      if (launches) launches[k] += 1;
+      if (ms) ms[k] += t;
+      if (bytes) bytes[k] += c->prof_bytes[i];
+    }
+  }
+  for (int i = 0; i < 2 * c->prof_cap; ++i) cudaEventDestroy(c->prof_ev[i]);
+  delete[] c->prof_ev;
+  delete[] c->prof_kind;
+  delete[] c->prof_bytes;
+  c->prof_ev = nullptr;
+  c->prof_cap = c->prof_n = 0;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Shared device-side building blocks: model constants, periodic indexing,
+// warp/block reductions and the deterministic grid reduction used by every
+// kernel that produces a scalar.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "moto.h"
+
+namespace moto {
+
+constexpr int kThreads = 256;         // block size of the streaming kernels
+constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
+constexpr int kStreamBlocks = 2 * kSMs;  // persistent-style grid of the vector kernels
+
+// Device copy of the model.  Shell offsets are compile-time constants in
+// stencil.cuh; only strengths and sizes travel here.
+struct ModelDev {
+  int L1, L2, N, n_shells;
+  double J[3];
+  double D, K, muB;
+};
+
+// Status bits written by kernels into the context's status word.
+enum : int {
+  kStatusNonfinite = 1,
+  kStatusBreakdown = 2,
+  kStatusNotSPD = 4,
+};
+
+__device__ __forceinline__ int wrap(int a, int L) {
+  a %= L;
+  return a < 0 ? a + L : a;
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum of NV values over the block in a fixed order; result valid in thread 0.
+// scratch: at least NV * (blockDim/32) doubles of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) scratch[j * nw + wid] = v[j];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double a = 0.0;
+      for (int w = 0; w < nw; ++w) a += scratch[j * nw + w];
+      v[j] = a;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double block_max(double v, double* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = scratch[0];
+    for (int w = 1; w < nw; ++w) a = fmax(a, scratch[w]);
+    v = a;
+  }
+  __syncthreads();
+  return v;
+}
+
+// Deterministic grid reduction.  Every block has written `nv` partial values at
+// part[blockIdx.x * nv + j] (thread 0, before calling).  The last block to
+// arrive reduces them in block-index order (sum, or max where is_max[j]) and
+// returns true in all of its threads with the totals in `tot` (shared memory,
+// nv doubles); it also resets the arrival counter for the next launch.
+__device__ __forceinline__ bool grid_last_block(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Inside the last block: tot[j] = sum_b part[b * nv + j] in b order (the
+// sequential order per entry makes the result independent of which block came
+// last).  Threads split the entries.
+__device__ __forceinline__ void grid_sum_entries(const double* part, int nblocks, int nv, double* tot) {
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double a = 0.0;
+    for (int b = 0; b < nblocks; ++b) a += __ldcg(part + (size_t)b * nv + j);
+    tot[j] = a;
+  }
+}
+
+__device__ __forceinline__ void grid_max_entries(const double* part, int nblocks, int nv, double* tot) {
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double a = -1.0 / 0.0;
+    for (int b = 0; b < nblocks; ++b) a = fmax(a, __ldcg(part + (size_t)b * nv + j));
+    tot[j] = a;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool finite3(T a, T b, T c) {
+  return isfinite((double)a) && isfinite((double)b) && isfinite((double)c);
+}
+
+}  // namespace moto

@@ -1,0 +1,120 @@
+// Internal launchers shared by the C-ABI implementation and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace moto {
+
+// ---- gate bits: kernels given (gate, mask) return at once if (*gate & mask) ----
+enum : int {
+  kGateKrylov = 1,  // the Krylov recurrence broke down; skip its remaining steps
+  kGateDone = 2,    // the ascent / descent has converged; skip the rest
+};
+
+// Device-side bookkeeping of one eigensolve / optimisation, in device memory.
+struct DevState {
+  int gate;        // kGate* bits
+  int status;      // kStatus* bits (sticky until cleared)
+  int steps;       // Krylov blocks in the basis (block Lanczos)
+  int nT;          // order of the projected matrix
+  int iters;       // iterations (LOBPCG) or steps done
+  int lb_head;     // L-BFGS ring: next slot
+  int lb_count;    // L-BFGS ring: pairs held
+  int lb_have_prev;
+  int converged;   // 1 once the stopping test passed
+  int pad[7];      // pad[0]: current LOBPCG set; pad[1]: outer steps taken
+  double tnorm;    // running estimate of |T| (largest row sum seen)
+  double hnorm;    // LOBPCG: largest |theta| seen
+  double scale;    // step scale of the current direction
+  double dot;      // g . v1 of the current step
+};
+
+int tile_blocks(const ModelDev& md);
+
+template <typename T>
+void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
+                        int* status, bool fp64_arith, cudaStream_t st);
+template <typename T>
+void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec,
+                const int* gate, int mask, cudaStream_t st);
+template <typename T>
+void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st);
+
+// out[r*ny + c] = sum_e X_r[e] Y_c[e] over n elements, r < nx <= 96, c < ny <= 8.
+// FP32 products summed in FP32 over at most 16 x (tile share) elements, then
+// promoted to FP64 for every cross-thread and cross-block sum (T = float);
+// all-FP64 for T = double.
+template <typename T>
+void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+                 double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st);
+int gram_blocks();
+
+// Site-wise combination of vector fields (3N elements, component-major):
+//   out_c = beta * Y_c + sigma * sum_{r < nx} X_r C[r*ny + c]      (c < ny <= 8)
+// nx is read from *nx_dev when nx_dev != NULL (then nx_max bounds it).
+// If m != NULL the result is projected on the tangent planes of m.
+// Y may alias out (in-place), X must not.
+template <typename T>
+void launch_combine(const T* X, size_t ldx, int nx, const int* nx_dev, const double* C, int ny, const T* Y,
+                    size_t ldy, double beta, double sigma, T* out, size_t ldo, const T* m, int N, const int* gate,
+                    int mask, cudaStream_t st);
+
+// out_j = P(in_j) for nvec fields (in may alias out).
+template <typename T>
+void launch_project(const T* m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N, const int* gate,
+                    int mask, cudaStream_t st);
+
+// Ritz finishing: V_c <- P(V_c) / |P(V_c)| * sign, sign making the entry of
+// largest magnitude positive (lowest flat index on ties).  Two launches.
+template <typename T>
+void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, unsigned* counter, double* scal,
+                   const int* gate, int mask, cudaStream_t st);
+
+// ---- small dense FP64 steps, one block each ----
+// Block Lanczos, after A = Q_j^T H Q_j: symmetrise into T(j,j), build the
+// three-term coefficients [R_j^T ; A] (rows for Q_{j-1}, Q_j) into C3.
+void launch_lanczos_coeffs(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st,
+                           cudaStream_t s);
+// Cholesky QR step on G (b x b): writes Rinv (b x b, coefficient matrix) and
+// accumulates R.  second != 0: final pass of CholQR2; then R is placed at
+// T(j+1, j) / T(j, j+1) (when j >= 0) and st->steps advanced.  Breakdown sets
+// kGateKrylov.
+void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T, int ldT,
+                   DevState* st, double rel_tol, cudaStream_t s);
+// Symmetric eigensolver (cyclic Jacobi, FP64) on the leading nT x nT block of
+// T (nT read from st->nT, <= 96): theta ascending (MOTO_MAX_BASIS entries,
+// +inf padded) and the first k eigenvectors as an (nT x k) coefficient matrix Y.
+void launch_small_eig(const double* T, int ldT, double* theta, double* Y, int k, DevState* st, cudaStream_t s);
+
+// LOBPCG small steps (see kernels_vec.cu)
+void launch_lob_rr(const double* Gb, const double* Mb, int k, int nb, double drop, double* Cx, double* Cp,
+                   double* theta, DevState* st, cudaStream_t s);
+void launch_lob_check(const double* Gw, int k, double tol, const double* theta, DevState* st, cudaStream_t s);
+// mode 0: out = diag(src[0..k));  mode 1: out = diag(1 / sqrt(src[j*k + j]))
+void launch_diag(const double* src, int k, int mode, double* out, const DevState* st, int mask, cudaStream_t s);
+
+// ---- L-BFGS / MMF ----
+template <typename T>
+void launch_mmf_force(const T* g, const T* v1, const double* dot, double reflect, T* G, int N, double* part,
+                      unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st);
+template <typename T>
+void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
+                       const DevState* dst, int N, const int* gate, int mask, cudaStream_t st);
+void launch_lbfgs_solve(double* M, int mem, const double* newdots, double gamma0, double* coef, DevState* dst,
+                        cudaStream_t st);
+template <typename T>
+void launch_lbfgs_direction(const T* basis, size_t ld, int nb, const double* coef, const T* m, T* d, int N,
+                            double theta_max, double* part, unsigned* counter, DevState* dst, const int* gate,
+                            int mask, cudaStream_t st);
+template <typename T>
+void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int mask, cudaStream_t st);
+template <typename T>
+void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign, T* out, int N, double* part,
+                         unsigned* counter, double* scal, cudaStream_t st);
+void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, double tau_F, double* out6,
+                        int* status_out, DevState* dst, int ascent, cudaStream_t st);
+
+}  // namespace moto

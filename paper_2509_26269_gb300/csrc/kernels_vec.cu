@@ -1,0 +1,1171 @@
+// Vector-field kernels of the Krylov solvers and the L-BFGS ascent/descent:
+// skinny Gram products (FP64-accumulated), site-wise combinations with
+// tangent projection, Ritz finishing, and the small dense FP64 steps
+// (Cholesky QR factors, Jacobi eigensolver, L-BFGS two-loop in coefficient
+// space) that run in a single block.
+#include <float.h>
+
+#include "internal.h"
+
+namespace moto {
+
+// ===========================================================================
+// Gram:  out[r][c] = X_r . Y_c
+// ===========================================================================
+constexpr int kGramKT = 64;  // elements per shared-memory tile
+
+int gram_blocks() { return kStreamBlocks; }
+
+template <typename T, int NY>
+__global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ X, size_t ldx, int nx,
+                                                        const T* __restrict__ Y, size_t ldy, int ny, size_t n,
+                                                        double* out, double* part, unsigned* counter,
+                                                        const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int npairs = (nx + 1) >> 1;
+  const int nxp = 2 * npairs + 2;  // padded row of the transposed X tile
+  T* Xs = reinterpret_cast<T*>(smem_raw);
+  T* Ys = Xs + kGramKT * nxp;
+  const int nkg = blockDim.x / npairs;
+  const int q = threadIdx.x % npairs, kg = threadIdx.x / npairs;
+  const bool worker = kg < nkg;
+
+  double acc64[2][NY];
+  T mid[2][NY];
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int c = 0; c < NY; ++c) {
+      acc64[j][c] = 0.0;
+      mid[j][c] = (T)0;
+    }
+  const size_t ntiles = (n + kGramKT - 1) / kGramKT;
+  int since_flush = 0;
+  for (size_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const size_t e0 = t * kGramKT;
+    const int len = (int)min((size_t)kGramKT, n - e0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nx * kGramKT; idx += blockDim.x) {
+      const int r = idx / kGramKT, k = idx - r * kGramKT;
+      Xs[k * nxp + r] = k < len ? X[(size_t)r * ldx + e0 + k] : (T)0;
+    }
+    for (int idx = threadIdx.x; idx < kGramKT * nxp; idx += blockDim.x) {
+      // zero the padding columns (r >= nx) once per tile
+      const int k = idx / nxp, r = idx - k * nxp;
+      if (r >= nx) Xs[idx] = (T)0;
+      (void)k;
+    }
+    for (int idx = threadIdx.x; idx < NY * kGramKT; idx += blockDim.x) {
+      const int c = idx / kGramKT, k = idx - c * kGramKT;
+      Ys[k * NY + c] = (c < ny && k < len) ? Y[(size_t)c * ldy + e0 + k] : (T)0;
+    }
+    __syncthreads();
+    if (worker) {
+      T tacc[2][NY];
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int c = 0; c < NY; ++c) tacc[j][c] = (T)0;
+      for (int k = kg; k < kGramKT; k += nkg) {
+        const T x0 = Xs[k * nxp + 2 * q], x1 = Xs[k * nxp + 2 * q + 1];
+#pragma unroll
+        for (int c = 0; c < NY; ++c) {
+          const T y = Ys[k * NY + c];
+          tacc[0][c] += x0 * y;
+          tacc[1][c] += x1 * y;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int c = 0; c < NY; ++c) mid[j][c] += tacc[j][c];
+      if (++since_flush == 16) {
+        since_flush = 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+          for (int c = 0; c < NY; ++c) {
+            acc64[j][c] += (double)mid[j][c];
+            mid[j][c] = (T)0;
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+#pragma unroll
+    for (int c = 0; c < NY; ++c) acc64[j][c] += (double)mid[j][c];
+  // block reduction over k-groups, fixed order
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem_raw);  // nkg * npairs * 2 * NY doubles
+  if (worker) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int c = 0; c < NY; ++c) red[((size_t)kg * npairs + q) * 2 * NY + j * NY + c] = acc64[j][c];
+  }
+  __syncthreads();
+  const int nout = nx * ny;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int r = o / ny, c = o - r * ny;
+    const int qq = r >> 1, jj = r & 1;
+    double a = 0.0;
+    for (int g = 0; g < nkg; ++g) a += red[((size_t)g * npairs + qq) * 2 * NY + jj * NY + c];
+    part[(size_t)blockIdx.x * nout + o] = a;
+  }
+  if (!grid_last_block(counter)) return;
+  grid_sum_entries(part, gridDim.x, nout, out);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <typename T, int NY>
+static void gram_launch_ny(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+                           double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st) {
+  const int npairs = (nx + 1) / 2;
+  const int nxp = 2 * npairs + 2;
+  const int nkg = kThreads / npairs;
+  size_t tile = (size_t)kGramKT * (nxp + NY) * sizeof(T);
+  size_t red = (size_t)nkg * npairs * 2 * NY * sizeof(double);
+  size_t smem = tile > red ? tile : red;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(gram_kernel<T, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const size_t ntiles = (n + kGramKT - 1) / kGramKT;
+  const int grid = (int)(ntiles < (size_t)kStreamBlocks ? ntiles : (size_t)kStreamBlocks);
+  gram_kernel<T, NY><<<grid, kThreads, smem, st>>>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask);
+}
+
+template <typename T>
+void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+                 double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st) {
+  if (ny <= 1)
+    gram_launch_ny<T, 1>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
+  else if (ny <= 2)
+    gram_launch_ny<T, 2>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
+  else if (ny <= 4)
+    gram_launch_ny<T, 4>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
+  else
+    gram_launch_ny<T, 8>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
+}
+
+// ===========================================================================
+// Combination:  out_c = beta Y_c + sigma sum_r X_r C[r][c]   (site-wise)
+// ===========================================================================
+template <typename T, int NY>
+__global__ void __launch_bounds__(kThreads) combine_kernel(const T* __restrict__ X, size_t ldx, int nx,
+                                                           const int* nx_dev, const double* __restrict__ C, int ny,
+                                                           const T* Y, size_t ldy, T beta, T sigma, T* out,
+                                                           size_t ldo, const T* __restrict__ m, int N,
+                                                           const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  if (nx_dev) nx = min(*nx_dev, nx);
+  __shared__ T Cs[MOTO_MAX_BASIS * NY];
+  for (int idx = threadIdx.x; idx < nx * NY; idx += blockDim.x) {
+    const int r = idx / NY, c = idx - r * NY;
+    Cs[idx] = c < ny ? (T)((double)sigma * C[r * ny + c]) : (T)0;
+  }
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T acc[NY][3];
+#pragma unroll
+    for (int c = 0; c < NY; ++c) {
+      if (c < ny && beta != (T)0) {
+        acc[c][0] = beta * Y[(size_t)c * ldy + i];
+        acc[c][1] = beta * Y[(size_t)c * ldy + N + i];
+        acc[c][2] = beta * Y[(size_t)c * ldy + 2 * (size_t)N + i];
+      } else {
+        acc[c][0] = acc[c][1] = acc[c][2] = (T)0;
+      }
+    }
+    for (int r = 0; r < nx; ++r) {
+      const T* xr = X + (size_t)r * ldx;
+      const T x0 = __ldg(xr + i), x1 = __ldg(xr + N + i), x2 = __ldg(xr + 2 * (size_t)N + i);
+#pragma unroll
+      for (int c = 0; c < NY; ++c) {
+        const T w = Cs[r * NY + c];
+        acc[c][0] += x0 * w;
+        acc[c][1] += x1 * w;
+        acc[c][2] += x2 * w;
+      }
+    }
+    T m0 = 0, m1 = 0, m2 = 0;
+    if (m) {
+      m0 = __ldg(m + i);
+      m1 = __ldg(m + N + i);
+      m2 = __ldg(m + 2 * (size_t)N + i);
+    }
+#pragma unroll
+    for (int c = 0; c < NY; ++c) {
+      if (c >= ny) continue;
+      T a0 = acc[c][0], a1 = acc[c][1], a2 = acc[c][2];
+      if (m) {
+        const T p = m0 * a0 + m1 * a1 + m2 * a2;
+        a0 -= p * m0;
+        a1 -= p * m1;
+        a2 -= p * m2;
+      }
+      out[(size_t)c * ldo + i] = a0;
+      out[(size_t)c * ldo + N + i] = a1;
+      out[(size_t)c * ldo + 2 * (size_t)N + i] = a2;
+    }
+  }
+}
+
+static int stream_grid(size_t sites) {
+  size_t b = (sites + kThreads - 1) / kThreads;
+  const size_t cap = (size_t)kSMs * 8;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <typename T>
+void launch_combine(const T* X, size_t ldx, int nx, const int* nx_dev, const double* C, int ny, const T* Y,
+                    size_t ldy, double beta, double sigma, T* out, size_t ldo, const T* m, int N, const int* gate,
+                    int mask, cudaStream_t st) {
+  const int g = stream_grid(N);
+  if (ny <= 1)
+    combine_kernel<T, 1><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask);
+  else if (ny <= 2)
+    combine_kernel<T, 2><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask);
+  else if (ny <= 4)
+    combine_kernel<T, 4><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask);
+  else
+    combine_kernel<T, 8><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask);
+}
+
+// ===========================================================================
+// projection and Ritz finishing
+// ===========================================================================
+template <typename T>
+__global__ void project_kernel(const T* __restrict__ m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N,
+                               const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    for (int j = 0; j < nvec; ++j) {
+      const T* a = in + (size_t)j * ldi;
+      T* b = out + (size_t)j * ldo;
+      const T a0 = a[i], a1 = a[N + i], a2 = a[2 * (size_t)N + i];
+      const T p = m0 * a0 + m1 * a1 + m2 * a2;
+      b[i] = a0 - p * m0;
+      b[N + i] = a1 - p * m1;
+      b[2 * (size_t)N + i] = a2 - p * m2;
+    }
+  }
+}
+
+template <typename T>
+void launch_project(const T* m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N, const int* gate,
+                    int mask, cudaStream_t st) {
+  project_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, in, ldi, out, ldo, nvec, N, gate, mask);
+}
+
+// argmax with ties to the lowest index: (abs, idx) pairs
+__device__ __forceinline__ void amax_merge(double& a, double& ai, double& av, double b, double bi, double bv) {
+  if (b > a || (b == a && bi < ai)) {
+    a = b;
+    ai = bi;
+    av = bv;
+  }
+}
+
+// pass 1: V_c <- P(V_c); partials per block and vector: |V_c|^2, max |entry|,
+// its flat index, its signed value.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__ m, T* V, size_t ldv, int k, int N,
+                                                           double* part, unsigned* counter, double* scal,
+                                                           const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  double nrm[MOTO_MAX_K], amx[MOTO_MAX_K], aidx[MOTO_MAX_K], aval[MOTO_MAX_K];
+  for (int c = 0; c < k; ++c) {
+    nrm[c] = 0.0;
+    amx[c] = -1.0;
+    aidx[c] = 1e300;
+    aval[c] = 0.0;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    for (int c = 0; c < k; ++c) {
+      T* v = V + (size_t)c * ldv;
+      T a0 = v[i], a1 = v[N + i], a2 = v[2 * (size_t)N + i];
+      const T p = m0 * a0 + m1 * a1 + m2 * a2;
+      a0 -= p * m0;
+      a1 -= p * m1;
+      a2 -= p * m2;
+      v[i] = a0;
+      v[N + i] = a1;
+      v[2 * (size_t)N + i] = a2;
+      nrm[c] += (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2;
+      amax_merge(amx[c], aidx[c], aval[c], fabs((double)a0), (double)i, (double)a0);
+      amax_merge(amx[c], aidx[c], aval[c], fabs((double)a1), (double)N + i, (double)a1);
+      amax_merge(amx[c], aidx[c], aval[c], fabs((double)a2), 2.0 * N + i, (double)a2);
+    }
+  }
+  __shared__ double sh[kThreads / 32][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = 0; c < k; ++c) {
+    double s = warp_sum(nrm[c]);
+    double a = amx[c], ai = aidx[c], av = aval[c];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b = __shfl_xor_sync(0xffffffffu, a, o);
+      const double bi = __shfl_xor_sync(0xffffffffu, ai, o);
+      const double bv = __shfl_xor_sync(0xffffffffu, av, o);
+      amax_merge(a, ai, av, b, bi, bv);
+    }
+    if (lane == 0) {
+      sh[wid][0] = s;
+      sh[wid][1] = a;
+      sh[wid][2] = ai;
+      sh[wid][3] = av;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double S = 0.0, A = -1.0, AI = 1e300, AV = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        S += sh[w][0];
+        amax_merge(A, AI, AV, sh[w][1], sh[w][2], sh[w][3]);
+      }
+      double* p = part + ((size_t)blockIdx.x * MOTO_MAX_K + c) * 4;
+      p[0] = S;
+      p[1] = A;
+      p[2] = AI;
+      p[3] = AV;
+    }
+    __syncthreads();
+  }
+  if (!grid_last_block(counter)) return;
+  if (threadIdx.x < k) {
+    const int c = threadIdx.x;
+    double S = 0.0, A = -1.0, AI = 1e300, AV = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const double* p = part + ((size_t)b * MOTO_MAX_K + c) * 4;
+      S += __ldcg(p);
+      amax_merge(A, AI, AV, __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3));
+    }
+    const double nrm_ = sqrt(S);
+    scal[c] = (nrm_ > 0.0 ? 1.0 / nrm_ : 0.0) * (AV < 0.0 ? -1.0 : 1.0);
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <typename T>
+__global__ void scale_kernel(T* V, size_t ldv, int k, size_t n, const double* scal, const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    for (int c = 0; c < k; ++c) V[(size_t)c * ldv + e] *= (T)scal[c];
+}
+
+template <typename T>
+void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, unsigned* counter, double* scal,
+                   const int* gate, int mask, cudaStream_t st) {
+  const int g = stream_grid(N);
+  finish1_kernel<T><<<g, kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask);
+  scale_kernel<T><<<stream_grid(3 * (size_t)N), kThreads, 0, st>>>(V, ldv, k, 3 * (size_t)N, scal, gate, mask);
+}
+
+// ===========================================================================
+// small dense FP64 steps (one block)
+// ===========================================================================
+__global__ void lanczos_coeffs_kernel(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st) {
+  if (st->gate & (kGateKrylov | kGateDone)) return;
+  if (threadIdx.x != 0) return;
+  // T(j, j) = sym(A)
+  for (int r = 0; r < b; ++r)
+    for (int c = 0; c < b; ++c) T[(size_t)(j * b + r) * ldT + j * b + c] = 0.5 * (A[r * b + c] + A[c * b + r]);
+  // C3 rows: [R_j^T (for Q_{j-1}); A (for Q_j)],   R_j = T(j, j-1)
+  int row = 0;
+  if (j > 0) {
+    for (int r = 0; r < b; ++r, ++row)
+      for (int c = 0; c < b; ++c) C3[row * b + c] = T[(size_t)(j * b + c) * ldT + (j - 1) * b + r];
+  }
+  for (int r = 0; r < b; ++r, ++row)
+    for (int c = 0; c < b; ++c) C3[row * b + c] = T[(size_t)(j * b + r) * ldT + j * b + c];
+}
+
+void launch_lanczos_coeffs(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st,
+                           cudaStream_t s) {
+  lanczos_coeffs_kernel<<<1, 32, 0, s>>>(A, b, j, T, ldT, C3, st);
+}
+
+// Cholesky QR factor of the b x b Gram G.  Pass 1 (second == 0) also updates
+// the |T| estimate with block row j (sum of |A| and |R_j| row entries plus the
+// largest new diagonal) and tests for breakdown (smallest diagonal of the
+// factor <= rel_tol * |T|).  Pass 2 composes R and stores it in T.
+__global__ void cholqr_kernel(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T,
+                              int ldT, DevState* st, double rel_tol) {
+  if (st->gate & (kGateKrylov | kGateDone)) return;
+  // j >= 0: block Lanczos step j; j == -1: start block; j == -2: LOBPCG block
+  if (threadIdx.x != 0) return;
+  double L[MOTO_MAX_K][MOTO_MAX_K];
+  bool ok = true;
+  for (int r = 0; r < b; ++r) {
+    for (int c = 0; c <= r; ++c) {
+      double a = 0.5 * (G[r * b + c] + G[c * b + r]);
+      for (int t = 0; t < c; ++t) a -= L[r][t] * L[c][t];
+      if (r == c) {
+        if (!(a > 0.0)) {
+          ok = false;
+          a = 1.0;
+        }
+        L[r][r] = sqrt(a);
+      } else {
+        L[r][c] = a / L[c][c];
+      }
+    }
+    for (int c = r + 1; c < b; ++c) L[r][c] = 0.0;
+  }
+  double dmin = 1e300, dmax = 0.0;
+  for (int r = 0; r < b; ++r) {
+    dmin = fmin(dmin, L[r][r]);
+    dmax = fmax(dmax, L[r][r]);
+  }
+  if (!second && j >= 0) {
+    double rs = 0.0;
+    for (int r = 0; r < b; ++r) {
+      double a = 0.0;
+      for (int c = 0; c < b; ++c) {
+        a += fabs(T[(size_t)(j * b + r) * ldT + j * b + c]);
+        if (j > 0) a += fabs(T[(size_t)(j * b + r) * ldT + (j - 1) * b + c]);
+      }
+      rs = fmax(rs, a);
+    }
+    st->tnorm = fmax(st->tnorm, rs + dmax);
+    if (!ok || dmin <= rel_tol * st->tnorm) {
+      st->gate |= kGateKrylov;
+      return;
+    }
+  } else if (!ok || [&] {
+               for (int r = 0; r < b; ++r)
+                 if (L[r][r] <= 1e-6 * sqrt(fmax(G[r * b + r], 0.0))) return true;
+               return false;
+             }()) {
+    if (j == -2) {
+      // LOBPCG residual block: fall back to column scaling; the SVQB step of
+      // the Rayleigh-Ritz drops what stays dependent
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) Rinv[r * b + c] = (r == c) ? (G[r * b + r] > 0.0 ? 1.0 / sqrt(G[r * b + r]) : 1.0) : 0.0;
+      return;
+    }
+    st->gate |= kGateKrylov;
+    if (j < 0) st->status |= kStatusBreakdown;
+    return;
+  }
+  // Rinv = (L^T)^{-1}, upper triangular: solve L^T X = I
+  double U[MOTO_MAX_K][MOTO_MAX_K];
+  for (int c = 0; c < b; ++c) {
+    for (int r = b - 1; r >= 0; --r) {
+      double a = (r == c) ? 1.0 : 0.0;
+      for (int t = r + 1; t < b; ++t) a -= L[t][r] * U[t][c];
+      U[r][c] = a / L[r][r];
+    }
+  }
+  for (int r = 0; r < b; ++r)
+    for (int c = 0; c < b; ++c) Rinv[r * b + c] = U[r][c];
+  if (!second) {
+    for (int r = 0; r < b; ++r)
+      for (int c = 0; c < b; ++c) Racc[r * b + c] = L[c][r];  // R1 = L^T
+  } else {
+    double R[MOTO_MAX_K][MOTO_MAX_K];
+    for (int r = 0; r < b; ++r)
+      for (int c = 0; c < b; ++c) {
+        double a = 0.0;
+        for (int t = 0; t < b; ++t) a += L[t][r] * Racc[t * b + c];  // (L2^T R1)[r][c]
+        R[r][c] = a;
+      }
+    for (int r = 0; r < b; ++r)
+      for (int c = 0; c < b; ++c) Racc[r * b + c] = R[r][c];
+    if (j >= 0) {
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) {
+          T[(size_t)((j + 1) * b + r) * ldT + j * b + c] = R[r][c];
+          T[(size_t)(j * b + c) * ldT + (j + 1) * b + r] = R[r][c];
+        }
+    }
+    if (j >= -1) {
+      st->steps += 1;
+      st->nT = st->steps * b;
+    }
+  }
+}
+
+void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T, int ldT,
+                   DevState* st, double rel_tol, cudaStream_t s) {
+  cholqr_kernel<<<1, 32, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol);
+}
+
+// Cyclic Jacobi with round-robin (parallel) ordering on an n x n symmetric
+// matrix A (row stride ld >= n + (n & 1)) held in shared memory; V receives the
+// eigenvectors (columns), diag(A) the eigenvalues.  Whole block participates.
+// scratch: cs, sn (n/2 + 1 doubles each), pp, qq (n/2 + 1 ints), red (>= 16 doubles).
+__device__ void block_jacobi(double* A, double* V, int n, int ld, double* cs, double* sn, int* pp, int* qq,
+                             double* red) {
+  const int n2 = n + (n & 1);
+  for (int idx = threadIdx.x; idx < n2 * n2; idx += blockDim.x) {
+    const int r = idx / n2, c = idx - r * n2;
+    if (r >= n || c >= n) A[r * ld + c] = 0.0;
+    V[r * ld + c] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int half = n2 / 2;
+  __shared__ bool stop;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int r = idx / n, c = idx - r * n;
+      const double a = A[r * ld + c];
+      if (r == c)
+        dia += a * a;
+      else
+        off += a * a;
+    }
+    double v2[2] = {off, dia};
+    block_sum<2>(v2, red);
+    if (threadIdx.x == 0) stop = !(v2[0] > 1e-30 * v2[1]) || n <= 1;
+    __syncthreads();
+    if (stop) break;
+    for (int round = 0; round < n2 - 1; ++round) {
+      for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int a0 = t, b0 = n2 - 1 - t;
+        int p = a0 == 0 ? 0 : ((a0 - 1 + round) % (n2 - 1)) + 1;
+        int q = b0 == 0 ? 0 : ((b0 - 1 + round) % (n2 - 1)) + 1;
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        pp[t] = p;
+        qq[t] = q;
+        double c = 1.0, s = 0.0;
+        const double apq = A[p * ld + q];
+        if (q < n && fabs(apq) > 1e-300) {
+          const double tau = (A[q * ld + q] - A[p * ld + p]) / (2.0 * apq);
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          s = tt * c;
+        }
+        cs[t] = c;
+        sn[t] = s;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < half * n2; idx += blockDim.x) {
+        const int t = idx / n2, col = idx - t * n2;
+        const int p = pp[t], q = qq[t];
+        const double c = cs[t], s = sn[t];
+        const double ap = A[p * ld + col], aq = A[q * ld + col];
+        A[p * ld + col] = c * ap - s * aq;
+        A[q * ld + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < half * n2; idx += blockDim.x) {
+        const int t = idx / n2, row = idx - t * n2;
+        const int p = pp[t], q = qq[t];
+        const double c = cs[t], s = sn[t];
+        const double ap = A[row * ld + p], aq = A[row * ld + q];
+        A[row * ld + p] = c * ap - s * aq;
+        A[row * ld + q] = s * ap + c * aq;
+        const double vp = V[row * ld + p], vq = V[row * ld + q];
+        V[row * ld + p] = c * vp - s * vq;
+        V[row * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// rank of diag entry i among the first n (ascending, ties by index)
+__device__ __forceinline__ int diag_rank(const double* A, int ld, int n, int i) {
+  const double li = A[i * ld + i];
+  int rank = 0;
+  for (int j = 0; j < n; ++j) {
+    const double lj = A[j * ld + j];
+    rank += (lj < li) || (lj == li && j < i);
+  }
+  return rank;
+}
+
+constexpr int kEigMax = MOTO_MAX_BASIS;
+
+__global__ void __launch_bounds__(256) small_eig_kernel(const double* Tm, int ldT, double* theta, double* Y, int k,
+                                                        DevState* st) {
+  if (st->gate & kGateDone) return;
+  extern __shared__ double sm[];
+  const int n = st->nT;
+  const int n2 = n + (n & 1);
+  const int ld = n2 + 1;
+  double* A = sm;
+  double* V = A + (size_t)n2 * ld;
+  double* cs = V + (size_t)n2 * ld;
+  double* sn = cs + n2 / 2 + 1;
+  double* red = sn + n2 / 2 + 1;
+  int* pp = reinterpret_cast<int*>(red + 32);
+  int* qq = pp + n2 / 2 + 1;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    A[r * ld + c] = 0.5 * (Tm[(size_t)r * ldT + c] + Tm[(size_t)c * ldT + r]);
+  }
+  __syncthreads();
+  block_jacobi(A, V, n, ld, cs, sn, pp, qq, red);
+  for (int i = threadIdx.x; i < MOTO_MAX_BASIS; i += blockDim.x) theta[i] = 1.0 / 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int rank = diag_rank(A, ld, n, i);
+    theta[rank] = A[i * ld + i];
+    if (rank < k)
+      for (int r = 0; r < n; ++r) Y[(size_t)r * k + rank] = V[r * ld + i];
+  }
+}
+
+void launch_small_eig(const double* T, int ldT, double* theta, double* Y, int k, DevState* st, cudaStream_t s) {
+  const int n2 = kEigMax;
+  const size_t smem = (size_t)2 * n2 * (n2 + 1) * sizeof(double) + (n2 + 2) * sizeof(double) +
+                      32 * sizeof(double) + (n2 + 2) * sizeof(int);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(small_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  small_eig_kernel<<<1, 256, smem, s>>>(T, ldT, theta, Y, k, st);
+}
+
+// LOBPCG Rayleigh-Ritz on the trial subspace S = [X, W, P] (nS = nb*k columns):
+// G = S^T S and M = S^T A S arrive as nb column blocks (nS x k each).  SVQB:
+// D = diag(G)^-1/2, eig(D G D) = U w U^T, keep w > drop*max(w),
+// Z = D U_keep w_keep^-1/2; eig(Z^T M Z) = U2 w2 U2^T ascending;
+// Cx = Z U2[:, :k]; Cp = Cx with the X rows zeroed; theta = w2[:k];
+// hnorm = max(hnorm, max |w2|).
+__global__ void __launch_bounds__(256) lob_rr_kernel(const double* Gb, const double* Mb, int k, int nb,
+                                                     double drop, double* Cx, double* Cp, double* theta,
+                                                     DevState* st) {
+  if (st->gate & (kGateKrylov | kGateDone)) return;
+  constexpr int NM = 3 * MOTO_MAX_K;
+  constexpr int LD = NM + 1;
+  __shared__ double A[NM * LD], V[NM * LD], G[NM * NM], Mm[NM * NM], Z[NM * NM];
+  __shared__ double cs[NM / 2 + 1], sn[NM / 2 + 1], red[32], dinv[NM], w[NM];
+  __shared__ int pp[NM / 2 + 1], qq[NM / 2 + 1], keep_idx[NM];
+  __shared__ int nkeep;
+  const int n = nb * k;
+  // assemble G and M (symmetrised)
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    const int cb = c / k, cc = c - cb * k;
+    const int rb = r / k, rr = r - rb * k;
+    const double g1 = Gb[(size_t)cb * n * k + r * k + cc], g2 = Gb[(size_t)rb * n * k + c * k + rr];
+    const double m1 = Mb[(size_t)cb * n * k + r * k + cc], m2 = Mb[(size_t)rb * n * k + c * k + rr];
+    G[r * NM + c] = 0.5 * (g1 + g2);
+    Mm[r * NM + c] = 0.5 * (m1 + m2);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = G[i * NM + i];
+    dinv[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx - r * n;
+    A[r * LD + c] = dinv[r] * G[r * NM + c] * dinv[c];
+  }
+  __syncthreads();
+  block_jacobi(A, V, n, LD, cs, sn, pp, qq, red);
+  if (threadIdx.x == 0) {
+    double wmax = 0.0;
+    for (int i = 0; i < n; ++i) wmax = fmax(wmax, A[i * LD + i]);
+    // kept directions in ascending eigenvalue order of the scaled Gram
+    int cnt = 0;
+    for (int rank = 0; rank < n; ++rank)
+      for (int i = 0; i < n; ++i)
+        if (diag_rank(A, LD, n, i) == rank && A[i * LD + i] > drop * wmax) {
+          keep_idx[cnt] = i;
+          w[cnt] = A[i * LD + i];
+          ++cnt;
+        }
+    nkeep = cnt;
+  }
+  __syncthreads();
+  const int nk = nkeep;
+  // Z = D U_keep w^-1/2  (n x nk)
+  for (int idx = threadIdx.x; idx < n * nk; idx += blockDim.x) {
+    const int r = idx / nk, c = idx - r * nk;
+    Z[r * NM + c] = dinv[r] * V[r * LD + keep_idx[c]] / sqrt(w[c]);
+  }
+  __syncthreads();
+  // A = Z^T M Z (nk x nk)
+  for (int idx = threadIdx.x; idx < n * nk; idx += blockDim.x) {
+    const int r = idx / nk, c = idx - r * nk;  // tmp = M Z  stored in V (n x nk)
+    double a = 0.0;
+    for (int t = 0; t < n; ++t) a += Mm[r * NM + t] * Z[t * NM + c];
+    V[r * LD + c] = a;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nk * nk; idx += blockDim.x) {
+    const int r = idx / nk, c = idx - r * nk;
+    double a = 0.0;
+    for (int t = 0; t < n; ++t) a += Z[t * NM + r] * V[t * LD + c];
+    A[r * LD + c] = a;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nk * nk; idx += blockDim.x) {
+    const int r = idx / nk, c = idx - r * nk;
+    G[r * NM + c] = 0.5 * (A[r * LD + c] + A[c * LD + r]);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nk * nk; idx += blockDim.x) {
+    const int r = idx / nk, c = idx - r * nk;
+    A[r * LD + c] = G[r * NM + c];
+  }
+  __syncthreads();
+  block_jacobi(A, V, nk, LD, cs, sn, pp, qq, red);
+  // ascending order; Cx = Z U2[:, :k]
+  for (int i = threadIdx.x; i < nk; i += blockDim.x) {
+    const int rank = diag_rank(A, LD, nk, i);
+    if (rank < k) {
+      theta[rank] = A[i * LD + i];
+      for (int r = 0; r < n; ++r) {
+        double a = 0.0;
+        for (int t = 0; t < nk; ++t) a += Z[r * NM + t] * V[t * LD + i];
+        Cx[r * k + rank] = a;
+        Cp[r * k + rank] = r < k ? 0.0 : a;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    double h = st->hnorm;
+    for (int i = 0; i < nk; ++i) h = fmax(h, fabs(A[i * LD + i]));
+    st->hnorm = h;
+  }
+}
+
+void launch_lob_rr(const double* Gb, const double* Mb, int k, int nb, double drop, double* Cx, double* Cp,
+                   double* theta, DevState* st, cudaStream_t s) {
+  lob_rr_kernel<<<1, 256, 0, s>>>(Gb, Mb, k, nb, drop, Cx, Cp, theta, st);
+}
+
+// LOBPCG convergence test on the residual Gram diagonal; also builds the
+// coefficient matrix diag(theta) used to form R = AX - X theta, and sets the
+// solver gate when max_j |r_j| <= tol * hnorm.
+__global__ void lob_check_kernel(const double* Gw, int k, double tol, const double* theta, DevState* st) {
+  if (threadIdx.x != 0) return;
+  if (st->gate & (kGateKrylov | kGateDone)) return;
+  double r = 0.0;
+  for (int j = 0; j < k; ++j) r = fmax(r, sqrt(fmax(Gw[j * k + j], 0.0)));
+  if (r <= tol * st->hnorm)
+    st->gate |= kGateKrylov;
+  else
+    st->iters += 1;
+  (void)theta;
+}
+
+void launch_lob_check(const double* Gw, int k, double tol, const double* theta, DevState* st, cudaStream_t s) {
+  lob_check_kernel<<<1, 32, 0, s>>>(Gw, k, tol, theta, st);
+}
+
+// diag(theta) (k x k) and diag(1/sqrt(G_jj)) helpers for combine launches
+__global__ void diag_kernel(const double* src, int k, int mode, double* out, const DevState* st, int mask) {
+  if (st && (st->gate & mask)) return;
+  for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) {
+    const int r = idx / k, c = idx - r * k;
+    double v = 0.0;
+    if (r == c) {
+      if (mode == 0)
+        v = src[r];
+      else {
+        const double g = src[r * k + r];
+        v = g > 0.0 ? 1.0 / sqrt(g) : 1.0;
+      }
+    }
+    out[idx] = v;
+  }
+}
+
+void launch_diag(const double* src, int k, int mode, double* out, const DevState* st, int mask, cudaStream_t s) {
+  diag_kernel<<<1, 64, 0, s>>>(src, k, mode, out, st, mask);
+}
+
+// ===========================================================================
+// MMF / L-BFGS
+// ===========================================================================
+// G = g - 2 reflect (g . v1) v1  (= -F_mmf for reflect = 1, F = -g);  max_i |G_i|.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict__ g, const T* __restrict__ v1,
+                                                             const double* dot, double reflect, T* G, int N,
+                                                             double* part, unsigned* counter, double* fmax_out,
+                                                             const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  const T a = v1 ? (T)(2.0 * reflect * dot[0]) : (T)0;
+  double mx = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t e = (size_t)c * N + i;
+      r[c] = g[e] - (v1 ? a * v1[e] : (T)0);
+      G[e] = r[c];
+    }
+    mx = fmax(mx, (double)(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]));
+  }
+  __shared__ double red[8];
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = mx;
+  if (!grid_last_block(counter)) return;
+  double b = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) b = fmax(b, __ldcg(part + k));
+  b = block_max(b, red);
+  if (threadIdx.x == 0) {
+    fmax_out[0] = sqrt(b);
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+void launch_mmf_force(const T* g, const T* v1, const double* dot, double reflect, T* G, int N, double* part,
+                      unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
+  mmf_force_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(g, v1, dot, reflect, G, N, part, counter, fmax_out,
+                                                           gate, mask);
+}
+
+// New pair at the current point: s = P d_prev, y = G - P G_prev, written into
+// ring slot lb_head (interleaved storage: s at 2*head, y at 2*head+1) and into
+// the two staging fields (contiguous, for the Gram launch).
+template <typename T>
+__global__ void lbfgs_pair_kernel(const T* __restrict__ m, const T* __restrict__ d_prev,
+                                  const T* __restrict__ G_prev, const T* __restrict__ G, T* ring, size_t ld,
+                                  T* stage, const DevState* dst, int N, const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  if (!dst->lb_have_prev) return;
+  T* s_out = ring + (size_t)(2 * dst->lb_head) * ld;
+  T* y_out = s_out + ld;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    T d[3], gp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      d[c] = d_prev[(size_t)c * N + i];
+      gp[c] = G_prev[(size_t)c * N + i];
+    }
+    const T pd = m0 * d[0] + m1 * d[1] + m2 * d[2];
+    const T pg = m0 * gp[0] + m1 * gp[1] + m2 * gp[2];
+    const T mm[3] = {m0, m1, m2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t e = (size_t)c * N + i;
+      const T sv = d[c] - pd * mm[c];
+      const T yv = G[e] - (gp[c] - pg * mm[c]);
+      s_out[e] = sv;
+      y_out[e] = yv;
+      stage[e] = sv;
+      stage[ld + e] = yv;
+    }
+  }
+}
+
+template <typename T>
+void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
+                       const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
+  lbfgs_pair_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, d_prev, G_prev, G, ring, ld, stage, dst, N, gate,
+                                                            mask);
+}
+
+// Two-loop recursion in coefficient space over the basis
+//   b_{2j} = s_j, b_{2j+1} = y_j (j < R = mem + 1 ring slots), b_{2R} = G.
+// The ring keeps `lb_count` <= mem accepted pairs in the slots preceding
+// `lb_head`; slot lb_head is free and receives the next candidate pair, so a
+// rejected candidate never evicts a kept pair.  M is the persistent
+// (2R+1)^2 Gram matrix of the basis.  newdots holds, for every basis vector,
+// its dots with the candidate s and y ((2R+1) x 2) followed by its dots with
+// G ((2R+1) x 1).
+__global__ void lbfgs_solve_kernel(double* M, int mem, const double* newdots, double gamma0, double* coef,
+                                   DevState* dst) {
+  if (dst->gate & kGateDone) return;
+  if (threadIdx.x != 0) return;
+  const int R = mem + 1;
+  const int nb = 2 * R + 1, gi = 2 * R;
+  const double* pd = newdots;
+  const double* gd = newdots + 2 * nb;
+  if (dst->lb_have_prev) {
+    const int h = dst->lb_head;
+    const int si = 2 * h, yi = 2 * h + 1;
+    for (int t = 0; t < nb; ++t) {
+      M[si * nb + t] = M[t * nb + si] = pd[t * 2 + 0];
+      M[yi * nb + t] = M[t * nb + yi] = pd[t * 2 + 1];
+    }
+    const double sy = M[si * nb + yi], ss = M[si * nb + si], yy = M[yi * nb + yi];
+    if (sy > 1e-12 * sqrt(ss * yy)) {
+      dst->lb_head = (h + 1) % R;
+      dst->lb_count = min(dst->lb_count + 1, mem);
+    }
+  }
+  for (int t = 0; t < nb; ++t) M[gi * nb + t] = M[t * nb + gi] = gd[t];
+  // coefficient-space dot products: u^T M w
+  auto dotc = [&](const double* u, const double* w) {
+    double a = 0.0;
+    for (int r = 0; r < nb; ++r) {
+      if (u[r] == 0.0) continue;
+      double b = 0.0;
+      for (int c = 0; c < nb; ++c) b += M[r * nb + c] * w[c];
+      a += u[r] * b;
+    }
+    return a;
+  };
+  double q[2 * MOTO_MAX_MEM + 3], e[2 * MOTO_MAX_MEM + 3], alpha[MOTO_MAX_MEM], rho[MOTO_MAX_MEM];
+  for (int t = 0; t < nb; ++t) q[t] = 0.0;
+  q[gi] = 1.0;
+  const int cnt = dst->lb_count;
+  // newest .. oldest
+  for (int k = 0; k < cnt; ++k) {
+    const int slot = ((dst->lb_head - 1 - k) % R + R) % R;
+    const int si = 2 * slot, yi = si + 1;
+    rho[k] = 1.0 / M[yi * nb + si];
+    for (int t = 0; t < nb; ++t) e[t] = 0.0;
+    e[si] = 1.0;
+    alpha[k] = rho[k] * dotc(e, q);
+    q[yi] -= alpha[k];
+  }
+  double gamma = gamma0;
+  if (cnt > 0) {
+    const int slot = ((dst->lb_head - 1) % R + R) % R;
+    const int si = 2 * slot, yi = si + 1;
+    gamma = M[si * nb + yi] / M[yi * nb + yi];
+  }
+  for (int t = 0; t < nb; ++t) q[t] *= gamma;  // r
+  // oldest .. newest
+  for (int k = cnt - 1; k >= 0; --k) {
+    const int slot = ((dst->lb_head - 1 - k) % R + R) % R;
+    const int si = 2 * slot, yi = si + 1;
+    for (int t = 0; t < nb; ++t) e[t] = 0.0;
+    e[yi] = 1.0;
+    const double beta = rho[k] * dotc(e, q);
+    q[si] += alpha[k] - beta;
+  }
+  for (int t = 0; t < nb; ++t) q[t] = -q[t];  // d = -r
+  for (int t = 0; t < nb; ++t) e[t] = 0.0;
+  e[gi] = 1.0;
+  if (dotc(q, e) >= 0.0) {
+    dst->lb_count = 0;
+    for (int t = 0; t < nb; ++t) q[t] = 0.0;
+    q[gi] = -gamma0;
+  }
+  for (int t = 0; t < nb; ++t) coef[t] = q[t];
+  dst->lb_have_prev = 1;
+}
+
+void launch_lbfgs_solve(double* M, int mem, const double* newdots, double gamma0, double* coef, DevState* dst,
+                        cudaStream_t st) {
+  lbfgs_solve_kernel<<<1, 32, 0, st>>>(M, mem, newdots, gamma0, coef, dst);
+}
+
+// d = P(sum_t coef_t b_t); max_i |d_i| -> step scale min(1, theta_max / max).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) lbfgs_direction_kernel(const T* __restrict__ basis, size_t ld, int nb,
+                                                                   const double* coef, const T* __restrict__ m,
+                                                                   T* d, int N, double theta_max, double* part,
+                                                                   unsigned* counter, DevState* dst,
+                                                                   const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  __shared__ T cf[2 * MOTO_MAX_MEM + 3];
+  if (threadIdx.x < nb) cf[threadIdx.x] = (T)coef[threadIdx.x];
+  __syncthreads();
+  double mx = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T a[3] = {0, 0, 0};
+    for (int t = 0; t < nb; ++t) {
+      const T w = cf[t];
+      if (w == (T)0) continue;
+      const T* b = basis + (size_t)t * ld;
+      a[0] += w * b[i];
+      a[1] += w * b[N + i];
+      a[2] += w * b[2 * (size_t)N + i];
+    }
+    const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    const T p = m0 * a[0] + m1 * a[1] + m2 * a[2];
+    a[0] -= p * m0;
+    a[1] -= p * m1;
+    a[2] -= p * m2;
+    d[i] = a[0];
+    d[N + i] = a[1];
+    d[2 * (size_t)N + i] = a[2];
+    mx = fmax(mx, (double)(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+  }
+  __shared__ double red[8];
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = mx;
+  if (!grid_last_block(counter)) return;
+  double b = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) b = fmax(b, __ldcg(part + k));
+  b = block_max(b, red);
+  if (threadIdx.x == 0) {
+    const double t = sqrt(b);
+    dst->scale = (t > theta_max) ? theta_max / t : 1.0;
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+void launch_lbfgs_direction(const T* basis, size_t ld, int nb, const double* coef, const T* m, T* d, int N,
+                            double theta_max, double* part, unsigned* counter, DevState* dst, const int* gate,
+                            int mask, cudaStream_t st) {
+  lbfgs_direction_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(basis, ld, nb, coef, m, d, N, theta_max, part,
+                                                                 counter, dst, gate, mask);
+}
+
+// d <- scale d;  m_i <- m_i cos|d_i| + d_i/|d_i| sin|d_i|, renormalised.
+template <typename T>
+__device__ __forceinline__ void rodrigues(T& m0, T& m1, T& m2, T d0, T d1, T d2) {
+  const T th = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  if (th > (T)0) {
+    T sn, cs;
+    if (sizeof(T) == 4) {
+      float sf, cf;
+      sincosf((float)th, &sf, &cf);
+      sn = (T)sf;
+      cs = (T)cf;
+    } else {
+      double sd, cd;
+      sincos((double)th, &sd, &cd);
+      sn = (T)sd;
+      cs = (T)cd;
+    }
+    const T f = sn / th;
+    m0 = m0 * cs + d0 * f;
+    m1 = m1 * cs + d1 * f;
+    m2 = m2 * cs + d2 * f;
+  }
+  const T inv = (T)1 / sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+  m0 *= inv;
+  m1 *= inv;
+  m2 *= inv;
+}
+
+template <typename T>
+__global__ void retract_kernel(T* m, T* d, const DevState* dst, int N, const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  const T sc = (T)dst->scale;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T d0 = d[i] * sc, d1 = d[N + i] * sc, d2 = d[2 * (size_t)N + i] * sc;
+    d[i] = d0;
+    d[N + i] = d1;
+    d[2 * (size_t)N + i] = d2;
+    T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    rodrigues(m0, m1, m2, d0, d1, d2);
+    m[i] = m0;
+    m[N + i] = m1;
+    m[2 * (size_t)N + i] = m2;
+  }
+}
+
+template <typename T>
+void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
+  retract_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, d, dst, N, gate, mask);
+}
+
+// Descent seed: out = Rodrigues(m, sign * eta * v1), eta = eta_theta / max|v1_i|.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) vmax_kernel(const T* v, int N, double* part, unsigned* counter,
+                                                        double* out) {
+  double mx = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double a = v[i], b = v[N + i], c = v[2 * (size_t)N + i];
+    mx = fmax(mx, a * a + b * b + c * c);
+  }
+  __shared__ double red[8];
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = mx;
+  if (!grid_last_block(counter)) return;
+  double b = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) b = fmax(b, __ldcg(part + k));
+  b = block_max(b, red);
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(b);
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+__global__ void seed_kernel(const T* m, const T* v1, const double* vmax, double eta_theta, double sign, T* out,
+                            int N) {
+  const T f = (T)(sign * eta_theta / vmax[0]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    rodrigues(m0, m1, m2, f * v1[i], f * v1[N + i], f * v1[2 * (size_t)N + i]);
+    out[i] = m0;
+    out[N + i] = m1;
+    out[2 * (size_t)N + i] = m2;
+  }
+}
+
+template <typename T>
+void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign, T* out, int N, double* part,
+                         unsigned* counter, double* scal, cudaStream_t st) {
+  vmax_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(v1, N, part, counter, scal);
+  seed_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, v1, scal, eta_theta, sign, out, N);
+}
+
+// Saddle / minimum test and the per-step output vector.
+__global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, double tau_F,
+                                   double* out6, int* status_out, DevState* dst, int ascent) {
+  if (threadIdx.x != 0) return;
+  if (dst->gate & kGateDone) {
+    if (status_out) *status_out = 1;
+    return;
+  }
+  const double E = eg_out[0], gmax = eg_out[1];
+  bool conv;
+  if (ascent) {
+    conv = fmax[0] <= tau_F && lam[0] < 0.0 && 0.0 < lam[1];
+    if (out6) {
+      out6[0] = E;
+      out6[1] = fmax[0];
+      out6[2] = lam[0];
+      out6[3] = lam[1];
+      out6[4] = gmax;
+      out6[5] = dst->dot;
+    }
+  } else {
+    conv = gmax <= tau_F;
+    if (out6) {
+      out6[0] = E;
+      out6[1] = gmax;
+    }
+  }
+  if (!isfinite(E) || !isfinite(gmax)) dst->status |= kStatusNonfinite;
+  if (conv) {
+    dst->gate |= kGateDone;
+    dst->converged = 1;
+  } else {
+    dst->pad[1] += 1;  // outer steps taken
+  }
+  if (status_out) *status_out = conv ? 1 : 0;
+}
+
+void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, double tau_F, double* out6,
+                        int* status_out, DevState* dst, int ascent, cudaStream_t st) {
+  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, tau_F, out6, status_out, dst, ascent);
+}
+
+#define INST(T)                                                                                                   \
+  template void launch_gram<T>(const T*, size_t, int, const T*, size_t, int, size_t, double*, double*, unsigned*, \
+                               const int*, int, cudaStream_t);                                                    \
+  template void launch_combine<T>(const T*, size_t, int, const int*, const double*, int, const T*, size_t,        \
+                                  double, double, T*, size_t, const T*, int, const int*, int, cudaStream_t);      \
+  template void launch_project<T>(const T*, const T*, size_t, T*, size_t, int, int, const int*, int,              \
+                                  cudaStream_t);                                                                  \
+  template void launch_finish<T>(const T*, T*, size_t, int, int, double*, unsigned*, double*, const int*, int,    \
+                                 cudaStream_t);                                                                   \
+  template void launch_mmf_force<T>(const T*, const T*, const double*, double, T*, int, double*, unsigned*,       \
+                                    double*, const int*, int, cudaStream_t);                                      \
+  template void launch_lbfgs_pair<T>(const T*, const T*, const T*, const T*, T*, size_t, T*, const DevState*,     \
+                                     int, const int*, int, cudaStream_t);                                         \
+  template void launch_lbfgs_direction<T>(const T*, size_t, int, const double*, const T*, T*, int, double,        \
+                                          double*, unsigned*, DevState*, const int*, int, cudaStream_t);          \
+  template void launch_retract<T>(T*, T*, const DevState*, int, const int*, int, cudaStream_t);                   \
+  template void launch_descent_seed<T>(const T*, const T*, double, double, T*, int, double*, unsigned*, double*,  \
+                                       cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace moto

@@ -1,0 +1,158 @@
+"""GPU parity of the inner layer (block Lanczos / LOBPCG) against the oracle.
+
+Eigenvalue bar: FP64 runs match the oracle's same-algorithm run to 1e-9
+relative; FP32 runs satisfy |dlam| <= 1e-4 |lam| + 1e-6 |H| (the second term is
+the rounding floor of an FP32 HVP, |H| estimated by the top Ritz value).
+Eigenvectors are compared by |cos| (their sign rule is checked separately)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import krylov, spin
+from oracle.model import Model
+from gpu_util import context, rand_spins, require_gpu, to_dev, to_np, workload_model
+
+pytestmark = pytest.mark.gpu
+
+FULL = dict(J=(1.0, -0.1, -0.05), D=0.3, K=0.05, muB=0.02)
+
+
+def vdot(a, b):
+    return float(np.dot(a.ravel(), b.ravel()))
+
+
+def fp32_ok(lam_gpu, lam_ref, hnorm):
+    return abs(lam_gpu - lam_ref) <= 1e-4 * abs(lam_ref) + 1e-6 * hnorm
+
+
+def test_lanczos_fp64_matches_oracle_step_for_step():
+    require_gpu()
+    M = workload_model(1)
+    m = inputs.workload1_state()
+    q0 = inputs.gaussian_field(inputs.workload_seed(1, 0), 32, 32, offset=10**6)
+    ctx = context(M, torch.float64, k=1, block=1, krylov_steps=60)
+    md = to_dev(m, torch.float64)
+    lam, V, info = ctx.lowest_modes(md, to_dev(q0, torch.float64)[None].contiguous())
+    _, s_ref = spin.riemann_grad(M, m)
+    th, Vr = krylov.lanczos_modes(M, m, s_ref, q0, 60, k=1)
+    lam = to_np(lam)
+    assert int(to_np(info)[0]) == 60
+    np.testing.assert_allclose(lam[:60], th, rtol=1e-9, atol=1e-12)
+    v = to_np(V[0])
+    assert abs(vdot(v, Vr[0])) == pytest.approx(1.0, abs=1e-9)
+    # the sign rule of the Ritz vector
+    np.testing.assert_allclose(v, Vr[0], atol=1e-7)
+    ctx.close()
+
+
+def test_lanczos_breakdown_on_a_tiny_lattice_recovers_the_dense_spectrum():
+    require_gpu()
+    M = Model(5, 5, **FULL)
+    m = inputs.add_noise(inputs.skyrmion(5, 5, 1.2), 0.3, 17)
+    ctx = context(M, torch.float64, k=1, block=1, krylov_steps=80)
+    lam, V, info = ctx.lowest_modes(to_dev(m, torch.float64), to_dev(inputs.gaussian_field(3, 5, 5), torch.float64)[None].contiguous())
+    w = np.linalg.eigvalsh(spin.dense_tangent_hessian(M, m)[0])
+    lam = to_np(lam)
+    n = int(to_np(info)[0])
+    assert n <= 2 * 25
+    assert lam[0] == pytest.approx(w[0], abs=1e-10)
+    assert lam[1] == pytest.approx(w[1], abs=1e-10)
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_block_lanczos_matches_oracle(dtype):
+    require_gpu()
+    M = Model(24, 20, **FULL)
+    m = inputs.add_noise(inputs.skyrmion(24, 20, 3.0), 0.05, 23)
+    X0 = [inputs.gaussian_field(40 + j, 24, 20) for j in range(3)]
+    ctx = context(M, dtype, k=3, block=3, krylov_steps=30)
+    md = to_dev(m, dtype)
+    lam, V, info = ctx.lowest_modes(md, to_dev(np.stack(X0), dtype))
+    mo = to_np(md)
+    _, s_ref = spin.riemann_grad(M, mo)
+    th, Vr = krylov.block_lanczos_modes(M, mo, s_ref, X0, 30, 3)
+    lam = to_np(lam)
+    hnorm = th[-1]
+    for j in range(3):
+        if dtype == torch.float64:
+            assert lam[j] == pytest.approx(th[j], rel=1e-9, abs=1e-12)
+            assert abs(vdot(to_np(V[j]), Vr[j])) == pytest.approx(1.0, abs=1e-8)
+        else:
+            assert fp32_ok(lam[j], th[j], hnorm)
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_lobpcg_matches_dense_spectrum(dtype):
+    require_gpu()
+    L1, L2 = 7, 6
+    M = Model(L1, L2, **FULL)
+    m = inputs.add_noise(inputs.skyrmion(L1, L2, 1.5), 0.3, 101)
+    w = np.linalg.eigvalsh(spin.dense_tangent_hessian(M, m)[0])
+    X0 = np.stack([inputs.gaussian_field(2 + j, L1, L2) for j in range(3)])
+    ctx = context(M, dtype, k=3, solver=1, max_iter=400, tol=1e-7 if dtype == torch.float64 else 1e-5)
+    md = to_dev(m, dtype)
+    lam, V, info = ctx.lowest_modes(md, to_dev(X0, dtype))
+    lam = to_np(lam)
+    it = int(to_np(info)[0])
+    assert it < 400
+    for j in range(3):
+        if dtype == torch.float64:
+            assert lam[j] == pytest.approx(w[j], abs=1e-9)
+        else:
+            assert fp32_ok(lam[j], w[j], w[-1])
+    ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_lobpcg_matches_oracle_lobpcg(dtype):
+    require_gpu()
+    L = 48
+    M = workload_model(2, L, L)
+    m = inputs.add_noise(inputs.skyrmion(L, L, 5.0), 0.01, 2024)
+    X0 = [inputs.gaussian_field(60 + j, L, L) for j in range(4)]
+    _, s_ref = spin.riemann_grad(M, m)
+    th, Vr, it, conv = krylov.lobpcg_modes(M, m, s_ref, X0, 4, tol=1e-9, max_iter=1500)
+    assert conv
+    ctx = context(M, dtype, k=4, solver=1, max_iter=1500, tol=1e-8 if dtype == torch.float64 else 2e-6)
+    md = to_dev(m, dtype)
+    lam, V, info = ctx.lowest_modes(md, to_dev(np.stack(X0), dtype))
+    lam = to_np(lam)
+    assert int(to_np(info)[0]) < 1500
+    for j in range(4):
+        if dtype == torch.float64:
+            assert lam[j] == pytest.approx(th[j], rel=1e-8, abs=1e-12)
+        else:
+            assert fp32_ok(lam[j], th[j], 12.0)
+    ctx.close()
+
+
+def test_lobpcg_fp32_workload2_size_checked_by_oracle_residuals():
+    """At full 256 x 256 size the oracle checks the GPU's own output: each Ritz
+    value equals the FP64 Rayleigh quotient of its vector, vectors are tangent,
+    orthonormal, and the residuals are as small as reported."""
+    require_gpu()
+    M = workload_model(2)
+    m = inputs.workload2_states(1)[0]
+    X0 = np.stack([inputs.gaussian_field(70 + j, 256, 256) for j in range(6)])
+    ctx = context(M, torch.float32, k=6, solver=1, max_iter=200, tol=1e-6)
+    md = to_dev(m, torch.float32)
+    lam, V, info = ctx.lowest_modes(md, to_dev(X0, torch.float32))
+    mo = to_np(md)
+    _, s_ref = spin.riemann_grad(M, mo)
+    lam = to_np(lam)
+    Vh = to_np(V)
+    G = np.array([[vdot(a, b) for b in Vh] for a in Vh])
+    np.testing.assert_allclose(G, np.eye(6), atol=1e-4)
+    for j in range(6):
+        v = Vh[j]
+        assert np.max(np.abs(np.sum(v * mo, axis=0))) < 1e-5
+        hv = spin.hvp(M, mo, s_ref, v)
+        rq = vdot(v, hv) / vdot(v, v)
+        assert fp32_ok(lam[j], rq, 12.0)
+    assert np.all(np.diff(lam[:6]) >= -1e-7)
+    ctx.close()

@@ -1,0 +1,76 @@
+"""GPU parity of the outer layer on the 32 x 32 single-walker workload (FP64):
+the reflected-force ascent must retrace the oracle's trajectory step by step,
+stop at the same index-1 saddle, and the two-sided descent must reach the same
+two minima with bit-equal integer Q."""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import mmf, spin, topo
+from gpu_util import context, require_gpu, to_dev, to_np, workload_model
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def oracle_run():
+    M = workload_model(1)
+    m0 = inputs.workload1_state()
+    q0 = inputs.gaussian_field(inputs.workload_seed(1, 0), 32, 32, offset=10**6)
+    P = mmf.MMFParams()
+    res = mmf.ascend(M, m0, [q0], P)
+    plus, minus = mmf.descend(M, res.m, res.v1, P)
+    return M, m0, q0, P, res, plus, minus
+
+
+@pytest.fixture(scope="module")
+def gpu_run(oracle_run):
+    require_gpu()
+    M, m0, q0, P, res, plus, minus = oracle_run
+    ctx = context(M, torch.float64)
+    m = to_dev(m0, torch.float64)
+    V = to_dev(q0, torch.float64)[None].contiguous()
+    rc, steps, trace = ctx.ascend(m, V, check_every=10)
+    rc2, mp, mm, out = ctx.descend(m, V[0].contiguous())
+    r = dict(rc=rc, steps=steps, trace=to_np(trace), m=to_np(m), v1=to_np(V[0]), rc2=rc2, mp=to_np(mp),
+             mm=to_np(mm), out=to_np(out))
+    ctx.close()
+    return r
+
+
+def test_ascent_retraces_the_oracle(oracle_run, gpu_run):
+    M, m0, q0, P, res, plus, minus = oracle_run
+    assert res.converged and gpu_run["rc"] == 0
+    assert gpu_run["steps"] == res.steps
+    tr = gpu_run["trace"]
+    for t, row in enumerate(res.trace):
+        assert tr[t, 0] == pytest.approx(row["E"], abs=1e-7)
+        assert tr[t, 1] == pytest.approx(row["fmax"], rel=1e-5, abs=1e-9)
+        assert tr[t, 2] == pytest.approx(row["lam1"], rel=1e-5, abs=1e-9)
+        assert tr[t, 3] == pytest.approx(row["lam2"], rel=1e-5, abs=1e-9)
+
+
+def test_saddle_matches_and_is_index1(oracle_run, gpu_run):
+    M, m0, q0, P, res, plus, minus = oracle_run
+    E_gpu = spin.energy(M, gpu_run["m"])
+    assert E_gpu == pytest.approx(spin.energy(M, res.m), abs=1e-4)
+    dev = np.sqrt(np.max(np.sum((gpu_run["m"] - res.m) ** 2, axis=0)))
+    assert dev < 1e-3
+    w = np.linalg.eigvalsh(spin.dense_tangent_hessian(M, gpu_run["m"])[0])
+    assert w[0] < 0.0 < w[1]
+
+
+def test_descent_minima_and_charges(oracle_run, gpu_run):
+    M, m0, q0, P, res, plus, minus = oracle_run
+    out = gpu_run["out"]
+    assert gpu_run["rc2"] == 0
+    E_p, Q_p, E_m, Q_m = out[:4]
+    assert int(round(Q_p)) == plus.Qint and int(round(Q_m)) == minus.Qint
+    assert E_p == pytest.approx(plus.E, abs=1e-4)
+    assert E_m == pytest.approx(minus.E, abs=1e-4)
+    assert E_p == pytest.approx(spin.energy(M, gpu_run["mp"]), abs=1e-9)
+    assert Q_p == pytest.approx(topo.topo_charge(gpu_run["mp"]), abs=1e-9)
+    for mm in (gpu_run["mp"], gpu_run["mm"]):
+        g, _ = spin.riemann_grad(M, mm)
+        assert mmf.max_torque(g) <= P.tau_F * (1 + 1e-9)
