@@ -216,6 +216,26 @@ const char* moto_status_string(int code);
 int moto_profile_begin(moto_ctx* ctx, int capacity);
 int moto_profile_end(moto_ctx* ctx, int nkinds, int* launches, double* ms, double* bytes);
 
+/* Allocation-free energy and Riemannian gradient (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory).
+ * Creating a moto_ctx allocates scratch, which some callers cannot do: a host
+ * framework that owns all device memory and hands a library only the buffers
+ * of each call, or a caller that must not risk the device-wide
+ * synchronisation cudaMalloc / cudaFree may imply.  This call computes the
+ * same outputs as moto_energy_grad (g_dev, s_dev, out_dev = [E, max_i |g_i|];
+ * each optional) for the model and dtype given here, without a context.
+ * Its only scratch is a fixed device array inside the library (512 KB + 256 B,
+ * held by every GPU that loads the library until the process exits); it
+ * holds the partial sums of at most 32768 tiles of 32 x 32 sites, so
+ * ceil(L1/32) * ceil(L2/32) > 32768 is rejected with MOTO_ERR_ARG.  The first
+ * call on a device looks the array up with that device current; make that
+ * first call outside any stream capture.  Every call shares the array and
+ * keeps the last call's contents, so calls that overlap on the GPU (several
+ * streams or devices' threads at once) race; serialise them.  Non-finite
+ * inputs are not reported by this variant.  Calls no cudaMalloc or cudaFree. */
+int moto_energy_grad_noalloc(const moto_model* model, int dtype, const void* m_dev, void* g_dev,
+                             void* s_dev, double* out_dev, void* stream);
+
 /* Bytes of device scratch owned by the context. */
 size_t moto_workspace_bytes(const moto_ctx* ctx);
 

@@ -68,6 +68,7 @@ def _load():
         "moto_status_string": (ctypes.c_char_p, [I]),
         "moto_workspace_bytes": (Z, [P]),
         "moto_profile_begin": (I, [P, I]),
+        "moto_energy_grad_noalloc": (I, [ctypes.POINTER(moto_model), I, P, P, P, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -82,7 +83,7 @@ EXPORTED = (
     "moto_default_params", "moto_create", "moto_destroy", "moto_energy_grad", "moto_energy", "moto_hvp",
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
-    "moto_profile_end",
+    "moto_profile_end", "moto_energy_grad_noalloc",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec")
 
@@ -216,6 +217,13 @@ def moto_status_string(code: int) -> str:
 
 def moto_workspace_bytes(ctx) -> int:
     return int(_lib.moto_workspace_bytes(ctx))
+
+
+def moto_energy_grad_noalloc(model: moto_model, dtype: int, m, g=None, s=None, out=None, stream=None):
+    """Energy and Riemannian gradient without a context: for callers that
+    cannot allocate device memory (see include/moto.h)."""
+    _check(_lib.moto_energy_grad_noalloc(ctypes.byref(model), int(dtype), _ptr(m), _ptr(g), _ptr(s), _ptr(out),
+                                         _stream(stream)), "moto_energy_grad_noalloc")
 
 
 def moto_profile_begin(ctx, capacity=8192):
