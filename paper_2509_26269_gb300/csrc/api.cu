@@ -82,6 +82,7 @@ template <typename T>
 void P_gram(moto_ctx* c, const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
             double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st) {
   PROF(kPkGram, (double)((X == Y) ? nx : nx + ny) * n * sizeof(T));
+  set_gram_status(&c->st->status);
   launch_gram<T>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
 }
 template <typename T>
@@ -548,6 +549,7 @@ int moto_status(moto_ctx* c, void* stream) {
   CK(cudaMemcpyAsync(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
   CK(cudaStreamSynchronize(S(stream)));
   if (h.status & kStatusNonfinite) return MOTO_ERR_NONFINITE;
+  if (h.status & kStatusTimeout) return MOTO_ERR_TIMEOUT;
   if (h.status & (kStatusBreakdown | kStatusNotSPD)) return MOTO_ERR_NUMERIC;
   return MOTO_OK;
 }
@@ -678,6 +680,7 @@ int read_state(moto_ctx* c, DevState* h, cudaStream_t st) {
 
 int status_code(const DevState& h) {
   if (h.status & kStatusNonfinite) return MOTO_ERR_NONFINITE;
+  if (h.status & kStatusTimeout) return MOTO_ERR_TIMEOUT;
   if (h.status & (kStatusBreakdown | kStatusNotSPD)) return MOTO_ERR_NUMERIC;
   return MOTO_OK;
 }

@@ -27,6 +27,7 @@ enum : int {
   kStatusNonfinite = 1,
   kStatusBreakdown = 2,
   kStatusNotSPD = 4,
+  kStatusTimeout = 8,
 };
 
 __device__ __forceinline__ int wrap(int a, int L) {

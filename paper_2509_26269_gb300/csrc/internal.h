@@ -51,6 +51,14 @@ template <typename T>
 void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
                  double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st);
 int gram_blocks();
+// TMA-pipelined Gram (kernels_gram.cu); returns false when the fields are not
+// 16-byte aligned or the shape is out of range (the caller then uses the
+// plain kernel).
+template <typename T>
+bool launch_gram_tma(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+                     double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st);
+// status word of the last context that set one (timeouts of bounded waits)
+void set_gram_status(int* status);
 
 // Site-wise combination of vector fields (3N elements, component-major):
 //   out_c = beta * Y_c + sigma * sum_{r < nx} X_r C[r*ny + c]      (c < ny <= 8)

@@ -138,9 +138,13 @@ static void gram_launch_ny(const T* X, size_t ldx, int nx, const T* Y, size_t ld
   gram_kernel<T, NY><<<grid, kThreads, smem, st>>>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask);
 }
 
+static int* g_gram_status = nullptr;
+void set_gram_status(int* status) { g_gram_status = status; }
+
 template <typename T>
 void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
                  double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st) {
+  if (launch_gram_tma<T>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, g_gram_status, st)) return;
   if (ny <= 1)
     gram_launch_ny<T, 1>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, st);
   else if (ny <= 2)
