@@ -303,7 +303,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", type=int, default=2048,
+                    help="lattice side; values other than 2048 are small cases for profiler captures")
     args = ap.parse_args()
+    global L, WORKLOAD
+    if args.lattice != L:
+        L = args.lattice
+        WORKLOAD = f"profiling case {L}x{L} (same path as the 2048x2048 workload)"
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

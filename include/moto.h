@@ -157,6 +157,16 @@ int moto_lowest_modes(moto_ctx* ctx, const void* m_dev, const void* s_dev,
  * (i+a1, i+a1+a2, i+a2)).  Q_dev: 1 double. */
 int moto_topo_charge(moto_ctx* ctx, const void* m_dev, double* Q_dev, void* stream);
 
+/* Skinny Gram product out[r * ny + c] = X_r . Y_c over the 3N elements of
+ * nx <= MOTO_MAX_BASIS fields X_r (at X_dev + r * ldx) and ny <= MOTO_MAX_K
+ * fields Y_c (at Y_dev + c * ldy), accumulated as the Krylov solvers do it
+ * (FP32 products and short FP32 runs, FP64 above; all FP64 in an FP64
+ * context).  out_dev: nx * ny doubles, row-major.  The building block of the
+ * reorthogonalisation and Rayleigh-Ritz steps, exposed for checks of
+ * orthogonality and for tests. */
+int moto_gram(moto_ctx* ctx, const void* X_dev, size_t ldx, int nx, const void* Y_dev, size_t ldy,
+              int ny, double* out_dev, void* stream);
+
 /* Clears the L-BFGS history of the context (start of an ascent or descent). */
 int moto_lbfgs_reset(moto_ctx* ctx, void* stream);
 

@@ -69,6 +69,7 @@ def _load():
         "moto_workspace_bytes": (Z, [P]),
         "moto_profile_begin": (I, [P, I]),
         "moto_energy_grad_noalloc": (I, [ctypes.POINTER(moto_model), I, P, P, P, P, P]),
+        "moto_gram": (I, [P, P, Z, I, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -83,7 +84,7 @@ EXPORTED = (
     "moto_default_params", "moto_create", "moto_destroy", "moto_energy_grad", "moto_energy", "moto_hvp",
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
-    "moto_profile_end", "moto_energy_grad_noalloc",
+    "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec")
 
@@ -172,6 +173,11 @@ def moto_hvp(ctx, m, s, v, ldv, hv, ldhv, nvec=1, stream=None):
 def moto_lowest_modes(ctx, m, s, params, v0, V, lam, info=None, stream=None):
     _check(_lib.moto_lowest_modes(ctx, _ptr(m), _ptr(s), ctypes.byref(params), _ptr(v0), _ptr(V), _ptr(lam),
                                   _ptr(info), _stream(stream)), "moto_lowest_modes")
+
+
+def moto_gram(ctx, X, ldx, nx, Y, ldy, ny, out, stream=None):
+    _check(_lib.moto_gram(ctx, _ptr(X), int(ldx), int(nx), _ptr(Y), int(ldy), int(ny), _ptr(out),
+                          _stream(stream)), "moto_gram")
 
 
 def moto_topo_charge(ctx, m, Q, stream=None):

@@ -868,3 +868,21 @@ int moto_profile_end(moto_ctx* c, int nkinds, int* launches, double* ms, double*
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Gram utility
+// ============================================================================
+extern "C" int moto_gram(moto_ctx* c, const void* X, size_t ldx, int nx, const void* Y, size_t ldy, int ny,
+                         double* out, void* stream) {
+  if (!c || !X || !Y || !out || nx < 1 || nx > MOTO_MAX_BASIS || ny < 1 || ny > MOTO_MAX_K) return MOTO_ERR_ARG;
+  if ((nx > 1 && ldx < c->n3) || (ny > 1 && ldy < c->n3)) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  if (c->dtype == MOTO_F32)
+    P_gram<float>(c, (const float*)X, ldx, nx, (const float*)Y, ldy, ny, c->n3, out, c->part, c->counter, nullptr,
+                  0, st);
+  else
+    P_gram<double>(c, (const double*)X, ldx, nx, (const double*)Y, ldy, ny, c->n3, out, c->part, c->counter,
+                   nullptr, 0, st);
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}

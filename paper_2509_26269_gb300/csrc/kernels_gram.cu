@@ -2,14 +2,19 @@
 // n elements), the reorthogonalisation and Rayleigh-Ritz workhorse of the
 // Krylov solvers.  HBM-bound: every element of the nx + ny fields is read once.
 //
-// Pipeline: one persistent block per SM walks a contiguous range of 1 KB
-// element tiles.  Per tile, one thread issues nx + ny bulk copies
-// (cp.async.bulk, the TMA engine) of 1 KB rows into a two-stage shared-memory
-// ring completed on an mbarrier (transaction bytes).  Warp w owns rows
-// [R w, R w + R), lane l owns elements l, l + 32, ...; each lane keeps an
-// R x NY block of FP32 partial sums in registers, flushed every kFlush tiles
-// by a warp reduction into FP64 accumulators in shared memory.  Block results
-// go to FP64 partials reduced in block order by the last block.
+// Pipeline: one persistent block per SM walks a contiguous range of element
+// tiles.  The fields of X (and of Y) are equally strided, so each operand is a
+// 2D tensor (elements x fields) and one TMA instruction
+// (cp.async.bulk.tensor.2d) moves a whole [fields][KT] tile into shared
+// memory, completed on an mbarrier by transaction bytes; elements past n are
+// zero-filled by the TMA unit.  A 4-stage ring keeps ~150 KB in flight per SM.
+// Warp w owns rows [R w, R w + R), lane l owns elements l, l + 32, ...; each
+// lane keeps an R x NY block of FP32 partial sums in registers, flushed every
+// kFlush tiles by a warp reduction into FP64 accumulators in shared memory.
+// Block results go to FP64 partials reduced in block order by the last block.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "internal.h"
 
 namespace moto {
@@ -31,11 +36,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -57,71 +62,56 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
-constexpr int kStages = 2;
-constexpr int kFlush = 4;  // tiles between FP32 -> FP64 flushes
+constexpr int kStages = 4;
+constexpr int kTileBytes = 512;  // bytes of one field row in a tile
+constexpr int kFlush = 8;        // tiles between FP32 -> FP64 flushes
 
 }  // namespace
 
 template <typename T, int R, int NY>
-__global__ void __launch_bounds__(256, 1) gram_tma_kernel(const T* __restrict__ X, size_t ldx, int nx,
-                                                          const T* __restrict__ Y, size_t ldy, int ny, size_t n,
-                                                          double* out, double* part, unsigned* counter,
+__global__ void __launch_bounds__(256) gram_tma_kernel(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmY, int nx, int ny,
+                                                          size_t n, double* out, double* part, unsigned* counter,
                                                           const int* gate, int mask, int* status) {
   if (gate && (*gate & mask)) return;
-  constexpr int KT = 1024 / (int)sizeof(T);  // elements per 1 KB row chunk
-  constexpr int VEC = 16 / (int)sizeof(T);   // elements per 16 B
-  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int KT = kTileBytes / (int)sizeof(T);
+  extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ double facc[MOTO_MAX_BASIS * 8];
   __shared__ int timed_out;
   const int rows = nx + ny;
-  T* stage_buf = reinterpret_cast<T*>(smem);
-  const size_t stage_elems = (size_t)rows * KT;
+  // stage s: X tile [nx][KT] then Y tile [ny][KT]; stage stride rounded up to 1 KB
+  const size_t stage_bytes = ((size_t)rows * kTileBytes + 1023) / 1024 * 1024;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r0 = w * R;
 
   const size_t ntiles = (n + KT - 1) / KT;
   const size_t t_begin = ntiles * blockIdx.x / gridDim.x;
   const size_t t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const unsigned tx_bytes = (unsigned)rows * kTileBytes;
 
   for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) facc[i] = 0.0;
   if (threadIdx.x == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmY)) : "memory");
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     timed_out = 0;
     fence_async_shared();
   }
   __syncthreads();
 
-  // issue tile t into stage s: bulk copies for the 16 B-aligned prefix, plain
-  // loads for the ragged remainder and zeros past the end
-  auto issue = [&](size_t t, int s) {
-    const size_t e0 = t * KT;
-    const int len = (int)min((size_t)KT, n - e0);
-    const int pre = (len / VEC) * VEC;
-    T* buf = stage_buf + (size_t)s * stage_elems;
-    if (threadIdx.x == 0) {
-      fence_async_shared();
-      mbar_expect_tx(&full[s], (unsigned)(pre * sizeof(T)) * rows);
-      if (pre > 0) {
-        for (int r = 0; r < nx; ++r) bulk_g2s(buf + (size_t)r * KT, X + (size_t)r * ldx + e0, pre * sizeof(T), &full[s]);
-        for (int c = 0; c < ny; ++c)
-          bulk_g2s(buf + (size_t)(nx + c) * KT, Y + (size_t)c * ldy + e0, pre * sizeof(T), &full[s]);
-      }
-    }
-    if (pre < KT) {
-      const int tail = KT - pre;
-      for (int idx = threadIdx.x; idx < rows * tail; idx += blockDim.x) {
-        const int r = idx / tail, k = pre + (idx - r * tail);
-        T v = (T)0;
-        if (k < len) v = r < nx ? X[(size_t)r * ldx + e0 + k] : Y[(size_t)(r - nx) * ldy + e0 + k];
-        buf[(size_t)r * KT + k] = v;
-      }
-    }
+  auto issue = [&](size_t t, int s) {  // thread 0 only
+    unsigned char* buf = smem + (size_t)s * stage_bytes;
+    fence_async_shared();
+    mbar_expect_tx(&full[s], tx_bytes);
+    const int x = (int)(t * KT);
+    tma_load_2d(buf, &tmX, x, 0, &full[s]);
+    tma_load_2d(buf + (size_t)nx * kTileBytes, &tmY, x, 0, &full[s]);
   };
 
-  for (int s = 0; s < kStages; ++s)
-    if (t_begin + s < t_end) issue(t_begin + s, s);
-  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < kStages; ++s)
+      if (t_begin + s < t_end) issue(t_begin + s, s);
 
   T acc[R][NY];
 #pragma unroll
@@ -156,10 +146,10 @@ __global__ void __launch_bounds__(256, 1) gram_tma_kernel(const T* __restrict__ 
       }
       break;
     }
-    const T* buf = stage_buf + (size_t)s * stage_elems;
+    const T* buf = reinterpret_cast<const T*>(smem + (size_t)s * stage_bytes);
     const T* Ys = buf + (size_t)nx * KT;
     if (r0 < nx) {
-#pragma unroll 2
+#pragma unroll
       for (int k = lane; k < KT; k += 32) {
         T y[NY];
 #pragma unroll
@@ -173,19 +163,18 @@ __global__ void __launch_bounds__(256, 1) gram_tma_kernel(const T* __restrict__ 
           }
         }
       }
-    }
-    if (++since == kFlush) {
-      since = 0;
-      if (r0 < nx) flush();
+      if (++since == kFlush) {
+        since = 0;
+        flush();
+      }
     }
     __syncthreads();  // every warp is done with stage s
-    if (t + kStages < t_end) issue(t + kStages, s);
-    __syncthreads();  // tail fill of the new tile visible before its compute
+    if (threadIdx.x == 0 && t + kStages < t_end) issue(t + kStages, s);
   }
   if (r0 < nx) flush();
   __syncthreads();
   if (timed_out) {
-    // bounded drain: let bulk copies still in flight land before the block
+    // bounded drain: let tensor copies still in flight land before the block
     // exits (a phase that already completed returns at once)
     if (threadIdx.x == 0)
       for (int s = 0; s < kStages; ++s) {
@@ -203,36 +192,84 @@ __global__ void __launch_bounds__(256, 1) gram_tma_kernel(const T* __restrict__ 
 
 namespace {
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 2D map over `rows` fields of n elements, field stride ld elements; box
+// [rows][KT].
+template <typename T>
+bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  constexpr int KT = kTileBytes / (int)sizeof(T);
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(T))};
+  cuuint32_t box[2] = {(cuuint32_t)KT, (cuuint32_t)rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  return fn(map, dt, 2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 template <typename T, int R, int NY>
-void gram_tma_launch(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+void gram_tma_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, size_t n, double* out,
                      double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st) {
-  constexpr int KT = 1024 / (int)sizeof(T);
-  const size_t smem = (size_t)kStages * (nx + ny) * KT * sizeof(T);
+  constexpr int KT = kTileBytes / (int)sizeof(T);
+  const size_t stage_bytes = ((size_t)(nx + ny) * kTileBytes + 1023) / 1024 * 1024;
+  const size_t smem = kStages * stage_bytes;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(gram_tma_kernel<T, R, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(gram_tma_kernel<T, R, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 216 * 1024);
     attr = true;
   }
+  // as many resident blocks per SM as registers and shared memory allow: the
+  // small-row shapes are latency-bound with a single block of 8 warps
+  static int per_sm[MOTO_MAX_BASIS + 9] = {0};
+  const int key = nx + ny;
+  if (!per_sm[key]) {
+    int b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gram_tma_kernel<T, R, NY>, 256, smem) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    per_sm[key] = b < 8 ? b : 8;
+  }
   const size_t ntiles = (n + KT - 1) / KT;
-  const int grid = (int)(ntiles < (size_t)kSMs ? (ntiles > 0 ? ntiles : 1) : kSMs);
-  gram_tma_kernel<T, R, NY><<<grid, 256, smem, st>>>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask,
-                                                     status);
+  size_t want = (size_t)kSMs * per_sm[key];
+  // every context holds at least kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K
+  // partial sums; keep grid * nx * ny within that
+  const size_t cap = (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K / ((size_t)nx * ny);
+  if (want > cap) want = cap;
+  const int grid = (int)(ntiles < want ? (ntiles > 0 ? ntiles : 1) : want);
+  gram_tma_kernel<T, R, NY><<<grid, 256, smem, st>>>(mx, my, nx, ny, n, out, part, counter, gate, mask, status);
 }
 
 template <typename T, int NY>
-void gram_tma_rows(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
+void gram_tma_rows(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, size_t n, double* out,
                    double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st) {
   const int r = (nx + 7) / 8;
   if (r <= 1)
-    gram_tma_launch<T, 1, NY>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_launch<T, 1, NY>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else if (r <= 2)
-    gram_tma_launch<T, 2, NY>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_launch<T, 2, NY>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else if (r <= 4)
-    gram_tma_launch<T, 4, NY>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_launch<T, 4, NY>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else if (r <= 8)
-    gram_tma_launch<T, 8, NY>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_launch<T, 8, NY>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else
-    gram_tma_launch<T, 12, NY>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_launch<T, 12, NY>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
 }
 
 }  // namespace
@@ -240,17 +277,21 @@ void gram_tma_rows(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int n
 template <typename T>
 bool launch_gram_tma(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
                      double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st) {
-  constexpr int VEC = 16 / (int)sizeof(T);
-  const bool aligned = ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0) && (ldx % VEC == 0) && (ldy % VEC == 0);
-  if (!aligned || nx < 1 || nx > MOTO_MAX_BASIS || ny < 1 || ny > 8) return false;
+  // TMA: 16 B-aligned bases and strides, box dims <= 256, 4 stages fit in
+  // shared memory
+  const bool aligned = ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0) && ((ldx * sizeof(T)) % 16 == 0) &&
+                       ((ldy * sizeof(T)) % 16 == 0);
+  if (!aligned || nx < 1 || nx > MOTO_MAX_BASIS || ny < 1 || ny > 8 || n >= (1ull << 31)) return false;
+  CUtensorMap mx, my;
+  if (!make_map<T>(&mx, X, n, nx, ldx) || !make_map<T>(&my, Y, n, ny, ldy)) return false;
   if (ny <= 1)
-    gram_tma_rows<T, 1>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_rows<T, 1>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else if (ny <= 2)
-    gram_tma_rows<T, 2>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_rows<T, 2>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else if (ny <= 4)
-    gram_tma_rows<T, 4>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_rows<T, 4>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   else
-    gram_tma_rows<T, 8>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, status, st);
+    gram_tma_rows<T, 8>(mx, my, nx, ny, n, out, part, counter, gate, mask, status, st);
   return true;
 }
 
