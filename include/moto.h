@@ -144,8 +144,9 @@ int moto_hvp(moto_ctx* ctx, const void* m_dev, const void* s_dev, const void* v_
  *            planes before use.
  *   V_dev:   out, k Ritz vectors (3N each, consecutive), tangent, unit norm,
  *            entry of largest magnitude positive (lowest index on ties).
- *   lam_dev: out, MOTO_MAX_BASIS doubles: Ritz values ascending (unused
- *            entries set to +inf).
+ *   lam_dev: out, MOTO_MAX_BASIS doubles: the lowest Ritz values ascending
+ *            (block Lanczos: the lowest min(16, basis size); LOBPCG: k);
+ *            the other entries are set to +inf.
  *   info_dev: out, 2 ints: [iterations or steps done, device status].
  * s_dev may be NULL, in which case it is recomputed from m. */
 int moto_lowest_modes(moto_ctx* ctx, const void* m_dev, const void* s_dev,
@@ -217,7 +218,8 @@ const char* moto_status_string(int code);
  * event pair around each of the next `capacity` launches that the context's
  * solver sequences enqueue, tagged with a kernel class
  *   0 HVP, 1 Gram (skinny X^T Y), 2 field combination, 3 energy/gradient
- *   stencil, 4 single-block FP64 steps, 5 other field kernels
+ *   stencil, 4 single-block FP64 steps, 5 other field kernels, 6 the
+ *   projected-matrix eigensolver
  * and the algorithmic bytes of the launch (every field read or written once).
  * moto_profile_end synchronises, writes per class (nkinds entries each,
  * NULL to skip) the number of launches, the summed event time in ms and the

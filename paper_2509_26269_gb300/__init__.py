@@ -86,7 +86,7 @@ EXPORTED = (
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram",
 )
-PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec")
+PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig")
 
 
 # ---------------------------------------------------------------------------

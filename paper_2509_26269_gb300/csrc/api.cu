@@ -72,7 +72,7 @@ struct ProfScope {
 #define PROF(kind, bytes) ProfScope MOTO_CAT(prof_scope_, __LINE__)(c, (kind), (double)(bytes), st)
 
 // kernel classes of the profiler
-enum { kPkHvp = 0, kPkGram = 1, kPkCombine = 2, kPkStencil = 3, kPkSmall = 4, kPkVec = 5, kPkCount = 6 };
+enum { kPkHvp = 0, kPkGram = 1, kPkCombine = 2, kPkStencil = 3, kPkSmall = 4, kPkVec = 5, kPkEig = 6, kPkCount = 7 };
 
 namespace {
 // Profiled launch wrappers: same arguments as the launchers, plus the context.
@@ -141,6 +141,42 @@ void P_retract(moto_ctx* c, T* m, T* d, const DevState* dst, int N, const int* g
   PROF(kPkVec, 12.0 * N * sizeof(T));
   launch_retract<T>(m, d, dst, N, gate, mask, st);
 }
+// Streaming reorthogonalisation step (see internal.h, modes 0-3) with the
+// combine + Gram fallback for fields that break the TMA alignment rules.
+template <typename T>
+void P_tile(moto_ctx* c, int mode, const T* X, int nx, T* Y, int ny, const double* C, T* Yout, double* out,
+            const int* gate, int mask, cudaStream_t st) {
+  const size_t ld = c->ld;
+  const int N = c->N;
+  bool done;
+  {
+    const double f = 3.0 * N * sizeof(T);
+    const double fields = (mode == 0) ? nx + ny : (mode == 3 ? nx + ny : nx + 2.0 * ny);
+    PROF(kPkGram, f * fields);
+    set_gram_status(&c->st->status);
+    done = launch_tile<T>(mode, X, ld, nx, Y, ld, ny, c->n3, C, Yout, ld, out, c->part, c->counter, gate, mask,
+                          &c->st->status, st);
+  }
+  if (done) return;
+  switch (mode) {
+    case 0:
+      P_gram<T>(c, X, ld, nx, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
+      break;
+    case 1:
+      P_combine<T>(c, X, ld, nx, nullptr, C, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate, mask, st);
+      P_gram<T>(c, X, ld, nx, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
+      break;
+    case 2:
+      P_combine<T>(c, X, ld, nx, nullptr, C, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate, mask, st);
+      P_gram<T>(c, Y, ld, ny, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
+      break;
+    default:
+      P_combine<T>(c, X, ld, nx, nullptr, C, ny, nullptr, 0, 0.0, 1.0, Yout, ld, nullptr, N, gate, mask, st);
+      P_gram<T>(c, Yout, ld, ny, Yout, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
+      break;
+  }
+}
+
 #define SMALL_WRAP(name)                                                 \
   template <typename... A>                                               \
   void P_##name(moto_ctx* c, A... args) {                                \
@@ -156,7 +192,13 @@ SMALL_WRAP(lob_check)
 SMALL_WRAP(diag)
 SMALL_WRAP(lbfgs_solve)
 SMALL_WRAP(saddle_test)
+SMALL_WRAP(arnoldi_diag)
 #undef SMALL_WRAP
+void P_tridiag_eig(moto_ctx* c, const double* T, int ldT, int band, double* theta, double* Y, int k, DevState* dst,
+                   cudaStream_t st) {
+  PROF(kPkEig, 0.0);
+  launch_tridiag_eig(T, ldT, band, c->dtype == MOTO_F64 ? 1 : 0, theta, Y, k, dst, st);
+}
 }  // namespace
 
 namespace {
@@ -167,7 +209,8 @@ constexpr size_t kTheta = kT + MOTO_MAX_BASIS * MOTO_MAX_BASIS;    // MAX_BASIS
 constexpr size_t kY = kTheta + MOTO_MAX_BASIS;                     // MAX_BASIS * MAX_K
 constexpr size_t kC = kY + MOTO_MAX_BASIS * MOTO_MAX_K;            // MAX_BASIS * MAX_K
 constexpr size_t kC3 = kC + MOTO_MAX_BASIS * MOTO_MAX_K;           // 2K * K
-constexpr size_t kA = kC3 + 2 * MOTO_MAX_K * MOTO_MAX_K;           // K*K
+constexpr size_t kC2 = kC3 + 2 * MOTO_MAX_K * MOTO_MAX_K;          // MAX_BASIS * MAX_K (second CGS pass)
+constexpr size_t kA = kC2 + MOTO_MAX_BASIS * MOTO_MAX_K;           // K*K
 constexpr size_t kG = kA + MOTO_MAX_K * MOTO_MAX_K;                // K*K
 constexpr size_t kRinv = kG + MOTO_MAX_K * MOTO_MAX_K;             // K*K
 constexpr size_t kRacc = kRinv + MOTO_MAX_K * MOTO_MAX_K;          // K*K
@@ -281,35 +324,32 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   P_project<T>(c, m, v0, ld0, W, ld, b, N, gate, kGateDone, st);
   P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
   P_cholqr(c, D + kG, b, 0, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-  P_combine<T>(c, W, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Wt, ld, nullptr, N, gate, mk, st);
-  P_gram<T>(c, Wt, ld, b, Wt, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+  P_tile<T>(c, 3, W, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
   P_cholqr(c, D + kG, b, 1, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
   P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q, ld, nullptr, N, gate, mk, st);
+  // Block Lanczos in CGS2 form: W = H Q_j; G1 = Q^T W gives T(j, j);
+  // W <- W - Q G1 with G2 = Q^T W in the same pass; W <- W - Q G2 with
+  // S = W^T W in the same pass; Cholesky QR of W (twice) gives Q_{j+1} and
+  // R = T(j+1, j); the new block is re-projected on the tangent planes in its
+  // final combination (a small beta would otherwise magnify rounding-level
+  // normal components step after step).  The basis Q is read three times per
+  // step.
   for (int j = 0; j < steps; ++j) {
     T* Qj = Q + (size_t)j * b * ld;
-    P_hvp<T>(c, c->md, m, s, Qj, ld, W, ld, b, gate, mk, st);
-    P_gram<T>(c, Qj, ld, b, W, ld, b, n3, D + kA, c->part, c->counter, gate, mk, st);
-    P_lanczos_coeffs(c, D + kA, b, j, D + kT, kLd, D + kC3, c->st, st);
-    const T* X3 = (j > 0) ? Q + (size_t)(j - 1) * b * ld : Qj;
-    // three-term recurrence, re-projected on the tangent planes: rounding-level
-    // normal components would otherwise grow by |alpha| / beta every step
-    P_combine<T>(c, X3, ld, (j > 0 ? 2 : 1) * b, nullptr, D + kC3, b, W, ld, 1.0, -1.0, W, ld, m, N, gate, mk,
-                      st);
     const int nq = (j + 1) * b;
-    for (int pass = 0; pass < 2; ++pass) {
-      P_gram<T>(c, Q, ld, nq, W, ld, b, n3, D + kC, c->part, c->counter, gate, mk, st);
-      P_combine<T>(c, Q, ld, nq, nullptr, D + kC, b, W, ld, 1.0, -1.0, W, ld, nullptr, N, gate, mk, st);
-    }
+    P_hvp<T>(c, c->md, m, s, Qj, ld, W, ld, b, gate, mk, st);
+    P_tile<T>(c, 0, Q, nq, W, b, nullptr, nullptr, D + kC, gate, mk, st);
+    P_arnoldi_diag(c, D + kC, b, j, D + kT, kLd, c->st, st);
     if (j == steps - 1) break;
-    P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_tile<T>(c, 1, Q, nq, W, b, D + kC, W, D + kC2, gate, mk, st);
+    P_tile<T>(c, 2, Q, nq, W, b, D + kC2, W, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-    P_combine<T>(c, W, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Wt, ld, nullptr, N, gate, mk, st);
-    P_gram<T>(c, Wt, ld, b, Wt, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
+    P_tile<T>(c, 3, W, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 1, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-    P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q + (size_t)(j + 1) * b * ld, ld,
-                      nullptr, N, gate, mk, st);
+    P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q + (size_t)(j + 1) * b * ld, ld, m, N,
+                 gate, mk, st);
   }
-  P_small_eig(c, D + kT, kLd, lam, D + kY, nout, c->st, st);
+  P_tridiag_eig(c, D + kT, kLd, b, lam, D + kY, nout, c->st, st);
   P_combine<T>(c, Q, ld, b * steps, &c->st->nT, D + kY, nout, nullptr, 0, 0.0, 1.0, V, ldv, nullptr, N,
                     gate, kGateDone, st);
   P_finish<T>(c, m, V, ldv, nout, N, c->part, c->counter, D + kScal, gate, kGateDone, st);
@@ -347,7 +387,10 @@ void lobpcg(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0, int k,
   double* D = c->dsm;
   int* gate = &c->st->gate;
   const int mk = kGateKrylov | kGateDone;
-  const double drop = (c->dtype == MOTO_F64) ? 1e-12 : 1e-8;
+  // SVQB drop level: a kept direction with scaled Gram eigenvalue w magnifies
+  // the rounding of AS (~eps |H|) by 1/w in the projected matrix, so FP32
+  // fields keep only directions with w > 1e-3
+  const double drop = (c->dtype == MOTO_F64) ? 1e-12 : 1e-3;
   T* base = static_cast<T*>(c->lob);
   T* Wt = static_cast<T*>(c->Wt);
   auto SET = [&](int a) { return base + (size_t)a * 6 * MOTO_MAX_K * ld; };

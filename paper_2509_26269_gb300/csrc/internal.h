@@ -40,6 +40,10 @@ void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part
 template <typename T>
 void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec,
                 const int* gate, int mask, cudaStream_t st);
+// register-blocked column-strip HVP (kernels_hvp.cu); launch_hvp uses it
+template <typename T>
+void launch_hvp_strip(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
+                      int nvec, const int* gate, int mask, cudaStream_t st);
 template <typename T>
 void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st);
 
@@ -51,12 +55,19 @@ template <typename T>
 void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
                  double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st);
 int gram_blocks();
-// TMA-pipelined Gram (kernels_gram.cu); returns false when the fields are not
-// 16-byte aligned or the shape is out of range (the caller then uses the
-// plain kernel).
+// Streaming reorthogonalisation kernels (kernels_tile.cu), modes
+//   0: out = X^T Y;  1: Y <- Y - X C, out = X^T Y;  2: Y <- Y - X C, out = Y^T Y;
+//   3: Yout <- X C, out = Yout^T Yout
+// over n elements (fields X at stride ldx, Y at ldy; updated fields go to Yout
+// at stride ldo, Yout == Y for modes 1 and 2).  Returns false (nothing
+// launched) when a base address or stride breaks the TMA alignment rules; the
+// caller then uses combine + the plain Gram kernel.
 template <typename T>
-bool launch_gram_tma(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
-                     double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st);
+bool launch_tile(int mode, const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, const double* C,
+                 T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate, int mask,
+                 int* status, cudaStream_t st);
+// Block Lanczos (CGS2 form): T(j, j) = sym of the Q_j rows of G1 = Q_all^T H Q_j.
+void launch_arnoldi_diag(const double* G1, int b, int j, double* T, int ldT, DevState* st, cudaStream_t s);
 // status word of the last context that set one (timeouts of bounded waits)
 void set_gram_status(int* status);
 
@@ -96,6 +107,10 @@ void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, doub
 // T (nT read from st->nT, <= 96): theta ascending (MOTO_MAX_BASIS entries,
 // +inf padded) and the first k eigenvectors as an (nT x k) coefficient matrix Y.
 void launch_small_eig(const double* T, int ldT, double* theta, double* Y, int k, DevState* st, cudaStream_t s);
+// Same contract, by Householder tridiagonalisation (skipped for band 1),
+// Sturm bisection and inverse iteration (kernels_eig.cu).
+void launch_tridiag_eig(const double* T, int ldT, int band, int fp64, double* theta, double* Y, int k, DevState* st,
+                        cudaStream_t s);
 
 // LOBPCG small steps (see kernels_vec.cu)
 void launch_lob_rr(const double* Gb, const double* Mb, int k, int nb, double drop, double* Cx, double* Cp,

@@ -1,0 +1,344 @@
+// Eigenpairs of the projected block-Lanczos matrix T (n <= 96, symmetric, band
+// width b) on one block.  GB300 executes dependent FP64 chains slowly, so FP64
+// is kept where it buys accuracy and FP32 does the search:
+//   1. Householder reduction to tridiagonal form Q^T T Q = tridiag(d, e) in the
+//      context precision R (skipped for b = 1, where T is tridiagonal);
+//   2. the lowest 16 eigenvalues located by FP32 bisection on the Sturm
+//      sequence of the characteristic polynomials
+//      p_r = (d_r - x) p_{r-1} - e_{r-1}^2 p_{r-2} (sign changes count the
+//      eigenvalues below x; rescaled to stay in range), one lane each;
+//   3. each located eigenvalue refined by FP64 inverse iteration on the
+//      tridiagonal matrix (LU with partial pivoting, three sweeps; vectors
+//      orthogonalised within clusters of close eigenvalues) and its FP64
+//      Rayleigh quotient;
+//   4. back-transformation of the k lowest eigenvectors (precision R) and, for
+//      them, FP64 Rayleigh quotients with the original T.
+// Golub & Van Loan, Matrix Computations, sec. 8.3 (tridiagonalisation), 8.4
+// (bisection), 8.2 (inverse iteration, Rayleigh quotient).
+#include "internal.h"
+
+namespace moto {
+
+namespace {
+constexpr int kN = MOTO_MAX_BASIS;
+constexpr int kLdA = kN + 1;
+constexpr int kNE = 16;  // lowest Ritz values computed; higher entries of theta stay +inf
+}  // namespace
+
+template <typename R>
+__global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restrict__ Tm, int ldT, int band,
+                                                          double* theta, double* Y, int k, DevState* st) {
+  if (st->gate & kGateDone) return;
+  extern __shared__ double sm[];
+  double* d = sm;                              // diagonal
+  double* e = d + kN;                          // off-diagonal
+  double* lam = e + kN;                        // eigenvalues
+  double* vec = lam + kN;                      // kNE x n eigenvectors (tridiagonal basis, then T basis)
+  R* A = reinterpret_cast<R*>(vec + (size_t)kNE * kN);  // n x (n+1), Householder vectors below the subdiagonal
+  R* beta = A + (size_t)kN * kLdA;             // reflector scales
+  R* pv = beta + kN;                           // work vector p / w
+  __shared__ double red[32];
+  __shared__ float shift[kNE];
+  __shared__ R sh_alpha, sh_beta, sh_K;
+  const int n = st->nT;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int wp = tid >> 5, ln = tid & 31, nw = nth >> 5;
+
+  for (int i = tid; i < MOTO_MAX_BASIS; i += nth) theta[i] = 1.0 / 0.0;
+  if (n <= 0) return;
+  for (int idx = tid; idx < n * n; idx += nth) {
+    const int r = idx / n, c = idx - r * n;
+    A[r * kLdA + c] = (R)(0.5 * (Tm[(size_t)r * ldT + c] + Tm[(size_t)c * ldT + r]));
+  }
+  __syncthreads();
+
+  // ---- 1. tridiagonalisation (precision R) -------------------------------------
+  if (band > 1) {
+    for (int j = 0; j + 2 < n; ++j) {
+      const int m0 = j + 1;
+      double s = 0.0;
+      for (int r = m0 + tid; r < n; r += nth) s += (double)A[r * kLdA + j] * A[r * kLdA + j];
+      double v1[1] = {s};
+      block_sum<1>(v1, red);
+      if (tid == 0) {
+        const R norm2 = (R)v1[0];
+        const R x0 = A[m0 * kLdA + j];
+        if (norm2 - x0 * x0 <= (R)1e-30 * (norm2 + (R)1e-30)) {
+          sh_beta = 0;
+          sh_alpha = x0;
+        } else {
+          const R alpha = -copysign(sqrt(norm2), x0);
+          const R v0 = x0 - alpha;
+          const R vtv = v0 * v0 + (norm2 - x0 * x0);
+          sh_alpha = alpha;
+          sh_beta = (R)2 / vtv;
+          A[m0 * kLdA + j] = v0;
+        }
+      }
+      __syncthreads();
+      const R b = sh_beta;
+      if (tid == 0) {
+        e[j] = (double)sh_alpha;
+        beta[j] = b;
+      }
+      if (b == (R)0) {
+        __syncthreads();
+        continue;
+      }
+      for (int r = m0 + wp; r < n; r += nw) {  // p = b A22 v, a warp per row
+        R a = 0;
+        for (int c2 = m0 + ln; c2 < n; c2 += 32) a += A[r * kLdA + c2] * A[c2 * kLdA + j];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (ln == 0) pv[r] = b * a;
+      }
+      __syncthreads();
+      double q = 0.0;
+      for (int r = m0 + tid; r < n; r += nth) q += (double)A[r * kLdA + j] * pv[r];
+      double v2[1] = {q};
+      block_sum<1>(v2, red);
+      if (tid == 0) sh_K = (R)(0.5 * (double)b * v2[0]);
+      __syncthreads();
+      const R K = sh_K;
+      for (int r = m0 + tid; r < n; r += nth) pv[r] -= K * A[r * kLdA + j];  // w = p - K v
+      __syncthreads();
+      const int m = n - m0;
+      for (int idx = tid; idx < m * m; idx += nth) {
+        const int r = m0 + idx / m, c2 = m0 + idx % m;
+        A[r * kLdA + c2] -= A[r * kLdA + j] * pv[c2] + pv[r] * A[c2 * kLdA + j];
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      for (int i = 0; i < n; ++i) d[i] = (double)A[i * kLdA + i];
+      if (n >= 2) e[n - 2] = (double)A[(n - 1) * kLdA + (n - 2)];
+      e[n - 1] = 0.0;
+      for (int i = (n >= 2 ? n - 2 : 0); i < n; ++i) beta[i] = 0;
+    }
+  } else {
+    for (int i = tid; i < n; i += nth) {
+      d[i] = 0.5 * (Tm[(size_t)i * ldT + i] + Tm[(size_t)i * ldT + i]);
+      e[i] = (i + 1 < n) ? 0.5 * (Tm[(size_t)(i + 1) * ldT + i] + Tm[(size_t)i * ldT + i + 1]) : 0.0;
+      beta[i] = 0;
+    }
+  }
+  __syncthreads();
+
+  // ---- 2. FP32 bisection for the lowest ne eigenvalues --------------------------
+  double tn = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+    tn = fmax(tn, fabs(d[i]) + r);
+  }
+  tn = fmax(tn, 1e-300);
+  const int ne = n < kNE ? n : kNE;
+  if (tid < ne) {
+    const int i = tid;
+    float lo = 1e30f, hi = -1e30f;
+    for (int r = 0; r < n; ++r) {
+      const float rr = (float)((r > 0 ? fabs(e[r - 1]) : 0.0) + (r + 1 < n ? fabs(e[r]) : 0.0));
+      lo = fminf(lo, (float)d[r] - rr);
+      hi = fmaxf(hi, (float)d[r] + rr);
+    }
+    lo -= 1e-6f * (float)tn;
+    hi += 1e-6f * (float)tn;
+    float a = lo, bb = hi;
+    for (int itn = 0; itn < 64 && (bb - a) > 4e-7f * fmaxf(fabsf(a), fabsf(bb)) + 1e-30f; ++itn) {
+      const float x = 0.5f * (a + bb);
+      float pm = 1.f, p = (float)d[0] - x;
+      if (p == 0.f) p = -1e-30f;
+      int cnt = (p < 0.f) ? 1 : 0;
+      for (int r = 1; r < n; ++r) {
+        const float er = (float)e[r - 1];
+        float pn = ((float)d[r] - x) * p - er * er * pm;
+        if (pn == 0.f) pn = -copysignf(1e-30f, p);
+        cnt += ((pn < 0.f) != (p < 0.f)) ? 1 : 0;
+        pm = p;
+        p = pn;
+        const float ap = fabsf(p);
+        if (ap > 1e18f || (ap < 1e-18f && fabsf(pm) < 1e-18f)) {
+          const float sc = ap > 1e18f ? 1e-18f : 1e18f;
+          p *= sc;
+          pm *= sc;
+        }
+      }
+      if (cnt > i)
+        bb = x;
+      else
+        a = x;
+    }
+    shift[i] = 0.5f * (a + bb);
+  }
+  __syncthreads();
+
+  // ---- 3. FP64 inverse iteration + Rayleigh quotient, one vector per warp lane 0
+  for (int i = wp; i < ne; i += nw) {
+    if (ln != 0) continue;
+    double dg[kN], su[kN], s2[kN], lm[kN], x[kN];
+    bool pivot[kN];
+    const double sigma = (double)shift[i];
+    const double tiny = 1e-14 * tn;
+    for (int r = 0; r < n; ++r) {
+      dg[r] = d[r] - sigma;
+      su[r] = (r + 1 < n) ? e[r] : 0.0;
+      s2[r] = 0.0;
+    }
+    for (int r = 0; r + 1 < n; ++r) {
+      const double sub = e[r];
+      if (fabs(dg[r]) >= fabs(sub)) {
+        pivot[r] = false;
+        const double l = (dg[r] != 0.0) ? sub / dg[r] : 0.0;
+        lm[r] = l;
+        dg[r + 1] -= l * su[r];
+      } else {
+        pivot[r] = true;
+        const double l = dg[r] / sub;
+        lm[r] = l;
+        const double d1 = dg[r + 1], u1 = su[r + 1], old_su = su[r];
+        dg[r] = sub;
+        su[r] = d1;
+        s2[r] = u1;
+        dg[r + 1] = old_su - l * d1;
+        su[r + 1] = -l * u1;
+      }
+    }
+    for (int r = 0; r < n; ++r)
+      if (fabs(dg[r]) < tiny) dg[r] = (dg[r] < 0.0 ? -tiny : tiny);
+    for (int r = 0; r < n; ++r) x[r] = 1.0 + 0.5 * sin(0.7 * r + 0.3 * i);
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      for (int r = 0; r + 1 < n; ++r) {
+        if (pivot[r]) {
+          const double t = x[r];
+          x[r] = x[r + 1];
+          x[r + 1] = t - lm[r] * x[r + 1];
+        } else {
+          x[r + 1] -= lm[r] * x[r];
+        }
+      }
+      for (int r = n - 1; r >= 0; --r) {
+        double a = x[r];
+        if (r + 1 < n) a -= su[r] * x[r + 1];
+        if (r + 2 < n) a -= s2[r] * x[r + 2];
+        x[r] = a / dg[r];
+      }
+      double nn = 0.0;
+      for (int r = 0; r < n; ++r) nn += x[r] * x[r];
+      nn = 1.0 / sqrt(nn);
+      for (int r = 0; r < n; ++r) x[r] *= nn;
+    }
+    for (int r = 0; r < n; ++r) vec[i * kN + r] = x[r];
+  }
+  __syncthreads();
+  // clusters: orthogonalise (modified Gram-Schmidt), then Rayleigh quotients
+  if (tid == 0) {
+    for (int i = 1; i < ne; ++i) {
+      bool touched = false;
+      for (int j = 0; j < i; ++j) {
+        if (fabs((double)shift[i] - (double)shift[j]) > 1e-5 * tn) continue;
+        double dot = 0.0;
+        for (int r = 0; r < n; ++r) dot += vec[i * kN + r] * vec[j * kN + r];
+        for (int r = 0; r < n; ++r) vec[i * kN + r] -= dot * vec[j * kN + r];
+        touched = true;
+      }
+      if (touched) {
+        double nn = 0.0;
+        for (int r = 0; r < n; ++r) nn += vec[i * kN + r] * vec[i * kN + r];
+        nn = 1.0 / sqrt(nn);
+        for (int r = 0; r < n; ++r) vec[i * kN + r] *= nn;
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = wp; i < ne; i += nw) {  // lambda_i = x^T tridiag x, a warp per vector
+    const double* x = vec + i * kN;
+    double a = 0.0;
+    for (int r = ln; r < n; r += 32) {
+      double t = d[r] * x[r];
+      if (r > 0) t += e[r - 1] * x[r - 1];
+      if (r + 1 < n) t += e[r] * x[r + 1];
+      a += x[r] * t;
+    }
+    a = warp_sum(a);
+    if (ln == 0) lam[i] = a;
+  }
+  __syncthreads();
+  // order (inverse iteration keeps the bisection order except inside clusters)
+  if (tid == 0) {
+    for (int i = 1; i < ne; ++i)
+      for (int j = i; j > 0 && lam[j] < lam[j - 1]; --j) {
+        const double t = lam[j];
+        lam[j] = lam[j - 1];
+        lam[j - 1] = t;
+        for (int r = 0; r < n; ++r) {
+          const double u = vec[j * kN + r];
+          vec[j * kN + r] = vec[(j - 1) * kN + r];
+          vec[(j - 1) * kN + r] = u;
+        }
+      }
+  }
+  __syncthreads();
+
+  // ---- 4. back-transformation x <- H_0 ... H_{n-3} x, then FP64 Rayleigh
+  //         quotients with the original T for the k vectors -----------------------
+  int kk = k < ne ? k : ne;
+  if (band > 1) {
+    for (int j = n - 3; j >= 0; --j) {
+      const R b = beta[j];
+      if (b == (R)0) continue;
+      const int m0 = j + 1;
+      for (int vi = wp; vi < kk; vi += nw) {
+        double* x = vec + vi * kN;
+        double dot = 0.0;
+        for (int r = m0 + ln; r < n; r += 32) dot += (double)A[r * kLdA + j] * x[r];
+        dot = warp_sum(dot) * (double)b;
+        for (int r = m0 + ln; r < n; r += 32) x[r] -= dot * (double)A[r * kLdA + j];
+      }
+      __syncthreads();
+    }
+    for (int vi = wp; vi < kk; vi += nw) {
+      const double* x = vec + vi * kN;
+      double a = 0.0, nn = 0.0;
+      for (int r = ln; r < n; r += 32) {
+        double t = 0.0;
+        const int c0 = r - band < 0 ? 0 : r - band, c1 = r + band + 1 > n ? n : r + band + 1;
+        for (int c2 = c0; c2 < c1; ++c2) t += 0.5 * (Tm[(size_t)r * ldT + c2] + Tm[(size_t)c2 * ldT + r]) * x[c2];
+        a += x[r] * t;
+        nn += x[r] * x[r];
+      }
+      a = warp_sum(a);
+      nn = warp_sum(nn);
+      if (ln == 0) lam[vi] = a / nn;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < ne; i += nth) theta[i] = lam[i];
+  for (int idx = tid; idx < n * kk; idx += nth) {
+    const int r = idx / kk, i = idx - r * kk;
+    Y[(size_t)r * k + i] = vec[i * kN + r];
+  }
+}
+
+void launch_tridiag_eig(const double* T, int ldT, int band, int fp64, double* theta, double* Y, int k, DevState* st,
+                        cudaStream_t s) {
+  auto bytes = [](size_t rsz) {
+    return (3 * kN + (size_t)kNE * kN) * sizeof(double) + ((size_t)kN * kLdA + 2 * kN) * rsz;
+  };
+  if (fp64) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tridiag_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes(sizeof(double)));
+      attr = true;
+    }
+    tridiag_eig_kernel<double><<<1, 256, bytes(sizeof(double)), s>>>(T, ldT, band, theta, Y, k, st);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(tridiag_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bytes(sizeof(float)));
+      attr = true;
+    }
+    tridiag_eig_kernel<float><<<1, 256, bytes(sizeof(float)), s>>>(T, ldT, band, theta, Y, k, st);
+  }
+}
+
+}  // namespace moto

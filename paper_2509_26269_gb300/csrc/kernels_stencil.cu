@@ -240,7 +240,7 @@ void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part
 template <typename T>
 void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec,
                 const int* gate, int mask, cudaStream_t st) {
-  hvp_kernel<T><<<tile_grid(md), kThreads, 0, st>>>(md, m, s, V, ldv, HV, ldhv, nvec, gate, mask);
+  launch_hvp_strip<T>(md, m, s, V, ldv, HV, ldhv, nvec, gate, mask, st);
 }
 
 template <typename T>
