@@ -142,10 +142,11 @@ void P_retract(moto_ctx* c, T* m, T* d, const DevState* dst, int N, const int* g
   launch_retract<T>(m, d, dst, N, gate, mask, st);
 }
 // Streaming reorthogonalisation step (see internal.h, modes 0-3) with the
-// combine + Gram fallback for fields that break the TMA alignment rules.
+// combine + Gram fallback for fields that break the TMA alignment rules.  In
+// mode 1 only X rows u0 .. u0 + nu - 1 take part in the update.
 template <typename T>
-void P_tile(moto_ctx* c, int mode, const T* X, int nx, T* Y, int ny, const double* C, T* Yout, double* out,
-            const int* gate, int mask, cudaStream_t st) {
+void P_tile(moto_ctx* c, int mode, const T* X, int nx, int u0, int nu, T* Y, int ny, const double* C, T* Yout,
+            double* out, const int* gate, int mask, cudaStream_t st) {
   const size_t ld = c->ld;
   const int N = c->N;
   bool done;
@@ -154,8 +155,8 @@ void P_tile(moto_ctx* c, int mode, const T* X, int nx, T* Y, int ny, const doubl
     const double fields = (mode == 0) ? nx + ny : (mode == 3 ? nx + ny : nx + 2.0 * ny);
     PROF(kPkGram, f * fields);
     set_gram_status(&c->st->status);
-    done = launch_tile<T>(mode, X, ld, nx, Y, ld, ny, c->n3, C, Yout, ld, out, c->part, c->counter, gate, mask,
-                          &c->st->status, st);
+    done = launch_tile<T>(mode, X, ld, nx, u0, nu, Y, ld, ny, c->n3, C, Yout, ld, out, c->part, c->counter, gate,
+                          mask, &c->st->status, st);
   }
   if (done) return;
   switch (mode) {
@@ -163,7 +164,8 @@ void P_tile(moto_ctx* c, int mode, const T* X, int nx, T* Y, int ny, const doubl
       P_gram<T>(c, X, ld, nx, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
       break;
     case 1:
-      P_combine<T>(c, X, ld, nx, nullptr, C, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate, mask, st);
+      P_combine<T>(c, X + (size_t)u0 * ld, ld, nu, nullptr, C, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate, mask,
+                   st);
       P_gram<T>(c, X, ld, nx, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
       break;
     case 2:
@@ -324,27 +326,30 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   P_project<T>(c, m, v0, ld0, W, ld, b, N, gate, kGateDone, st);
   P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
   P_cholqr(c, D + kG, b, 0, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-  P_tile<T>(c, 3, W, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
+  P_tile<T>(c, 3, W, b, 0, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
   P_cholqr(c, D + kG, b, 1, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
   P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q, ld, nullptr, N, gate, mk, st);
-  // Block Lanczos in CGS2 form: W = H Q_j; G1 = Q^T W gives T(j, j);
-  // W <- W - Q G1 with G2 = Q^T W in the same pass; W <- W - Q G2 with
-  // S = W^T W in the same pass; Cholesky QR of W (twice) gives Q_{j+1} and
-  // R = T(j+1, j); the new block is re-projected on the tangent planes in its
-  // final combination (a small beta would otherwise magnify rounding-level
-  // normal components step after step).  The basis Q is read three times per
-  // step.
+  // Block Lanczos step j, reorthogonalised twice: W = H Q_j; a local pass
+  // against the last two blocks (G1 = [Q_{j-1} Q_j]^T W, whose Q_j rows give
+  // T(j, j); W <- W - [Q_{j-1} Q_j] G1, with G2 = Q^T W over the whole basis in
+  // the same sweep); a full pass W <- W - Q G2 with S = W^T W in the same
+  // sweep; Cholesky QR of W (twice) gives Q_{j+1} and R = T(j+1, j).  The new
+  // block is re-projected on the tangent planes in its final combination (a
+  // small beta would otherwise magnify rounding-level normal components step
+  // after step).  The basis is read twice per step.
   for (int j = 0; j < steps; ++j) {
     T* Qj = Q + (size_t)j * b * ld;
     const int nq = (j + 1) * b;
+    const int jl = j > 0 ? 1 : 0;  // local block rows: Q_{j-1} (if any), Q_j
+    T* Qloc = Q + (size_t)(j - jl) * b * ld;
     P_hvp<T>(c, c->md, m, s, Qj, ld, W, ld, b, gate, mk, st);
-    P_tile<T>(c, 0, Q, nq, W, b, nullptr, nullptr, D + kC, gate, mk, st);
-    P_arnoldi_diag(c, D + kC, b, j, D + kT, kLd, c->st, st);
+    P_tile<T>(c, 0, Qloc, (jl + 1) * b, 0, 0, W, b, nullptr, nullptr, D + kC, gate, mk, st);
+    P_arnoldi_diag(c, D + kC, b, jl, j, D + kT, kLd, c->st, st);
     if (j == steps - 1) break;
-    P_tile<T>(c, 1, Q, nq, W, b, D + kC, W, D + kC2, gate, mk, st);
-    P_tile<T>(c, 2, Q, nq, W, b, D + kC2, W, D + kG, gate, mk, st);
+    P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC, W, D + kC2, gate, mk, st);
+    P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-    P_tile<T>(c, 3, W, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
+    P_tile<T>(c, 3, W, b, 0, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 1, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
     P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q + (size_t)(j + 1) * b * ld, ld, m, N,
                  gate, mk, st);

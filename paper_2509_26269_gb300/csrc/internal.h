@@ -56,18 +56,20 @@ void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny,
                  double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st);
 int gram_blocks();
 // Streaming reorthogonalisation kernels (kernels_tile.cu), modes
-//   0: out = X^T Y;  1: Y <- Y - X C, out = X^T Y;  2: Y <- Y - X C, out = Y^T Y;
-//   3: Yout <- X C, out = Yout^T Yout
+//   0: out = X^T Y;  1: Y <- Y - X[u0, u0 + nu) C, out = X^T Y;
+//   2: Y <- Y - X C, out = Y^T Y;  3: Yout <- X C, out = Yout^T Yout
 // over n elements (fields X at stride ldx, Y at ldy; updated fields go to Yout
-// at stride ldo, Yout == Y for modes 1 and 2).  Returns false (nothing
-// launched) when a base address or stride breaks the TMA alignment rules; the
-// caller then uses combine + the plain Gram kernel.
+// at stride ldo, Yout == Y for modes 1 and 2; C is nu x ny in mode 1, nx x ny
+// in modes 2 and 3).  Returns false (nothing launched) when a base address or
+// stride breaks the TMA alignment rules; the caller then uses combine + the
+// plain Gram kernel.
 template <typename T>
-bool launch_tile(int mode, const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, const double* C,
-                 T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate, int mask,
-                 int* status, cudaStream_t st);
-// Block Lanczos (CGS2 form): T(j, j) = sym of the Q_j rows of G1 = Q_all^T H Q_j.
-void launch_arnoldi_diag(const double* G1, int b, int j, double* T, int ldT, DevState* st, cudaStream_t s);
+bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
+                 const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
+                 int mask, int* status, cudaStream_t st);
+// Block Lanczos: T(j, j) = sym of block row jr of the local Gram G1 (b x b
+// blocks, row jr holding Q_j^T H Q_j).
+void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int ldT, DevState* st, cudaStream_t s);
 // status word of the last context that set one (timeouts of bounded waits)
 void set_gram_status(int* status);
 

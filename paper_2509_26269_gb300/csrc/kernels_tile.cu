@@ -1,27 +1,40 @@
 // Streaming kernels of the block-Krylov reorthogonalisation over element
 // tiles.  The fields of X (nx <= 96) and of Y (ny <= 8) are equally strided, so
-// each operand is a 2D tensor [fields][n]; one TMA instruction
-// (cp.async.bulk.tensor.2d) moves a [fields][KT] tile of 512-byte rows into
-// shared memory, completed on an mbarrier by transaction bytes; the TMA unit
-// zero-fills elements past n.  Modes:
+// each operand is a 2D tensor [fields][n].  A tile is TB bytes (256 or 512) of
+// every field, moved by one TMA load per operand (cp.async.bulk.tensor.2d,
+// box [fields][TB]) into a dense [fields][TB] shared-memory stage; the TMA
+// unit zero-fills elements past n.  Rows of at least 256 contiguous bytes keep
+// the tensor copies at full HBM rate (128-byte rows, as a swizzled layout
+// would need, stream at about two thirds of it), so bank conflicts are avoided
+// in the reads instead: in the Gram phase lane l starts its walk over the
+// 16-byte chunks of a row at chunk (l & 7), so the eight lanes of a quarter
+// warp always touch eight different bank groups.  Modes:
 //
 //   0 (kGram)    : out = X^T Y
-//   1 (kUpdGram) : Y <- Y - X C, then out = X^T Y      (CGS pass + next Gram)
-//   2 (kUpdSelf) : Y <- Y - X C, then out = Y^T Y      (CGS pass + Cholesky Gram)
-//   3 (kMulSelf) : Z <- X C,     then out = Z^T Z      (Cholesky QR step)
+//   1 (kUpdGram) : Y <- Y - X[u0, u0 + nu) C, then out = X^T Y
+//   2 (kUpdSelf) : Y <- Y - X C, then out = Y^T Y
+//   3 (kMulSelf) : Z <- X C,     then out = Z^T Z
 //
-// C is nx x ny (FP64 in global memory, FP32/FP64 in shared memory).  Updated
-// fields are written back with coalesced stores and reused from shared memory
-// by the Gram phase: every field crosses HBM once per launch.
+// C is nu x ny (FP64 in global memory, T in shared memory).  Updated fields are
+// written back with coalesced vector stores; in mode 1 they also replace Y in
+// the staged tile, from where the Gram phase reads them, so every field crosses
+// HBM once per launch.
 //
-// 512 threads (16 warps).  Update phase: thread -> (element e, 4 columns),
-// loop over the nx rows with one shared load of X and one broadcast 16-byte
-// load of C per row.  Gram phase: warp w owns R rows of A (X, or Y itself for
-// modes 2/3), lane l owns 16 contiguous bytes of every row (one 16-byte shared
-// load per row and column field), R x NY FP32 partial sums per lane flushed
-// every kFlush tiles by a warp reduction into FP64 (all FP64 for double).
-// Block partials in FP64 are reduced in block order by the last block.  A
-// 3-stage TMA ring with bounded waits (timeouts are reported, never hung).
+// Warp pairs per tile: one producer warp keeps a ring of up to 32 stages
+// full; each of the kPairs consumer warp pairs takes every kPairs-th tile of
+// the block's contiguous range, and warp g of the pair works alone on half g
+// of every row (update and Gram need only the elements they own, so the two
+// warps never wait for each other; a stage is freed by their two mbarrier
+// arrivals).  Two consumer warps share each scheduler and hide each other's
+// latencies.  Gram layout (modes 0, 1): lane (rl, cl) owns the outputs of rows
+// rl + NRL i (i < R) and columns cl CW + j (j < CW), so it needs no cross-lane
+// sum; per 16-byte chunk it loads its R rows of X and CW rows of Y and
+// multiplies them with packed FP32 FMAs (fma.rn.f32x2).  Update layout (modes
+// 1-3): a lane owns TB / 64 bytes of the tile of all 8 columns and loops over
+// the rows of X with one load of X and broadcast loads of the C row.  FP32 partial sums are promoted to FP64 every
+// 512 elements of a lane's share; warp and block partials are summed in FP64
+// in a fixed order, the block partials by the last block.  All waits are
+// bounded (timeouts are reported, never hung).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -33,245 +46,479 @@ namespace moto {
 using namespace tma;
 
 namespace {
-constexpr int kStagesT = 3;
-constexpr int kRowB = 512;  // bytes of one field row of a tile
-constexpr int kFlushT = 8;
-constexpr int kPrefetch = 6;  // tiles prefetched into L2 ahead of the shared-memory ring
-constexpr int kWarps = 12;  // consumer warps; with the producer warp at most 4 warps share a scheduler, so 128 registers each
-constexpr int kThr = 32 * kWarps;
+constexpr int kPairs = 4;  // consumer warp pairs per block
+constexpr int kConsumers = 2 * kPairs;
+constexpr int kThrT = 32 * (kConsumers + 1);
+// 9 warps per block: three of them share one scheduler's 64 KB register file
+#define MOTO_TILE_MAXREG 168
+constexpr int kMaxStages = 32;
+constexpr int kFlushE = 512;  // elements between FP32 -> FP64 promotions
+constexpr int kSelf = 36;  // upper-triangle entries of an 8 x 8 Gram
+constexpr size_t kDynBudget = 219 * 1024;  // dynamic shared memory of the ring (1 KB of it alignment slack)
 
-// OR-vote of `pred` over the kThr consumer threads (named barrier 2); a set
-// abort flag counts as a vote.
-__device__ __forceinline__ int __syncthreads_or_consumers(int pred, int abort_flag) {
-  int r;
-  pred = (pred || abort_flag) ? 1 : 0;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 2, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"(pred), "r"(kThr)
-      : "memory");
-  return r;
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
+__device__ __forceinline__ float4 lds128f(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double2 lds128d(uint32_t a) {
+  double2 v;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float2 lds64f(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double lds64d(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+
+// The lane's EL elements of one row of a stage (EL x sizeof(T) = 4, 8 or 16
+// bytes), as loads and stores.
+template <typename T, int EL>
+struct Lane {
+  static __device__ __forceinline__ void load(uint32_t a, T (&v)[EL]) {
+    if constexpr (sizeof(T) == 4 && EL == 1) {
+      asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v[0]) : "r"(a));
+    } else if constexpr (sizeof(T) == 4 && EL == 2) {
+      const float2 x = lds64f(a);
+      v[0] = x.x;
+      v[EL - 1] = x.y;
+    } else if constexpr (sizeof(T) == 4) {
+      const float4 x = lds128f(a);
+      v[0] = x.x;
+      v[1 % EL] = x.y;
+      v[2 % EL] = x.z;
+      v[3 % EL] = x.w;
+    } else if constexpr (EL == 1) {
+      v[0] = lds64d(a);
+    } else {
+      const double2 x = lds128d(a);
+      v[0] = x.x;
+      v[EL - 1] = x.y;
+    }
+  }
+  static __device__ __forceinline__ void store_smem(uint32_t a, const T (&v)[EL]) {
+    if constexpr (sizeof(T) == 4 && EL == 1) {
+      asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"((float)v[0]) : "memory");
+    } else if constexpr (sizeof(T) == 4 && EL == 2) {
+      asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"((float)v[0]), "f"((float)v[EL - 1]) : "memory");
+    } else if constexpr (sizeof(T) == 4) {
+      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"((float)v[0]), "f"((float)v[1 % EL]),
+                   "f"((float)v[2 % EL]), "f"((float)v[3 % EL])
+                   : "memory");
+    } else if constexpr (EL == 1) {
+      asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"((double)v[0]) : "memory");
+    } else {
+      asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"((double)v[0]), "d"((double)v[EL - 1]) : "memory");
+    }
+  }
+  // global store of elements el .. el + EL - 1 (those below n)
+  static __device__ __forceinline__ void store_global(T* dst, size_t el, size_t n, const T (&v)[EL]) {
+    if (el + EL <= n) {
+      if constexpr (EL == 1) {
+        *dst = v[0];
+      } else if constexpr (sizeof(T) == 4 && EL == 2) {
+        *reinterpret_cast<float2*>(dst) = make_float2((float)v[0], (float)v[EL - 1]);
+      } else if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(dst) = make_float4((float)v[0], (float)v[1 % EL], (float)v[2 % EL], (float)v[3 % EL]);
+      } else if constexpr (EL == 1) {
+        *dst = v[0];
+      } else {
+        *reinterpret_cast<double2*>(dst) = make_double2((double)v[0], (double)v[EL - 1]);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EL; ++e)
+        if (el + e < n) dst[e] = v[e];
+    }
+  }
+};
+
+// Gram accumulation of one 16-byte chunk: acc[s][i][j] += <x_i, y_j>.  Each
+// FP32 chunk is two packed FMAs; with few outputs per lane the two halves go
+// to separate accumulator sets (NS = 2) to keep more independent chains.
+template <int NS, int NR, int NC>
+__device__ __forceinline__ void gram_chunk(float2 (&acc)[NS][NR][NC], const float4 (&x)[NR], const float4 (&y)[NC]) {
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+      acc[0][i][j] = ffma2(make_float2(x[i].x, x[i].y), make_float2(y[j].x, y[j].y), acc[0][i][j]);
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+#pragma unroll
+    for (int j = 0; j < NC; ++j)
+      acc[NS - 1][i][j] = ffma2(make_float2(x[i].z, x[i].w), make_float2(y[j].z, y[j].w), acc[NS - 1][i][j]);
+}
+template <int NS, int NR, int NC>
+__device__ __forceinline__ void gram_chunk(double (&acc)[NS][NR][NC], const double2 (&x)[NR], const double2 (&y)[NC]) {
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[0][i][j] = fma(x[i].x, y[j].x, acc[0][i][j]);
+#pragma unroll
+  for (int i = 0; i < NR; ++i)
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[NS - 1][i][j] = fma(x[i].y, y[j].y, acc[NS - 1][i][j]);
 }
 
 template <typename T>
-struct V16;
+struct TileT;
 template <>
-struct V16<float> {
-  typedef float4 type;
-  static constexpr int n = 4;
+struct TileT<float> {
+  typedef float2 Acc;
+  typedef float4 V16;
+  static __device__ __forceinline__ Acc zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ double to_d(const Acc& a) { return (double)a.x + (double)a.y; }
+  static __device__ __forceinline__ float4 lds128(uint32_t a) { return lds128f(a); }
 };
 template <>
-struct V16<double> {
-  typedef double2 type;
-  static constexpr int n = 2;
+struct TileT<double> {
+  typedef double Acc;
+  typedef double2 V16;
+  static __device__ __forceinline__ Acc zero() { return 0.0; }
+  static __device__ __forceinline__ double to_d(const Acc& a) { return a; }
+  static __device__ __forceinline__ double2 lds128(uint32_t a) { return lds128d(a); }
 };
 
-template <typename T>
-__device__ __forceinline__ T vget(const typename V16<T>::type& v, int i);
-template <>
-__device__ __forceinline__ float vget<float>(const float4& v, int i) {
-  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+// Update of the lane's EL elements of the 8 columns: y += X[u0 .. u0 + nu) Cs
+// (Cs rows of 8, padded with zeros past ny).  FP32 keeps column pairs,
+// p[q][e] = (column 2q, column 2q + 1) of element e, for packed FMAs.
+template <int EL, int TB>
+__device__ __forceinline__ void update_rows(float2 (&p)[4][EL], uint32_t xa, int u0, int nu, const float* Cs) {
+#pragma unroll 4
+  for (int r = 0; r < nu; ++r) {
+    float xe[EL];
+    Lane<float, EL>::load(xa + (uint32_t)(u0 + r) * TB, xe);
+    const float4 c0 = *reinterpret_cast<const float4*>(Cs + r * 8);
+    const float4 c1 = *reinterpret_cast<const float4*>(Cs + r * 8 + 4);
+#pragma unroll
+    for (int e = 0; e < EL; ++e) {
+      const float2 xx = make_float2(xe[e], xe[e]);
+      p[0][e] = ffma2(xx, make_float2(c0.x, c0.y), p[0][e]);
+      p[1][e] = ffma2(xx, make_float2(c0.z, c0.w), p[1][e]);
+      p[2][e] = ffma2(xx, make_float2(c1.x, c1.y), p[2][e]);
+      p[3][e] = ffma2(xx, make_float2(c1.z, c1.w), p[3][e]);
+    }
+  }
 }
-template <>
-__device__ __forceinline__ double vget<double>(const double2& v, int i) {
-  return i == 0 ? v.x : v.y;
+
+template <int EL, int TB>
+__device__ __forceinline__ void update_rows_d(double (&y)[8][EL], uint32_t xa, int u0, int nu, const double* Cs) {
+#pragma unroll 2
+  for (int r = 0; r < nu; ++r) {
+    double xe[EL];
+    Lane<double, EL>::load(xa + (uint32_t)(u0 + r) * TB, xe);
+    const double2* cr = reinterpret_cast<const double2*>(Cs + r * 8);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double2 c = cr[q];
+#pragma unroll
+      for (int e = 0; e < EL; ++e) {
+        y[2 * q][e] = fma(xe[e], c.x, y[2 * q][e]);
+        y[2 * q + 1][e] = fma(xe[e], c.y, y[2 * q + 1][e]);
+      }
+    }
+  }
 }
+
 }  // namespace
 
-template <typename T, int MODE, int R, int NY>
-__global__ void __launch_bounds__(kThr + 32, 1) tile2d_kernel(const __grid_constant__ CUtensorMap tmX,
-                                                              const __grid_constant__ CUtensorMap tmY, int nx, int ny,
-                                                              size_t n, const double* __restrict__ C,
-                                                              T* __restrict__ Yout, size_t ldo, double* out,
-                                                              double* part, unsigned* counter, const int* gate,
-                                                              int mask, int* status) {
+template <typename T, int MODE, int R, int CW, int NRL, int TB>
+__global__ void __maxnreg__(MOTO_TILE_MAXREG)
+    tile2d_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int nx, int ny,
+                  int u0, int nu, size_t n, const double* __restrict__ C, T* __restrict__ Yout, size_t ldo, double* out,
+                  double* part, unsigned* counter, int nst, const int* gate, int mask, int* status) {
   if (gate && (*gate & mask)) return;
-  typedef typename V16<T>::type VT;
-  constexpr int VN = V16<T>::n;
-  constexpr int KT = kRowB / (int)sizeof(T);  // elements per row of a tile
-  static_assert(KT == 32 * VN, "one 16-byte chunk per lane per row");
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kStagesT];
-  __shared__ __align__(8) uint64_t empty[kStagesT];
-  __shared__ double facc[MOTO_MAX_BASIS * 8];
+  typedef TileT<T> TT;
+  typedef typename TT::Acc Acc;
+  typedef typename TT::V16 VT;
+  constexpr int TE = TB / (int)sizeof(T);  // elements of a tile
+  constexpr int HB = TB / 2;  // bytes of a row a warp of the pair owns
+  constexpr int EL = TE / 64;  // elements of a lane in the update layout
+  constexpr int NCH = HB / 16;  // 16-byte chunks of a half row
+  static_assert(EL == 1 || EL == 2, "a lane owns 4 to 16 bytes of a row");
+  static_assert(EL * (int)sizeof(T) >= 4 && EL * (int)sizeof(T) <= 16, "lane share");
+  constexpr bool kGramMode = (MODE <= 1);
+  constexpr bool kF32 = sizeof(T) == 4;
+  constexpr int NR = kGramMode ? R : 1, NC = kGramMode ? CW : 1;
+  constexpr int NS = (kF32 && NR * NC <= 8) ? 2 : 1;  // accumulator sets
+  constexpr int ND = kGramMode ? (kF32 ? NR * NC : 1) : kSelf;  // FP64 totals
+  constexpr int kFlushT = kFlushE / (TE / 2);
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[kMaxStages];
+  __shared__ __align__(8) uint64_t empty[kMaxStages];
   __shared__ __align__(16) T Cs[MOTO_MAX_BASIS * 8];
   __shared__ int abort_flag;
 
-  const int rows = nx + ny;
-  const size_t stage_bytes = ((size_t)rows * kRowB + 1023) / 1024 * 1024;
-  const unsigned tx_bytes = (unsigned)((MODE == 3 ? nx : rows) * kRowB);
-  const int na = (MODE <= 1) ? nx : ny;  // Gram rows
-  const int a_off = (MODE <= 1) ? 0 : nx;
-  const int nout = na * ny;
+  // ring base, 1024-byte aligned
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t ring = (raw + 1023u) & ~1023u;
+  unsigned char* ring_ptr = smem_raw + (ring - raw);
+  const int nxp = (nx + 7) & ~7;
+  const uint32_t yoff = (uint32_t)nxp * TB;
+  const uint32_t stage_bytes = yoff + 8u * TB;
+  const unsigned tx_bytes = (unsigned)((nx + (MODE == 3 ? 0 : ny)) * TB);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool producer = (w == kWarps);
-  const int r0 = w * R;
+  const int na = kGramMode ? nx : ny;
 
-  const size_t ntiles = (n + KT - 1) / KT;
+  const size_t ntiles = (n + TE - 1) / TE;
   const size_t t_begin = ntiles * blockIdx.x / gridDim.x;
   const size_t t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int ntile = (int)(t_end - t_begin);
 
-  for (int i = threadIdx.x; i < nout; i += blockDim.x) facc[i] = 0.0;
   if (MODE != 0)
-    for (int i = threadIdx.x; i < nx * 8; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nu * 8; i += blockDim.x) {
       const int r = i >> 3, c = i & 7;
       const double cf = c < ny ? C[r * ny + c] : 0.0;
       Cs[i] = (T)(MODE == 3 ? cf : -cf);
     }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStagesT; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kWarps);
+      mbar_init(&empty[s], 2);
     }
     abort_flag = 0;
     fence_async_shared();
   }
   __syncthreads();
 
-  if (producer) {
-    // ---- TMA producer warp: refill a stage once every consumer warp freed it
+  // FP64 totals of the lane's outputs (Gram layout, FP32) or of the self-Gram
+  // entries (update layout)
+  double dacc[ND];
+#pragma unroll
+  for (int i = 0; i < ND; ++i) dacc[i] = 0.0;
+  Acc acc[NS][NR][NC];
+#pragma unroll
+  for (int s2 = 0; s2 < NS; ++s2)
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+#pragma unroll
+      for (int j = 0; j < NC; ++j) acc[s2][i][j] = TT::zero();
+
+  if (w == kConsumers) {
+    // ---- TMA producer: lane 0 refills a stage once its consumer freed it
     if (lane == 0) {
-      // warm L2 with the first tiles beyond the ring
-      for (int p = 0; p < kPrefetch; ++p) {
-        const size_t tp = t_begin + kStagesT + p;
-        if (tp < t_end) {
-          tma_prefetch_2d(&tmX, (int)(tp * KT), 0);
-          if (MODE != 3) tma_prefetch_2d(&tmY, (int)(tp * KT), 0);
-        }
-      }
-      for (size_t t = t_begin; t < t_end; ++t) {
-        const int it = (int)(t - t_begin);
-        const int s = it % kStagesT;
-        if (it >= kStagesT && !mbar_wait(&empty[s], (unsigned)(((it / kStagesT) - 1) & 1))) {
+      for (int it = 0; it < ntile; ++it) {
+        const int s = it % nst;
+        if (it >= nst && !mbar_wait(&empty[s], (unsigned)(((it / nst) - 1) & 1))) {
           atomicExch(&abort_flag, 1);
           if (status) atomicOr(status, kStatusTimeout);
           break;
         }
         if (*(volatile int*)&abort_flag) break;
-        unsigned char* buf = smem + (size_t)s * stage_bytes;
-        fence_async_shared();
+        unsigned char* buf = ring_ptr + (size_t)s * stage_bytes;
         mbar_expect_tx(&full[s], tx_bytes);
-        const int x = (int)(t * KT);
+        const int x = (int)((t_begin + it) * TE);
         tma_load_2d(buf, &tmX, x, 0, &full[s]);
-        if (MODE != 3) tma_load_2d(buf + (size_t)nx * kRowB, &tmY, x, 0, &full[s]);
-        const size_t tp = t + kStagesT + kPrefetch;
-        if (tp < t_end) {
-          tma_prefetch_2d(&tmX, (int)(tp * KT), 0);
-          if (MODE != 3) tma_prefetch_2d(&tmY, (int)(tp * KT), 0);
-        }
+        if (MODE != 3) tma_load_2d(buf + yoff, &tmY, x, 0, &full[s]);
       }
     }
   } else {
-    // ---- consumer warps
-    T acc[R][NY];
+    // ---- consumer warp w: pair pw, half g of the rows; tiles it = pw, pw + kPairs, ...
+    // Gram layout: byte offsets of the lane's rows, chunk skew
+    uint32_t xrow[NR], yrow[NC];
+    {
+      const int rl = lane % NRL, cl = lane / NRL;
 #pragma unroll
-    for (int j = 0; j < R; ++j)
+      for (int i = 0; i < NR; ++i) xrow[i] = (uint32_t)min(rl + NRL * i, na - 1) * TB;
 #pragma unroll
-      for (int c = 0; c < NY; ++c) acc[j][c] = (T)0;
-    auto flush = [&]() {
+      for (int j = 0; j < NC; ++j) yrow[j] = yoff + (uint32_t)min(cl * CW + j, ny - 1) * TB;
+    }
+    const int skew = lane & 7;
+    float sacc[(MODE >= 2 && kF32) ? kSelf : 1];
 #pragma unroll
-      for (int j = 0; j < R; ++j)
-#pragma unroll
-        for (int c = 0; c < NY; ++c) {
-          T v = acc[j][c];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0 && r0 + j < na && c < ny) facc[(r0 + j) * ny + c] += (double)v;
-          acc[j][c] = (T)0;
-        }
-    };
+    for (int i = 0; i < ((MODE >= 2 && kF32) ? kSelf : 1); ++i) sacc[i] = 0.f;
+    const int pw = w >> 1, g = w & 1;
+    const uint32_t hoff = (uint32_t)g * HB;
+    const uint32_t lane_b = hoff + (uint32_t)lane * EL * sizeof(T);  // update layout: the lane's bytes of a row
     int since = 0;
-    for (size_t t = t_begin; t < t_end; ++t) {
-      const int it = (int)(t - t_begin);
-      const int s = it % kStagesT;
-      bool ok = mbar_wait(&full[s], (unsigned)((it / kStagesT) & 1));
-      if (MODE != 0) {
-        // consumers agree before the update phase (it is followed by a
-        // consumer-wide barrier)
-        ok = __syncthreads_or_consumers(!ok, abort_flag) == 0;
-      } else if (!ok) {
+    for (int it = pw; it < ntile; it += kPairs) {
+      const int s = it % nst;
+      if (!mbar_wait(&full[s], (unsigned)((it / nst) & 1))) {
         atomicExch(&abort_flag, 1);
         if (status) atomicOr(status, kStatusTimeout);
       }
-      if (!ok || *(volatile int*)&abort_flag) break;
-      T* buf = reinterpret_cast<T*>(smem + (size_t)s * stage_bytes);
-      T* Ys = buf + (size_t)nx * KT;
+      if (*(volatile int*)&abort_flag) break;
+      const uint32_t sb = ring + (uint32_t)s * stage_bytes;
       if (MODE != 0) {
-        // update phase: thread -> element e, columns 4q .. 4q+3
-        const int e = threadIdx.x % KT, q = threadIdx.x / KT;
-        if (4 * q < ny && q < 2) {
-          T v[4];
+        const uint32_t xa = sb + lane_b, ya = sb + yoff + lane_b;
+        const size_t el = (size_t)(t_begin + it) * TE + (size_t)g * (TE / 2) + (size_t)lane * EL;
+        T yv[8][EL];
+        if constexpr (kF32) {
+          float2 p[4][EL];
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            v[j] = (MODE == 3 || 4 * q + j >= ny) ? (T)0 : Ys[(size_t)(4 * q + j) * KT + e];
-          const T* xc = buf + e;
-          const T* cc = Cs + 4 * q;
+          for (int q = 0; q < 4; ++q) {
+            float a[EL], b[EL];
+#pragma unroll
+            for (int e = 0; e < EL; ++e) a[e] = b[e] = 0.f;
+            if (MODE != 3) {
+              if (2 * q < ny) Lane<float, EL>::load(ya + (uint32_t)(2 * q) * TB, a);
+              if (2 * q + 1 < ny) Lane<float, EL>::load(ya + (uint32_t)(2 * q + 1) * TB, b);
+            }
+#pragma unroll
+            for (int e = 0; e < EL; ++e) p[q][e] = make_float2(a[e], b[e]);
+          }
+          update_rows<EL, TB>(p, xa, MODE == 1 ? u0 : 0, nu, reinterpret_cast<const float*>(Cs));
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int e = 0; e < EL; ++e) {
+              yv[2 * q][e] = p[q][e].x;
+              yv[2 * q + 1][e] = p[q][e].y;
+            }
+        } else {
+          double y[8][EL];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+#pragma unroll
+            for (int e = 0; e < EL; ++e) y[c][e] = 0.0;
+            if (MODE != 3 && c < ny) Lane<double, EL>::load(ya + (uint32_t)c * TB, y[c]);
+          }
+          update_rows_d<EL, TB>(y, xa, MODE == 1 ? u0 : 0, nu, reinterpret_cast<const double*>(Cs));
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+#pragma unroll
+            for (int e = 0; e < EL; ++e) yv[c][e] = y[c][e];
+        }
+        // write back (and, in mode 1, into the staged tile for the Gram phase)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (c < ny) {
+            Lane<T, EL>::store_global(Yout + (size_t)c * ldo + el, el, n, yv[c]);
+            if (MODE == 1) Lane<T, EL>::store_smem(ya + (uint32_t)c * TB, yv[c]);
+          }
+        }
+        if constexpr (MODE >= 2) {
+          // self Gram of the updated columns (elements past n are zero)
+          int q = 0;
+#pragma unroll
+          for (int c1 = 0; c1 < 8; ++c1)
+#pragma unroll
+            for (int c2 = c1; c2 < 8; ++c2, ++q) {
+              if constexpr (kF32) {
+                float a = sacc[q];
+#pragma unroll
+                for (int e = 0; e < EL; ++e) a = fmaf((float)yv[c1][e], (float)yv[c2][e], a);
+                sacc[q] = a;
+              } else {
+#pragma unroll
+                for (int e = 0; e < EL; ++e) dacc[q] = fma((double)yv[c1][e], (double)yv[c2][e], dacc[q]);
+              }
+            }
+        }
+        if (MODE == 1) __syncwarp();
+      }
+      if constexpr (kGramMode) {
+        // Gram phase: acc[.][i][j] += <X row i, Y row j> over the tile, the
+        // lane's walk over the chunks starting at chunk `skew`
 #pragma unroll 4
-          for (int r = 0; r < nx; ++r) {
-            const T x = xc[(size_t)r * KT];
-            v[0] += x * cc[r * 8];
-            v[1] += x * cc[r * 8 + 1];
-            v[2] += x * cc[r * 8 + 2];
-            v[3] += x * cc[r * 8 + 3];
-          }
-          const size_t el = t * KT + e;
+        for (int k = 0; k < NCH; ++k) {
+          const uint32_t co = sb + hoff + (uint32_t)(((k + skew) & (NCH - 1)) << 4);
+          VT xv[NR], yw[NC];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int c = 4 * q + j;
-            if (c < ny) {
-              Ys[(size_t)c * KT + e] = el < n ? v[j] : (T)0;
-              if (el < n) Yout[(size_t)c * ldo + el] = v[j];
-            }
-          }
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(kThr) : "memory");  // consumers only
-      }
-      // Gram phase
-      if (r0 < na) {
-        const T* As = buf + (size_t)a_off * KT;
-        VT y[NY];
+          for (int i = 0; i < NR; ++i) xv[i] = TT::lds128(co + xrow[i]);
 #pragma unroll
-        for (int c = 0; c < NY; ++c) {
-          if (c < ny)
-            y[c] = reinterpret_cast<const VT*>(Ys + (size_t)c * KT)[lane];
-          else
-            y[c] = VT();
-        }
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          if (r0 + j < na) {
-            const VT x = reinterpret_cast<const VT*>(As + (size_t)(r0 + j) * KT)[lane];
-#pragma unroll
-            for (int c = 0; c < NY; ++c) {
-              T a = acc[j][c];
-#pragma unroll
-              for (int i = 0; i < VN; ++i) a += vget<T>(x, i) * vget<T>(y[c], i);
-              acc[j][c] = a;
-            }
-          }
-        }
-        if (++since == kFlushT) {
-          since = 0;
-          flush();
+          for (int j = 0; j < NC; ++j) yw[j] = TT::lds128(co + yrow[j]);
+          gram_chunk<NS, NR, NC>(acc, xv, yw);
         }
       }
+      // free the stage; the generic-proxy writes of mode 1 are ordered before
+      // the next tensor copy into it
+      if (MODE == 1) fence_async_shared();
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);
+      if (kF32 && ++since == kFlushT) {
+        since = 0;
+        if constexpr (kGramMode && kF32) {
+#pragma unroll
+          for (int i = 0; i < NR; ++i)
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+              double a = TT::to_d(acc[0][i][j]);
+              if (NS == 2) a += TT::to_d(acc[NS - 1][i][j]);
+              dacc[i * NC + j] += a;
+              acc[0][i][j] = TT::zero();
+              acc[NS - 1][i][j] = TT::zero();
+            }
+        } else if constexpr (MODE >= 2 && kF32) {
+#pragma unroll
+          for (int q = 0; q < kSelf; ++q) {
+            dacc[q] += (double)sacc[q];
+            sacc[q] = 0.f;
+          }
+        }
+      }
     }
-    if (r0 < na) flush();
+    if constexpr (MODE >= 2 && kF32) {
+#pragma unroll
+      for (int q = 0; q < kSelf; ++q) dacc[q] += (double)sacc[q];
+    }
   }
   __syncthreads();
   if (abort_flag) {
-    // bounded drain: let tensor copies still in flight land before the block
-    // exits (a phase that already completed returns at once)
+    // bounded drain: let tensor copies still in flight land before the ring
+    // is reused (a phase that already completed returns at once)
     if (threadIdx.x == 0)
-      for (int s = 0; s < kStagesT; ++s) {
+      for (int s = 0; s < nst; ++s) {
         mbar_wait(&full[s], 0);
         mbar_wait(&full[s], 1);
       }
     __syncthreads();
   }
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) part[(size_t)blockIdx.x * nout + o] = facc[o];
+  // per-warp partials in the (now idle) ring, then the block partial
+  const int nout = na * ny;
+  double* red = reinterpret_cast<double*>(ring_ptr);
+  if (w < kConsumers) {
+    double* rw = red + (size_t)w * nout;
+    if constexpr (kGramMode) {
+      const int rl = lane % NRL, cl = lane / NRL;
+#pragma unroll
+      for (int i = 0; i < NR; ++i)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+          const int r = rl + NRL * i, c = cl * CW + j;
+          double v = TT::to_d(acc[0][i][j]);
+          if (NS == 2) v += TT::to_d(acc[NS - 1][i][j]);
+          if constexpr (kF32) v += dacc[i * NC + j];
+          if (r < na && c < ny) rw[r * ny + c] = v;
+        }
+    } else {
+      int q = 0;
+#pragma unroll
+      for (int c1 = 0; c1 < 8; ++c1)
+#pragma unroll
+        for (int c2 = c1; c2 < 8; ++c2, ++q) {
+          double v = dacc[q];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0 && c2 < ny) {
+            rw[c1 * ny + c2] = v;
+            rw[c2 * ny + c1] = v;
+          }
+        }
+    }
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double a = 0.0;
+    for (int ww = 0; ww < kConsumers; ++ww) a += red[(size_t)ww * nout + o];
+    part[(size_t)blockIdx.x * nout + o] = a;
+  }
   if (!grid_last_block(counter)) return;
   grid_sum_entries(part, gridDim.x, nout, out);
   if (threadIdx.x == 0) *counter = 0u;
@@ -294,15 +541,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D map over `rows` fields of n elements, field stride ld; box [rows][KT]
+// 2D map over `rows` fields of n elements, field stride ld; box [rows][TB
+// bytes], no swizzle
 template <typename T>
-bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld) {
+bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld, int tb) {
   auto fn = encode_fn();
   if (!fn) return false;
-  constexpr int KT = kRowB / (int)sizeof(T);
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(T))};
-  cuuint32_t box[2] = {(cuuint32_t)KT, (cuuint32_t)rows};
+  cuuint32_t box[2] = {(cuuint32_t)(tb / sizeof(T)), (cuuint32_t)rows};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
   return fn(map, dt, 2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -310,97 +557,117 @@ bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld) {
          CUDA_SUCCESS;
 }
 
-template <typename T, int MODE, int R, int NY>
-void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, size_t n, const double* C, T* Yout,
-                 size_t ldo, double* out, double* part, unsigned* counter, const int* gate, int mask, int* status,
-                 cudaStream_t st) {
-  constexpr int KT = kRowB / (int)sizeof(T);
-  const size_t stage_bytes = ((size_t)(nx + ny) * kRowB + 1023) / 1024 * 1024;
-  const size_t smem = kStagesT * stage_bytes;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tile2d_kernel<T, MODE, R, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
-  static int per_sm[MOTO_MAX_BASIS + 10] = {0};
-  const int key = nx + ny;
-  if (!per_sm[key]) {
-    int b = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tile2d_kernel<T, MODE, R, NY>, kThr + 32, smem) != cudaSuccess ||
-        b < 1)
-      b = 1;
-    per_sm[key] = b < 4 ? b : 4;
-  }
-  const int na = MODE <= 1 ? nx : ny;
-  size_t want = (size_t)kSMs * per_sm[key];
-  const size_t cap = (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K / ((size_t)na * ny);
-  if (want > cap) want = cap;
-  const size_t ntiles = (n + KT - 1) / KT;
-  const int grid = (int)(ntiles < want ? (ntiles > 0 ? ntiles : 1) : want);
-  tile2d_kernel<T, MODE, R, NY><<<grid, kThr + 32, smem, st>>>(mx, my, nx, ny, n, C, Yout, ldo, out, part, counter, gate,
-                                                          mask, status);
+// Row bytes of a tile: 512 while eight stages still fit (few fields: a copy
+// then moves enough bytes to stay at full rate), else 256; FP64 always 512
+// (a lane's share is one element).
+template <typename T>
+int tile_bytes(int nx) {
+  if (sizeof(T) == 8) return 512;
+  return ((nx + 7) / 8 * 8 + 8) * 512 * 8 <= (int)kDynBudget - 1024 ? 512 : 256;
 }
 
-template <typename T, int MODE>
-void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, size_t n, const double* C, T* Yout,
-                   size_t ldo, double* out, double* part, unsigned* counter, const int* gate, int mask, int* status,
-                   cudaStream_t st) {
-  const int na = MODE <= 1 ? nx : ny;
-  const int r = (na + kWarps - 1) / kWarps;
-#define TL(RR, YY) tile_launch<T, MODE, RR, YY>(mx, my, nx, ny, n, C, Yout, ldo, out, part, counter, gate, mask, status, st)
-#define TROWS(YY)      \
-  if (r <= 1)          \
-    TL(1, YY);         \
-  else if (r <= 2)     \
-    TL(2, YY);         \
-  else if (r <= 4)     \
-    TL(4, YY);         \
-  else if (r <= 6)     \
-    TL(6, YY);         \
-  else                 \
-    TL(8, YY);
-  if (ny <= 1) {
-    TROWS(1)
-  } else if (ny <= 2) {
-    TROWS(2)
-  } else if (ny <= 4) {
-    TROWS(4)
-  } else {
-    TROWS(8)
+template <typename T, int MODE, int R, int CW, int NRL, int TB>
+void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
+                 const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
+                 int mask, int* status, cudaStream_t st) {
+  constexpr int TE = TB / (int)sizeof(T);
+  const int nxp = (nx + 7) & ~7;
+  const size_t stage_bytes = (size_t)(nxp + 8) * TB;
+  int nst = (int)((kDynBudget - 1024) / stage_bytes);
+  if (nst > kMaxStages) nst = kMaxStages;
+  nst -= nst % kPairs;  // a stage always goes to the same warp pair
+  const size_t smem = (size_t)nst * stage_bytes + 1024;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tile2d_kernel<T, MODE, R, CW, NRL, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kDynBudget);
+    attr = true;
   }
-#undef TROWS
+  const int na = MODE <= 1 ? nx : ny;
+  size_t want = kSMs;
+  const size_t cap = (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K / ((size_t)na * ny);
+  if (want > cap) want = cap;
+  const size_t ntiles = (n + TE - 1) / TE;
+  const int grid = (int)(ntiles < want ? (ntiles > 0 ? ntiles : 1) : want);
+  tile2d_kernel<T, MODE, R, CW, NRL, TB><<<grid, kThrT, smem, st>>>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out,
+                                                                    part, counter, nst, gate, mask, status);
+}
+
+template <typename T, int MODE, int TB>
+void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
+                   const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter,
+                   const int* gate, int mask, int* status, cudaStream_t st) {
+#define TL(RR, CC, NN)                                                                                           \
+  tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out, part, counter, gate, mask, \
+                                       status, st)
+  if constexpr (MODE >= 2) {
+    TL(1, 8, 32);
+  } else if (nx <= 8) {
+    TL(1, 2, 8);
+  } else if (nx <= 16) {
+    TL(1, 4, 16);
+  } else if (nx <= 32) {
+    TL(1, 8, 32);
+  } else if (nx <= 64) {
+    TL(2, 8, 32);
+  } else {
+    TL(3, 8, 32);
+  }
 #undef TL
 }
 
 }  // namespace
 
 template <typename T>
-bool launch_tile(int mode, const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, const double* C,
-                 T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate, int mask,
-                 int* status, cudaStream_t st) {
+bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
+                 const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
+                 int mask, int* status, cudaStream_t st) {
   auto al = [](const void* p) { return ((uintptr_t)p % 16) == 0; };
   if ((ldx * sizeof(T)) % 16 || (ldy * sizeof(T)) % 16 || !al(X) || (mode != 3 && !al(Y))) return false;
   if (mode != 0 && ((ldo * sizeof(T)) % 16 || !al(Yout))) return false;
   if (nx < 1 || nx > MOTO_MAX_BASIS || ny < 1 || ny > 8 || n >= (1ull << 31)) return false;
+  if (mode == 1 && (u0 < 0 || nu < 0 || u0 + nu > nx)) return false;
+  if (mode >= 2) {
+    u0 = 0;
+    nu = nx;
+  }
+  const int tb = tile_bytes<T>(nx);
   CUtensorMap mx, my;
-  if (!make_map<T>(&mx, X, n, nx, ldx)) return false;
+  if (!make_map<T>(&mx, X, n, nx, ldx, tb)) return false;
   if (mode != 3) {
-    if (!make_map<T>(&my, Y, n, ny, ldy)) return false;
+    if (!make_map<T>(&my, Y, n, ny, ldy, tb)) return false;
   } else {
     my = mx;
   }
-  switch (mode) {
-    case 0: tile_dispatch<T, 0>(mx, my, nx, ny, n, C, Yout, ldo, out, part, counter, gate, mask, status, st); break;
-    case 1: tile_dispatch<T, 1>(mx, my, nx, ny, n, C, Yout, ldo, out, part, counter, gate, mask, status, st); break;
-    case 2: tile_dispatch<T, 2>(mx, my, nx, ny, n, C, Yout, ldo, out, part, counter, gate, mask, status, st); break;
-    default: tile_dispatch<T, 3>(mx, my, nx, ny, n, C, Yout, ldo, out, part, counter, gate, mask, status, st); break;
+#define TD(M, B) tile_dispatch<T, M, B>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out, part, counter, gate, mask, status, st)
+  if constexpr (sizeof(T) == 8) {
+    switch (mode) {
+      case 0: TD(0, 512); break;
+      case 1: TD(1, 512); break;
+      case 2: TD(2, 512); break;
+      default: TD(3, 512); break;
+    }
+  } else {
+    switch (mode * 2 + (tb == 512 ? 1 : 0)) {
+      case 0: TD(0, 256); break;
+      case 1: TD(0, 512); break;
+      case 2: TD(1, 256); break;
+      case 3: TD(1, 512); break;
+      case 4: TD(2, 256); break;
+      case 5: TD(2, 512); break;
+      case 6: TD(3, 256); break;
+      default: TD(3, 512); break;
+    }
   }
+#undef TD
   return true;
 }
 
-template bool launch_tile<float>(int, const float*, size_t, int, const float*, size_t, int, size_t, const double*,
-                                 float*, size_t, double*, double*, unsigned*, const int*, int, int*, cudaStream_t);
-template bool launch_tile<double>(int, const double*, size_t, int, const double*, size_t, int, size_t, const double*,
-                                  double*, size_t, double*, double*, unsigned*, const int*, int, int*, cudaStream_t);
+template bool launch_tile<float>(int, const float*, size_t, int, int, int, const float*, size_t, int, size_t,
+                                 const double*, float*, size_t, double*, double*, unsigned*, const int*, int, int*,
+                                 cudaStream_t);
+template bool launch_tile<double>(int, const double*, size_t, int, int, int, const double*, size_t, int, size_t,
+                                  const double*, double*, size_t, double*, double*, unsigned*, const int*, int, int*,
+                                  cudaStream_t);
 
 }  // namespace moto

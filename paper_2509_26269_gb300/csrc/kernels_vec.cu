@@ -144,7 +144,7 @@ void set_gram_status(int* status) { g_gram_status = status; }
 template <typename T>
 void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
                  double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st) {
-  if (launch_tile<T>(0, X, ldx, nx, Y, ldy, ny, n, nullptr, nullptr, 0, out, part, counter, gate, mask,
+  if (launch_tile<T>(0, X, ldx, nx, 0, 0, Y, ldy, ny, n, nullptr, nullptr, 0, out, part, counter, gate, mask,
                     g_gram_status, st))
     return;
   if (ny <= 1)
@@ -399,16 +399,16 @@ void launch_lanczos_coeffs(const double* A, int b, int j, double* T, int ldT, do
   lanczos_coeffs_kernel<<<1, 32, 0, s>>>(A, b, j, T, ldT, C3, st);
 }
 
-__global__ void arnoldi_diag_kernel(const double* G1, int b, int j, double* T, int ldT, DevState* st) {
+__global__ void arnoldi_diag_kernel(const double* G1, int b, int jr, int j, double* T, int ldT, DevState* st) {
   if (st->gate & (kGateKrylov | kGateDone)) return;
   const int r = threadIdx.x / b, c = threadIdx.x % b;
   if (r >= b) return;
-  const double a = G1[(size_t)(j * b + r) * b + c], at = G1[(size_t)(j * b + c) * b + r];
+  const double a = G1[(size_t)(jr * b + r) * b + c], at = G1[(size_t)(jr * b + c) * b + r];
   T[(size_t)(j * b + r) * ldT + j * b + c] = 0.5 * (a + at);
 }
 
-void launch_arnoldi_diag(const double* G1, int b, int j, double* T, int ldT, DevState* st, cudaStream_t s) {
-  arnoldi_diag_kernel<<<1, 64, 0, s>>>(G1, b, j, T, ldT, st);
+void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int ldT, DevState* st, cudaStream_t s) {
+  arnoldi_diag_kernel<<<1, 64, 0, s>>>(G1, b, jr, j, T, ldT, st);
 }
 
 // Cholesky QR factor of the b x b Gram G.  Pass 1 (second == 0) also updates
