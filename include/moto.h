@@ -136,6 +136,24 @@ int moto_energy(moto_ctx* ctx, const void* m_dev, double* E_dev, void* stream);
 int moto_hvp(moto_ctx* ctx, const void* m_dev, const void* s_dev, const void* v_dev,
              size_t ldv, void* hv_dev, size_t ldhv, int nvec, void* stream);
 
+/* Energy and Euclidean gradient, the reverse-mode derivative an autodiff
+ * engine takes of E (Methods, "Gradient, HVP, and Hessian via the autograd
+ * engine"; the backward of torch.autograd.Function MotoEnergy):
+ *   grad_dev (3N): grad_i E = h_i(m) - muB z - 2 K m_iz z (no projection);
+ *   out_dev (2 doubles): [E, max_i |grad_i E|],
+ * both evaluated in double arithmetic whatever the context precision (grad
+ * stored in it).  m_dev need not be unit length here: E is the polynomial of
+ * Eq. param-hamiltonian.  All pointers required. */
+int moto_energy_euclid_grad(moto_ctx* ctx, const void* m_dev, void* grad_dev, double* out_dev, void* stream);
+
+/* Euclidean Hessian-vector products (hess E v_j) for nvec vectors (Methods,
+ * "HVP operator mode": the double backward of E).  E is quadratic in m, so
+ * hess E is the same at every m and no state is read:
+ *   (hess E v)_i = h_i(v) - 2 K v_iz z.
+ * Layout and strides as for moto_hvp; v need not be tangent. */
+int moto_euclid_hvp(moto_ctx* ctx, const void* v_dev, size_t ldv, void* hv_dev, size_t ldhv, int nvec,
+                    void* stream);
+
 /* Inner layer of the bilayer MMF kernel (Results, "Bilayer MMF"): the k
  * smallest eigenpairs of the tangent Hessian at m by HVP-driven block
  * Lanczos or LOBPCG (params->solver).

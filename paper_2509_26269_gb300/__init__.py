@@ -57,6 +57,8 @@ def _load():
         "moto_energy_grad": (I, [P, P, P, P, P, P]),
         "moto_energy": (I, [P, P, P, P]),
         "moto_hvp": (I, [P, P, P, P, Z, P, Z, I, P]),
+        "moto_energy_euclid_grad": (I, [P, P, P, P, P]),
+        "moto_euclid_hvp": (I, [P, P, Z, P, Z, I, P]),
         "moto_lowest_modes": (I, [P, P, P, ctypes.POINTER(moto_params), P, P, P, P, P]),
         "moto_topo_charge": (I, [P, P, P, P]),
         "moto_lbfgs_reset": (I, [P, P]),
@@ -84,7 +86,7 @@ EXPORTED = (
     "moto_default_params", "moto_create", "moto_destroy", "moto_energy_grad", "moto_energy", "moto_hvp",
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
-    "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram",
+    "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig")
 
@@ -170,6 +172,16 @@ def moto_hvp(ctx, m, s, v, ldv, hv, ldhv, nvec=1, stream=None):
                          _stream(stream)), "moto_hvp")
 
 
+def moto_energy_euclid_grad(ctx, m, grad, out, stream=None):
+    _check(_lib.moto_energy_euclid_grad(ctx, _ptr(m), _ptr(grad), _ptr(out), _stream(stream)),
+           "moto_energy_euclid_grad")
+
+
+def moto_euclid_hvp(ctx, v, ldv, hv, ldhv, nvec=1, stream=None):
+    _check(_lib.moto_euclid_hvp(ctx, _ptr(v), int(ldv), _ptr(hv), int(ldhv), int(nvec), _stream(stream)),
+           "moto_euclid_hvp")
+
+
 def moto_lowest_modes(ctx, m, s, params, v0, V, lam, info=None, stream=None):
     _check(_lib.moto_lowest_modes(ctx, _ptr(m), _ptr(s), ctypes.byref(params), _ptr(v0), _ptr(V), _ptr(lam),
                                   _ptr(info), _stream(stream)), "moto_lowest_modes")
@@ -248,3 +260,4 @@ def moto_profile_end(ctx):
 
 
 from .context import Context  # noqa: E402,F401
+from .autograd import MotoEnergy, energy  # noqa: E402,F401

@@ -16,7 +16,10 @@ class Context:
         self.L1, self.L2 = int(L1), int(L2)
         self.N = self.L1 * self.L2
         self.dtype = dtype
-        self.device = torch.device(device)
+        dev = torch.device(device)
+        if dev.type == "cuda" and dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
         self.params = make_params(**params)
         code = MOTO_F64 if dtype == torch.float64 else MOTO_F32
         with torch.cuda.device(self.device):

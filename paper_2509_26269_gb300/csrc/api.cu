@@ -649,6 +649,37 @@ int moto_hvp(moto_ctx* c, const void* m, const void* s, const void* v, size_t ld
   return MOTO_OK;
 }
 
+int moto_energy_euclid_grad(moto_ctx* c, const void* m, void* grad, double* out, void* stream) {
+  if (!c || !m || !grad || !out) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  if (c->dtype == MOTO_F32) {
+    PROF(kPkStencil, 6.0 * c->N * sizeof(float));
+    launch_energy_grad<float>(c->md, (const float*)m, (float*)grad, nullptr, c->part, c->counter, out,
+                              &c->st->status, true, st, true);
+  } else {
+    PROF(kPkStencil, 6.0 * c->N * sizeof(double));
+    launch_energy_grad<double>(c->md, (const double*)m, (double*)grad, nullptr, c->part, c->counter, out,
+                               &c->st->status, true, st, true);
+  }
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+int moto_euclid_hvp(moto_ctx* c, const void* v, size_t ldv, void* hv, size_t ldhv, int nvec, void* stream) {
+  if (!c || !v || !hv || nvec < 1) return MOTO_ERR_ARG;
+  if ((nvec > 1) && (ldv < c->n3 || ldhv < c->n3)) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  if (c->dtype == MOTO_F32) {
+    PROF(kPkHvp, 6.0 * nvec * c->N * sizeof(float));
+    launch_euclid_hvp<float>(c->md, (const float*)v, ldv, (float*)hv, ldhv, nvec, st);
+  } else {
+    PROF(kPkHvp, 6.0 * nvec * c->N * sizeof(double));
+    launch_euclid_hvp<double>(c->md, (const double*)v, ldv, (double*)hv, ldhv, nvec, st);
+  }
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
 int moto_topo_charge(moto_ctx* c, const void* m, double* Q, void* stream) {
   if (!c || !m || !Q) return MOTO_ERR_ARG;
   if (c->dtype == MOTO_F32)

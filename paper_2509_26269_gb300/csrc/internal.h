@@ -34,9 +34,13 @@ struct DevState {
 
 int tile_blocks(const ModelDev& md);
 
+// euclid: g receives grad E itself instead of the Riemannian gradient
 template <typename T>
 void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
-                        int* status, bool fp64_arith, cudaStream_t st);
+                        int* status, bool fp64_arith, cudaStream_t st, bool euclid = false);
+// Euclidean Hessian-vector product (hess E v)_i = h_i(v) - 2 K v_iz z
+template <typename T>
+void launch_euclid_hvp(const ModelDev& md, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec, cudaStream_t st);
 template <typename T>
 void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec,
                 const int* gate, int mask, cudaStream_t st);

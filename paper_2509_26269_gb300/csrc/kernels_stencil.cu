@@ -38,12 +38,13 @@ __device__ void finish_sum_max(const double* part, int nblocks, double* out, dou
 
 // grad_i E = h_i(m) - muB z - 2 K m_iz z;  s_i = m_i . grad_i E;
 // g_i = grad_i E - s_i m_i;  E = sum_i (s_i - muB m_iz) / 2 (E is quadratic in
-// m: E = m^T (grad E + b) / 2 with b = -muB z summed over sites).
+// m: E = m^T (grad E + b) / 2 with b = -muB z summed over sites).  With euclid
+// set, g receives grad_i E itself and out[1] its largest per-site norm.
 template <typename T, typename A>
 __global__ void __launch_bounds__(kThreads) energy_grad_kernel(ModelDev md, const T* __restrict__ m,
                                                                T* __restrict__ g, T* __restrict__ s,
                                                                double* part, unsigned* counter, double* out,
-                                                               int* status) {
+                                                               int* status, int euclid) {
   __shared__ Tile<T> tile;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   load_tile(m, md.N, md.L1, md.L2, x0, y0, tile);
@@ -64,7 +65,8 @@ __global__ void __launch_bounds__(kThreads) energy_grad_kernel(ModelDev md, cons
       const A mz = (A)tile.v[2][ly + kHalo][lx + kHalo];
       hz += (A)(-md.muB) - (A)(2.0 * md.K) * mz;
       const A si = mx * hx + my * hy + mz * hz;
-      const A gxv = hx - si * mx, gyv = hy - si * my, gzv = hz - si * mz;
+      const A pr = euclid ? (A)0 : si;
+      const A gxv = hx - pr * mx, gyv = hy - pr * my, gzv = hz - pr * mz;
       const size_t i = (size_t)gy * md.L1 + gx;
       if (g) {
         g[i] = (T)gxv;
@@ -155,6 +157,36 @@ __global__ void __launch_bounds__(kThreads) hvp_kernel(ModelDev md, const T* __r
   }
 }
 
+// (hess E v)_i = h_i(v) - 2 K v_iz z for nvec vectors: the Euclidean Hessian
+// of the quadratic energy, the same at every m (no projection, no s term).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) euclid_hvp_kernel(ModelDev md, const T* __restrict__ V, size_t ldv,
+                                                              T* __restrict__ HV, size_t ldhv, int nvec) {
+  __shared__ Tile<T> tile;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
+  const int lx = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const size_t N = md.N;
+  for (int j = 0; j < nvec; ++j) {
+    const T* v = V + (size_t)j * ldv;
+    T* hv = HV + (size_t)j * ldhv;
+    if (j > 0) __syncthreads();
+    load_tile(v, md.N, md.L1, md.L2, x0, y0, tile);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kTileRowsPerThread; ++r) {
+      const int ly = wy * kTileRowsPerThread + r;
+      if (x0 + lx >= md.L1 || y0 + ly >= md.L2) continue;
+      T hx, hy, hz;
+      linear_field<T>(md, tile, lx, ly, hx, hy, hz);
+      hz -= (T)(2.0 * md.K) * tile.v[2][ly + kHalo][lx + kHalo];
+      const size_t i = (size_t)(y0 + ly) * md.L1 + (x0 + lx);
+      hv[i] = hx;
+      hv[N + i] = hy;
+      hv[2 * N + i] = hz;
+    }
+  }
+}
+
 // Berg-Luescher charge: per site the up triangle (i, i+a1, i+a2) and the down
 // triangle (i+a1, i+a1+a2, i+a2); Omega = 2 atan2(a.(b x c), 1+a.b+b.c+c.a);
 // Q = -(1/4 pi) sum Omega.
@@ -230,11 +262,17 @@ int tile_blocks(const ModelDev& md) {
 
 template <typename T>
 void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
-                        int* status, bool fp64_arith, cudaStream_t st) {
+                        int* status, bool fp64_arith, cudaStream_t st, bool euclid) {
+  const int e = euclid ? 1 : 0;
   if (fp64_arith)
-    energy_grad_kernel<T, double><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status);
+    energy_grad_kernel<T, double><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e);
   else
-    energy_grad_kernel<T, T><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status);
+    energy_grad_kernel<T, T><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e);
+}
+
+template <typename T>
+void launch_euclid_hvp(const ModelDev& md, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec, cudaStream_t st) {
+  euclid_hvp_kernel<T><<<tile_grid(md), kThreads, 0, st>>>(md, V, ldv, HV, ldhv, nvec);
 }
 
 template <typename T>
@@ -250,7 +288,8 @@ void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter
 
 #define INST(T)                                                                                               \
   template void launch_energy_grad<T>(const ModelDev&, const T*, T*, T*, double*, unsigned*, double*, int*,  \
-                                      bool, cudaStream_t);                                                    \
+                                      bool, cudaStream_t, bool);                                              \
+  template void launch_euclid_hvp<T>(const ModelDev&, const T*, size_t, T*, size_t, int, cudaStream_t);      \
   template void launch_hvp<T>(const ModelDev&, const T*, const T*, const T*, size_t, T*, size_t, int,        \
                               const int*, int, cudaStream_t);                                                 \
   template void launch_topo<T>(const ModelDev&, const T*, double*, unsigned*, double*, cudaStream_t);

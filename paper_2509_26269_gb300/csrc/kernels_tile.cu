@@ -242,7 +242,7 @@ template <typename T, int MODE, int R, int CW, int NRL, int TB>
 __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     tile2d_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int nx, int ny,
                   int u0, int nu, size_t n, const double* __restrict__ C, T* __restrict__ Yout, size_t ldo, double* out,
-                  double* part, unsigned* counter, int nst, const int* gate, int mask, int* status) {
+                  double* part, unsigned* counter, int nst, int tps, const int* gate, int mask, int* status) {
   if (gate && (*gate & mask)) return;
   typedef TileT<T> TT;
   typedef typename TT::Acc Acc;
@@ -271,14 +271,17 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   unsigned char* ring_ptr = smem_raw + (ring - raw);
   const int nxp = (nx + 7) & ~7;
   const uint32_t yoff = (uint32_t)nxp * TB;
-  const uint32_t stage_bytes = yoff + 8u * TB;
-  const unsigned tx_bytes = (unsigned)((nx + (MODE == 3 ? 0 : ny)) * TB);
+  const uint32_t tile_b = yoff + (MODE == 3 ? 0u : 8u * TB);  // one tile of a stage
+  const uint32_t stage_bytes = (uint32_t)tps * tile_b;
+  const unsigned tx_bytes = (unsigned)(tps * (nx + (MODE == 3 ? 0 : ny)) * TB);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int na = kGramMode ? nx : ny;
 
-  const size_t ntiles = (n + TE - 1) / TE;
-  const size_t t_begin = ntiles * blockIdx.x / gridDim.x;
-  const size_t t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+  // the block's contiguous range of stage groups (tps tiles each; tiles past
+  // the end of the fields read zeros and store nothing)
+  const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
+  const size_t t_begin = ngroups * blockIdx.x / gridDim.x;
+  const size_t t_end = ngroups * (blockIdx.x + 1) / gridDim.x;
   const int ntile = (int)(t_end - t_begin);
 
   if (MODE != 0)
@@ -323,9 +326,11 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         if (*(volatile int*)&abort_flag) break;
         unsigned char* buf = ring_ptr + (size_t)s * stage_bytes;
         mbar_expect_tx(&full[s], tx_bytes);
-        const int x = (int)((t_begin + it) * TE);
-        tma_load_2d(buf, &tmX, x, 0, &full[s]);
-        if (MODE != 3) tma_load_2d(buf + yoff, &tmY, x, 0, &full[s]);
+        for (int q = 0; q < tps; ++q) {
+          const int x = (int)(((t_begin + it) * tps + q) * TE);
+          tma_load_2d(buf + (size_t)q * tile_b, &tmX, x, 0, &full[s]);
+          if (MODE != 3) tma_load_2d(buf + (size_t)q * tile_b + yoff, &tmY, x, 0, &full[s]);
+        }
       }
     }
   } else {
@@ -354,10 +359,11 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         if (status) atomicOr(status, kStatusTimeout);
       }
       if (*(volatile int*)&abort_flag) break;
-      const uint32_t sb = ring + (uint32_t)s * stage_bytes;
+      for (int qt = 0; qt < tps; ++qt) {
+      const uint32_t sb = ring + (uint32_t)s * stage_bytes + (uint32_t)qt * tile_b;
       if (MODE != 0) {
         const uint32_t xa = sb + lane_b, ya = sb + yoff + lane_b;
-        const size_t el = (size_t)(t_begin + it) * TE + (size_t)g * (TE / 2) + (size_t)lane * EL;
+        const size_t el = ((t_begin + it) * tps + qt) * TE + (size_t)g * (TE / 2) + (size_t)lane * EL;
         T yv[8][EL];
         if constexpr (kF32) {
           float2 p[4][EL];
@@ -437,11 +443,6 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
           gram_chunk<NS, NR, NC>(acc, xv, yw);
         }
       }
-      // free the stage; the generic-proxy writes of mode 1 are ordered before
-      // the next tensor copy into it
-      if (MODE == 1) fence_async_shared();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
       if (kF32 && ++since == kFlushT) {
         since = 0;
         if constexpr (kGramMode && kF32) {
@@ -463,6 +464,12 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
           }
         }
       }
+      }  // tiles of the stage
+      // free the stage; the generic-proxy writes of mode 1 are ordered before
+      // the next tensor copy into it
+      if (MODE == 1) fence_async_shared();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
     }
     if constexpr (MODE >= 2 && kF32) {
 #pragma unroll
@@ -572,7 +579,13 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
                  int mask, int* status, cudaStream_t st) {
   constexpr int TE = TB / (int)sizeof(T);
   const int nxp = (nx + 7) & ~7;
-  const size_t stage_bytes = (size_t)(nxp + 8) * TB;
+  const size_t tile_b = (size_t)(nxp + (MODE == 3 ? 0 : 8)) * TB;
+  const size_t loaded = (size_t)(nx + (MODE == 3 ? 0 : ny)) * TB;
+  // tiles per stage: a stage costs one CTA a roughly fixed handshake, so it
+  // should move 16 KB or more, while two stages per warp pair still fit
+  int tps = 1;
+  while (tps < 4 && loaded * tps < 16384 && (size_t)2 * tps * tile_b * (2 * kPairs) <= kDynBudget - 1024) tps *= 2;
+  const size_t stage_bytes = tps * tile_b;
   int nst = (int)((kDynBudget - 1024) / stage_bytes);
   if (nst > kMaxStages) nst = kMaxStages;
   nst -= nst % kPairs;  // a stage always goes to the same warp pair
@@ -587,10 +600,10 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   size_t want = kSMs;
   const size_t cap = (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K / ((size_t)na * ny);
   if (want > cap) want = cap;
-  const size_t ntiles = (n + TE - 1) / TE;
-  const int grid = (int)(ntiles < want ? (ntiles > 0 ? ntiles : 1) : want);
+  const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
+  const int grid = (int)(ngroups < want ? (ngroups > 0 ? ngroups : 1) : want);
   tile2d_kernel<T, MODE, R, CW, NRL, TB><<<grid, kThrT, smem, st>>>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out,
-                                                                    part, counter, nst, gate, mask, status);
+                                                                    part, counter, nst, tps, gate, mask, status);
 }
 
 template <typename T, int MODE, int TB>
@@ -601,17 +614,17 @@ void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny,
   tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out, part, counter, gate, mask, \
                                        status, st)
   if constexpr (MODE >= 2) {
-    TL(1, 8, 32);
+    TL(1, 4, 16);
   } else if (nx <= 8) {
     TL(1, 2, 8);
   } else if (nx <= 16) {
     TL(1, 4, 16);
   } else if (nx <= 32) {
-    TL(1, 8, 32);
+    TL(2, 4, 16);
   } else if (nx <= 64) {
-    TL(2, 8, 32);
+    TL(4, 4, 16);
   } else {
-    TL(3, 8, 32);
+    TL(6, 4, 16);
   }
 #undef TL
 }

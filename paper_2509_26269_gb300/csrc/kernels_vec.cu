@@ -282,18 +282,30 @@ __device__ __forceinline__ void amax_merge(double& a, double& ai, double& av, do
 }
 
 // pass 1: V_c <- P(V_c); partials per block and vector: |V_c|^2, max |entry|,
-// its flat index, its signed value.
+// its flat index, its signed value.  Per-thread shares are kept in the field
+// precision (a thread sees ~40 entries; comparisons of |entries| are exact in
+// either precision) and promoted to FP64 for the cross-thread reductions.
+template <typename A>
+__device__ __forceinline__ void amax_merge_t(A& a, int& ai, A& av, A b, int bi, A bv) {
+  if (b > a || (b == a && bi < ai)) {
+    a = b;
+    ai = bi;
+    av = bv;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__ m, T* V, size_t ldv, int k, int N,
                                                            double* part, unsigned* counter, double* scal,
                                                            const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
-  double nrm[MOTO_MAX_K], amx[MOTO_MAX_K], aidx[MOTO_MAX_K], aval[MOTO_MAX_K];
+  T nrm_t[MOTO_MAX_K], amx_t[MOTO_MAX_K], aval_t[MOTO_MAX_K];
+  int aidx_t[MOTO_MAX_K];
   for (int c = 0; c < k; ++c) {
-    nrm[c] = 0.0;
-    amx[c] = -1.0;
-    aidx[c] = 1e300;
-    aval[c] = 0.0;
+    nrm_t[c] = (T)0;
+    amx_t[c] = (T)-1;
+    aidx_t[c] = 0x7fffffff;
+    aval_t[c] = (T)0;
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
@@ -307,11 +319,18 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
       v[i] = a0;
       v[N + i] = a1;
       v[2 * (size_t)N + i] = a2;
-      nrm[c] += (double)a0 * a0 + (double)a1 * a1 + (double)a2 * a2;
-      amax_merge(amx[c], aidx[c], aval[c], fabs((double)a0), (double)i, (double)a0);
-      amax_merge(amx[c], aidx[c], aval[c], fabs((double)a1), (double)N + i, (double)a1);
-      amax_merge(amx[c], aidx[c], aval[c], fabs((double)a2), 2.0 * N + i, (double)a2);
+      nrm_t[c] += a0 * a0 + a1 * a1 + a2 * a2;
+      amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a0), i, a0);
+      amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a1), N + i, a1);
+      amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a2), 2 * N + i, a2);
     }
+  }
+  double nrm[MOTO_MAX_K], amx[MOTO_MAX_K], aidx[MOTO_MAX_K], aval[MOTO_MAX_K];
+  for (int c = 0; c < k; ++c) {
+    nrm[c] = (double)nrm_t[c];
+    amx[c] = (double)amx_t[c];
+    aidx[c] = aidx_t[c] == 0x7fffffff ? 1e300 : (double)aidx_t[c];
+    aval[c] = (double)aval_t[c];
   }
   __shared__ double sh[kThreads / 32][4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -415,106 +434,124 @@ void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int 
 // the |T| estimate with block row j (sum of |A| and |R_j| row entries plus the
 // largest new diagonal) and tests for breakdown (smallest diagonal of the
 // factor <= rel_tol * |T|).  Pass 2 composes R and stores it in T.
-__global__ void cholqr_kernel(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T,
-                              int ldT, DevState* st, double rel_tol) {
+// 64 threads, thread t = (r, c) = (t / 8, t % 8): the right-looking
+// factorisation, the triangular inverse (one column per thread) and the
+// product keep the dependent FP64 chain to a few dozen operations.
+__global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int second, int j, double* Rinv,
+                                                    double* Racc, double* T, int ldT, DevState* st, double rel_tol) {
   if (st->gate & (kGateKrylov | kGateDone)) return;
   // j >= 0: block Lanczos step j; j == -1: start block; j == -2: LOBPCG block
-  if (threadIdx.x != 0) return;
-  double L[MOTO_MAX_K][MOTO_MAX_K];
-  bool ok = true;
-  for (int r = 0; r < b; ++r) {
-    for (int c = 0; c <= r; ++c) {
-      double a = 0.5 * (G[r * b + c] + G[c * b + r]);
-      for (int t = 0; t < c; ++t) a -= L[r][t] * L[c][t];
-      if (r == c) {
-        if (!(a > 0.0)) {
-          ok = false;
-          a = 1.0;
+  __shared__ double Ls[MOTO_MAX_K][MOTO_MAX_K], Gs[MOTO_MAX_K][MOTO_MAX_K], Us[MOTO_MAX_K][MOTO_MAX_K];
+  __shared__ double dinv[MOTO_MAX_K], rsum[MOTO_MAX_K];
+  __shared__ int bad, verdict;  // verdict: 0 go on, 1 stop (gate set), 2 LOBPCG column scaling
+  const int t = threadIdx.x, r = t >> 3, c = t & 7;
+  const bool in = r < b && c < b;
+  if (t == 0) bad = 0;
+  if (in) {
+    Gs[r][c] = 0.5 * (G[r * b + c] + G[c * b + r]);
+    Ls[r][c] = 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < b; ++k) {
+    if (t == 0) {
+      double d = Gs[k][k];
+      if (!(d > 0.0)) {
+        bad = 1;
+        d = 1.0;
+      }
+      Ls[k][k] = sqrt(d);
+      dinv[k] = 1.0 / Ls[k][k];
+    }
+    __syncthreads();
+    if (c == k && r > k && r < b) Ls[r][k] = Gs[r][k] * dinv[k];
+    __syncthreads();
+    if (r < b && c > k && c <= r) Gs[r][c] -= Ls[r][k] * Ls[c][k];
+    __syncthreads();
+  }
+  if (!second && j >= 0 && t < b) {
+    double a = 0.0;
+    for (int cc = 0; cc < b; ++cc) {
+      a += fabs(T[(size_t)(j * b + t) * ldT + j * b + cc]);
+      if (j > 0) a += fabs(T[(size_t)(j * b + t) * ldT + (j - 1) * b + cc]);
+    }
+    rsum[t] = a;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double dmin = 1e300, dmax = 0.0;
+    for (int k = 0; k < b; ++k) {
+      dmin = fmin(dmin, Ls[k][k]);
+      dmax = fmax(dmax, Ls[k][k]);
+    }
+    int v = 0;
+    if (!second && j >= 0) {
+      double rs = 0.0;
+      for (int k = 0; k < b; ++k) rs = fmax(rs, rsum[k]);
+      st->tnorm = fmax(st->tnorm, rs + dmax);
+      if (bad || dmin <= rel_tol * st->tnorm) {
+        st->gate |= kGateKrylov;
+        v = 1;
+      }
+    } else {
+      bool dep = bad != 0;
+      for (int k = 0; k < b && !dep; ++k)
+        if (Ls[k][k] <= 1e-6 * sqrt(fmax(G[k * b + k], 0.0))) dep = true;
+      if (dep) {
+        if (j == -2) {
+          v = 2;
+        } else {
+          st->gate |= kGateKrylov;
+          if (j < 0) st->status |= kStatusBreakdown;
+          v = 1;
         }
-        L[r][r] = sqrt(a);
-      } else {
-        L[r][c] = a / L[c][c];
       }
     }
-    for (int c = r + 1; c < b; ++c) L[r][c] = 0.0;
+    verdict = v;
   }
-  double dmin = 1e300, dmax = 0.0;
-  for (int r = 0; r < b; ++r) {
-    dmin = fmin(dmin, L[r][r]);
-    dmax = fmax(dmax, L[r][r]);
-  }
-  if (!second && j >= 0) {
-    double rs = 0.0;
-    for (int r = 0; r < b; ++r) {
-      double a = 0.0;
-      for (int c = 0; c < b; ++c) {
-        a += fabs(T[(size_t)(j * b + r) * ldT + j * b + c]);
-        if (j > 0) a += fabs(T[(size_t)(j * b + r) * ldT + (j - 1) * b + c]);
-      }
-      rs = fmax(rs, a);
-    }
-    st->tnorm = fmax(st->tnorm, rs + dmax);
-    if (!ok || dmin <= rel_tol * st->tnorm) {
-      st->gate |= kGateKrylov;
-      return;
-    }
-  } else if (!ok || [&] {
-               for (int r = 0; r < b; ++r)
-                 if (L[r][r] <= 1e-6 * sqrt(fmax(G[r * b + r], 0.0))) return true;
-               return false;
-             }()) {
-    if (j == -2) {
-      // LOBPCG residual block: fall back to column scaling; the SVQB step of
-      // the Rayleigh-Ritz drops what stays dependent
-      for (int r = 0; r < b; ++r)
-        for (int c = 0; c < b; ++c) Rinv[r * b + c] = (r == c) ? (G[r * b + r] > 0.0 ? 1.0 / sqrt(G[r * b + r]) : 1.0) : 0.0;
-      return;
-    }
-    st->gate |= kGateKrylov;
-    if (j < 0) st->status |= kStatusBreakdown;
+  __syncthreads();
+  if (verdict == 1) return;
+  if (verdict == 2) {
+    // LOBPCG residual block: fall back to column scaling; the SVQB step of
+    // the Rayleigh-Ritz drops what stays dependent
+    if (in) Rinv[r * b + c] = (r == c) ? (G[r * b + r] > 0.0 ? 1.0 / sqrt(G[r * b + r]) : 1.0) : 0.0;
     return;
   }
-  // Rinv = (L^T)^{-1}, upper triangular: solve L^T X = I
-  double U[MOTO_MAX_K][MOTO_MAX_K];
-  for (int c = 0; c < b; ++c) {
-    for (int r = b - 1; r >= 0; --r) {
-      double a = (r == c) ? 1.0 : 0.0;
-      for (int t = r + 1; t < b; ++t) a -= L[t][r] * U[t][c];
-      U[r][c] = a / L[r][r];
+  // Rinv = (L^T)^{-1}, upper triangular: column cc solves L^T x = e_cc
+  if (t < b) {
+    const int cc = t;
+    for (int rr = b - 1; rr >= 0; --rr) {
+      double a = (rr == cc) ? 1.0 : 0.0;
+      for (int q = rr + 1; q <= cc; ++q) a -= Ls[q][rr] * Us[q][cc];
+      Us[rr][cc] = (rr <= cc) ? a * dinv[rr] : 0.0;
     }
   }
-  for (int r = 0; r < b; ++r)
-    for (int c = 0; c < b; ++c) Rinv[r * b + c] = U[r][c];
+  __syncthreads();
+  if (in) Rinv[r * b + c] = Us[r][c];
   if (!second) {
-    for (int r = 0; r < b; ++r)
-      for (int c = 0; c < b; ++c) Racc[r * b + c] = L[c][r];  // R1 = L^T
-  } else {
-    double R[MOTO_MAX_K][MOTO_MAX_K];
-    for (int r = 0; r < b; ++r)
-      for (int c = 0; c < b; ++c) {
-        double a = 0.0;
-        for (int t = 0; t < b; ++t) a += L[t][r] * Racc[t * b + c];  // (L2^T R1)[r][c]
-        R[r][c] = a;
-      }
-    for (int r = 0; r < b; ++r)
-      for (int c = 0; c < b; ++c) Racc[r * b + c] = R[r][c];
+    if (in) Racc[r * b + c] = Ls[c][r];  // R1 = L^T
+    return;
+  }
+  // R = L2^T R1 (R1 read completely before it is overwritten)
+  double Rv = 0.0;
+  if (in)
+    for (int q = 0; q < b; ++q) Rv += Ls[q][r] * Racc[q * b + c];
+  __syncthreads();
+  if (in) {
+    Racc[r * b + c] = Rv;
     if (j >= 0) {
-      for (int r = 0; r < b; ++r)
-        for (int c = 0; c < b; ++c) {
-          T[(size_t)((j + 1) * b + r) * ldT + j * b + c] = R[r][c];
-          T[(size_t)(j * b + c) * ldT + (j + 1) * b + r] = R[r][c];
-        }
+      T[(size_t)((j + 1) * b + r) * ldT + j * b + c] = Rv;
+      T[(size_t)(j * b + c) * ldT + (j + 1) * b + r] = Rv;
     }
-    if (j >= -1) {
-      st->steps += 1;
-      st->nT = st->steps * b;
-    }
+  }
+  if (t == 0 && j >= -1) {
+    st->steps += 1;
+    st->nT = st->steps * b;
   }
 }
 
 void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T, int ldT,
                    DevState* st, double rel_tol, cudaStream_t s) {
-  cholqr_kernel<<<1, 32, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol);
+  cholqr_kernel<<<1, 64, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol);
 }
 
 // Cyclic Jacobi with round-robin (parallel) ordering on an n x n symmetric
