@@ -226,6 +226,45 @@ int moto_descend(moto_ctx* ctx, const void* m_saddle_dev, const void* v1_dev,
 
 /* Device status word of the context (synchronises the stream): MOTO_OK or
  * the first device-detected error since the last moto_clear_status. */
+/* ------------------------------------------------------------------------
+ * Batched walkers.  The paper runs the bilayer MMF kernel on many perturbed
+ * starting points (Alg. 1, one walker per explorer proposal); the batch
+ * advances n independent walkers together on one GPU.  Each walker has its
+ * own lattice size (the model strengths are shared) and its own context
+ * (workspace sized at creation); one outer step of all walkers is captured
+ * once into a CUDA graph, fanned out over n_streams streams, and replayed
+ * until every walker has stopped.  Walkers never exchange data.
+ * ------------------------------------------------------------------------ */
+typedef struct moto_batch moto_batch;
+typedef struct {
+  int L1, L2;   /* lattice of this walker (L >= 5) */
+  void* m_dev;  /* 3N unit spins, caller-owned, updated in place */
+  void* V_dev;  /* max(k, block) x 3N mode block: start block in, modes out */
+} moto_walker;
+
+/* Creates one context per walker (MOTO_ERR_NOMEM if any allocation fails;
+ * nothing is kept then).  model->L1/L2 are ignored; walkers[i].L1/L2 are
+ * used.  Buffers stay bound to the batch until moto_batch_destroy. */
+int moto_batch_create(const moto_model* model, int dtype, const moto_params* params, const moto_walker* walkers,
+                      int n_walkers, int n_streams, moto_batch** out);
+void moto_batch_destroy(moto_batch* batch);
+
+/* MMF ascent of every walker (as moto_ascend, params->max_steps outer steps
+ * at most, the stopping test read every check_every steps).  rec_dev (n x 6
+ * doubles, device): per walker [E, max_i|F_mmf,i|, lambda_1, lambda_2,
+ * max_i|g_i|, g.v1] at its last test.  status_host / steps_host (n ints,
+ * host, optional): MOTO_OK at a saddle, MOTO_NOT_CONVERGED at the cap, or
+ * the walker's error; outer steps taken.  Synchronous.  Returns the worst
+ * walker code. */
+int moto_batch_ascend(moto_batch* batch, int check_every, double* rec_dev, int* status_host, int* steps_host,
+                      void* stream);
+
+/* Two-sided descent (as moto_descend) from every walker's current spins and
+ * first mode: m_plus[i], m_minus[i] (3N each, device) receive the two
+ * minima; out_dev (n x 6 doubles): [E+, Q+, E-, Q-, steps+, steps-]. */
+int moto_batch_descend(moto_batch* batch, void* const* m_plus, void* const* m_minus, double* out_dev,
+                       int* status_host, void* stream);
+
 int moto_status(moto_ctx* ctx, void* stream);
 int moto_clear_status(moto_ctx* ctx, void* stream);
 

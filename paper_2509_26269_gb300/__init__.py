@@ -39,6 +39,10 @@ class moto_params(ctypes.Structure):
     ]
 
 
+class moto_walker(ctypes.Structure):
+    _fields_ = [("L1", ctypes.c_int), ("L2", ctypes.c_int), ("m_dev", ctypes.c_void_p), ("V_dev", ctypes.c_void_p)]
+
+
 class MotoError(RuntimeError):
     pass
 
@@ -73,6 +77,11 @@ def _load():
         "moto_energy_grad_noalloc": (I, [ctypes.POINTER(moto_model), I, P, P, P, P, P]),
         "moto_gram": (I, [P, P, Z, I, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
+        "moto_batch_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params),
+                                  ctypes.POINTER(moto_walker), I, I, ctypes.POINTER(P)]),
+        "moto_batch_destroy": (None, [P]),
+        "moto_batch_ascend": (I, [P, I, P, P, P, P]),
+        "moto_batch_descend": (I, [P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -87,6 +96,7 @@ EXPORTED = (
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
+    "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig")
 
@@ -244,6 +254,43 @@ def moto_energy_grad_noalloc(model: moto_model, dtype: int, m, g=None, s=None, o
                                          _stream(stream)), "moto_energy_grad_noalloc")
 
 
+def moto_batch_create(model: moto_model, dtype: int, params: moto_params, walkers, n_streams=8) -> int:
+    """walkers: sequence of (L1, L2, m, V) with m, V CUDA tensors or device pointers."""
+    arr = (moto_walker * len(walkers))()
+    for i, (L1, L2, m, V) in enumerate(walkers):
+        arr[i].L1, arr[i].L2, arr[i].m_dev, arr[i].V_dev = int(L1), int(L2), _ptr(m), _ptr(V)
+    h = ctypes.c_void_p()
+    _check(_lib.moto_batch_create(ctypes.byref(model), int(dtype), ctypes.byref(params), arr, len(walkers),
+                                  int(n_streams), ctypes.byref(h)), "moto_batch_create")
+    return h.value
+
+
+def moto_batch_destroy(batch: int) -> None:
+    _lib.moto_batch_destroy(batch)
+
+
+def moto_batch_ascend(batch, n, rec, check_every=10, stream=None):
+    """Returns (code, per-walker codes, per-walker steps)."""
+    status = (ctypes.c_int * n)()
+    steps = (ctypes.c_int * n)()
+    rc = _lib.moto_batch_ascend(batch, int(check_every), _ptr(rec), ctypes.cast(status, ctypes.c_void_p),
+                                ctypes.cast(steps, ctypes.c_void_p), _stream(stream))
+    _check(rc, "moto_batch_ascend", ok=(MOTO_OK, MOTO_NOT_CONVERGED))
+    return rc, list(status), list(steps)
+
+
+def moto_batch_descend(batch, m_plus, m_minus, out, stream=None):
+    """m_plus, m_minus: sequences of CUDA tensors; returns (code, per-walker codes)."""
+    n = len(m_plus)
+    mp = (ctypes.c_void_p * n)(*[_ptr(x) for x in m_plus])
+    mm = (ctypes.c_void_p * n)(*[_ptr(x) for x in m_minus])
+    status = (ctypes.c_int * n)()
+    rc = _lib.moto_batch_descend(batch, ctypes.cast(mp, ctypes.c_void_p), ctypes.cast(mm, ctypes.c_void_p),
+                                 _ptr(out), ctypes.cast(status, ctypes.c_void_p), _stream(stream))
+    _check(rc, "moto_batch_descend", ok=(MOTO_OK, MOTO_NOT_CONVERGED))
+    return rc, list(status)
+
+
 def moto_profile_begin(ctx, capacity=8192):
     _check(_lib.moto_profile_begin(ctx, int(capacity)), "moto_profile_begin")
 
@@ -259,5 +306,5 @@ def moto_profile_end(ctx):
     return {k: (launches[i], ms[i], nbytes[i]) for i, k in enumerate(PROFILE_KINDS)}
 
 
-from .context import Context  # noqa: E402,F401
+from .context import Batch, Context  # noqa: E402,F401
 from .autograd import MotoEnergy, energy  # noqa: E402,F401

@@ -6,9 +6,10 @@ from __future__ import annotations
 
 import torch
 
-from . import (MOTO_F32, MOTO_F64, MOTO_MAX_BASIS, make_model, make_params, moto_ascend, moto_create,
-               moto_descend, moto_destroy, moto_energy, moto_energy_grad, moto_hvp, moto_lbfgs_reset,
-               moto_lowest_modes, moto_mmf_step, moto_topo_charge, moto_workspace_bytes)
+from . import (MOTO_F32, MOTO_F64, MOTO_MAX_BASIS, make_model, make_params, moto_ascend, moto_batch_ascend,
+               moto_batch_create, moto_batch_descend, moto_batch_destroy, moto_create, moto_descend, moto_destroy,
+               moto_energy, moto_energy_grad, moto_hvp, moto_lbfgs_reset, moto_lowest_modes, moto_mmf_step,
+               moto_topo_charge, moto_workspace_bytes)
 
 
 class Context:
@@ -104,6 +105,49 @@ class Context:
     def close(self):
         if getattr(self, "handle", None):
             moto_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent MMF walkers advanced together (``moto_batch_*``).  ``walkers``
+    is a list of (m, V): spins (3, L2, L1) and start block (nv, 3, L2, L1), all
+    of one dtype on one device; both are updated in place."""
+
+    def __init__(self, walkers, J=(1.0,), D=0.0, K=0.0, muB=0.0, dtype=torch.float32, n_streams=8, **params):
+        self.walkers = [(m, V) for m, V in walkers]
+        self.dtype = dtype
+        self.device = self.walkers[0][0].device
+        self.params = make_params(**params)
+        code = MOTO_F64 if dtype == torch.float64 else MOTO_F32
+        desc = []
+        for m, V in self.walkers:
+            if m.dtype != dtype or V.dtype != dtype or not m.is_contiguous() or not V.is_contiguous():
+                raise TypeError("walker tensors must be contiguous and of the batch dtype")
+            desc.append((m.shape[-1], m.shape[-2], m, V))
+        with torch.cuda.device(self.device):
+            self.handle = moto_batch_create(make_model(5, 5, J, D, K, muB), code, self.params, desc, n_streams)
+
+    def ascend(self, check_every=10):
+        rec = torch.full((len(self.walkers), 6), float("nan"), dtype=torch.float64, device=self.device)
+        rc, status, steps = moto_batch_ascend(self.handle, len(self.walkers), rec, check_every)
+        return rc, status, steps, rec
+
+    def descend(self):
+        mp = [torch.empty_like(m) for m, _ in self.walkers]
+        mm = [torch.empty_like(m) for m, _ in self.walkers]
+        out = torch.full((len(self.walkers), 6), float("nan"), dtype=torch.float64, device=self.device)
+        rc, status = moto_batch_descend(self.handle, mp, mm, out)
+        return rc, status, mp, mm, out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            moto_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

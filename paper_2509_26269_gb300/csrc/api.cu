@@ -965,3 +965,319 @@ extern "C" int moto_gram(moto_ctx* c, const void* X, size_t ldx, int nx, const v
   CK(cudaGetLastError());
   return MOTO_OK;
 }
+
+// ============================================================================
+// Batched walkers: many independent MMF walkers (one context each, any mix of
+// lattice sizes) advanced together.  One outer step of every walker is
+// captured once into a CUDA graph whose walkers fan out over n_streams
+// streams, so the small kernels of many walkers run concurrently; the graph
+// is replayed until every walker has stopped.  A walker that met its stopping
+// test sets its done gate on the device, after which its nodes return at once
+// (the graph never needs re-capturing).  Every check_every replays one packed
+// copy of all walkers' [converged, status, steps] words reaches the host.
+// ============================================================================
+namespace {
+
+__global__ void batch_flags_kernel(DevState* const* sts, int n, int* flags) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const DevState* s = sts[i];
+    flags[3 * i] = s->converged;
+    flags[3 * i + 1] = s->status;
+    flags[3 * i + 2] = s->pad[1];
+  }
+}
+
+__global__ void batch_reset_kernel(DevState* const* sts, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    DevState* st = sts[i];
+    st->gate = 0;
+    st->pad[1] = 0;
+    st->lb_head = 0;
+    st->lb_count = 0;
+    st->lb_have_prev = 0;
+    st->converged = 0;
+    st->iters = 0;
+  }
+}
+
+int status_of(int flags_status) {
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  h.status = flags_status;
+  return status_code(h);
+}
+
+}  // namespace
+
+struct moto_batch {
+  int n = 0, dtype = 0, nstreams = 1;
+  moto_params p;
+  moto_ctx** ctx = nullptr;
+  void** m = nullptr;
+  void** V = nullptr;
+  DevState** sts_dev = nullptr;  // device array of the walkers' state words
+  int* flags_dev = nullptr;
+  int* flags_host = nullptr;  // pinned
+  double* rec_scratch = nullptr;  // n x 6 doubles (descent records)
+  cudaStream_t master = nullptr;
+  cudaStream_t* streams = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t* join = nullptr;
+};
+
+namespace {
+
+void batch_free(moto_batch* b) {
+  if (!b) return;
+  if (b->ctx)
+    for (int i = 0; i < b->n; ++i) moto_destroy(b->ctx[i]);
+  if (b->streams)
+    for (int k = 0; k < b->nstreams; ++k)
+      if (b->streams[k]) cudaStreamDestroy(b->streams[k]);
+  if (b->join)
+    for (int k = 0; k < b->nstreams; ++k)
+      if (b->join[k]) cudaEventDestroy(b->join[k]);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->master) cudaStreamDestroy(b->master);
+  if (b->sts_dev) cudaFree(b->sts_dev);
+  if (b->flags_dev) cudaFree(b->flags_dev);
+  if (b->rec_scratch) cudaFree(b->rec_scratch);
+  if (b->flags_host) cudaFreeHost(b->flags_host);
+  delete[] b->ctx;
+  delete[] b->m;
+  delete[] b->V;
+  delete[] b->streams;
+  delete[] b->join;
+  delete b;
+}
+
+// Records one step of every walker (walker i on stream i % nstreams) and
+// the flag gather, forked from and joined into the master stream.
+template <typename T>
+int batch_record_step(moto_batch* b, bool ascent, double* rec, int rec_stride) {
+  CK(cudaEventRecord(b->fork, b->master));
+  for (int k = 0; k < b->nstreams; ++k) CK(cudaStreamWaitEvent(b->streams[k], b->fork, 0));
+  for (int i = 0; i < b->n; ++i) {
+    moto_ctx* c = b->ctx[i];
+    double* o = rec ? rec + (size_t)rec_stride * i : c->dsm + kTmp;
+    opt_step<T>(c, static_cast<T*>(b->m[i]), &b->p, ascent ? static_cast<T*>(b->V[i]) : nullptr, o, nullptr, ascent,
+                true, b->streams[i % b->nstreams]);
+  }
+  for (int k = 0; k < b->nstreams; ++k) {
+    CK(cudaEventRecord(b->join[k], b->streams[k]));
+    CK(cudaStreamWaitEvent(b->master, b->join[k], 0));
+  }
+  batch_flags_kernel<<<(b->n + 127) / 128, 128, 0, b->master>>>(b->sts_dev, b->n, b->flags_dev);
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+// Runs the captured step until every walker stopped or max_steps replays;
+// then one evaluation of the stopping test at the final iterate of the
+// walkers still running (as the one-walker loop does).
+template <typename T>
+int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double* rec, int rec_stride,
+              int* status_host, int* steps_host) {
+  if (check_every < 1) check_every = 1;
+  batch_reset_kernel<<<(b->n + 127) / 128, 128, 0, b->master>>>(b->sts_dev, b->n);
+  CK(cudaGetLastError());
+  int done = (max_steps == 0);
+  int t = 0;
+  if (!done) {
+    // first step uncaptured: it also sets the kernels' one-time attributes
+    int rc = batch_record_step<T>(b, ascent, rec, rec_stride);
+    if (rc) return rc;
+    t = 1;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (!done && t < max_steps) {
+    CK(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_record_step<T>(b, ascent, rec, rec_stride);
+    cudaError_t ce = cudaStreamEndCapture(b->master, &graph);
+    if (rc || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc ? rc : MOTO_ERR_CUDA;
+    }
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return MOTO_ERR_CUDA;
+    }
+  }
+  int rc = MOTO_OK;
+  while (!done) {
+    if (t % check_every == 0 || t >= max_steps) {
+      if (cudaMemcpyAsync(b->flags_host, b->flags_dev, 3 * sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->master) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(b->master) != cudaSuccess) {
+        rc = MOTO_ERR_CUDA;
+        break;
+      }
+      bool all = true;
+      for (int i = 0; i < b->n; ++i)
+        if (!b->flags_host[3 * i] && !status_of(b->flags_host[3 * i + 1])) all = false;
+      if (all || t >= max_steps) break;
+    }
+    if (cudaGraphLaunch(exec, b->master) != cudaSuccess) {
+      rc = MOTO_ERR_CUDA;
+      break;
+    }
+    ++t;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (rc) return rc;
+  // stopping test at the final iterate (no update) for walkers still running
+  for (int i = 0; i < b->n; ++i) {
+    moto_ctx* c = b->ctx[i];
+    double* o = rec ? rec + (size_t)rec_stride * i : c->dsm + kTmp;
+    opt_step<T>(c, static_cast<T*>(b->m[i]), &b->p, ascent ? static_cast<T*>(b->V[i]) : nullptr, o, nullptr, ascent,
+                false, b->master);
+  }
+  batch_flags_kernel<<<(b->n + 127) / 128, 128, 0, b->master>>>(b->sts_dev, b->n, b->flags_dev);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(b->flags_host, b->flags_dev, 3 * sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->master));
+  CK(cudaStreamSynchronize(b->master));
+  int result = MOTO_OK;
+  for (int i = 0; i < b->n; ++i) {
+    const int sc = status_of(b->flags_host[3 * i + 1]);
+    const int code = sc ? sc : (b->flags_host[3 * i] ? MOTO_OK : MOTO_NOT_CONVERGED);
+    if (status_host) status_host[i] = code;
+    if (steps_host) steps_host[i] = b->flags_host[3 * i + 2];
+    if (code < 0 && result >= 0) result = code;
+    if (code == MOTO_NOT_CONVERGED && result == MOTO_OK) result = MOTO_NOT_CONVERGED;
+  }
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+int moto_batch_create(const moto_model* model, int dtype, const moto_params* params, const moto_walker* walkers,
+                      int n_walkers, int n_streams, moto_batch** out) {
+  if (!model || !params || !walkers || !out || n_walkers < 1 || n_streams < 1) return MOTO_ERR_ARG;
+  for (int i = 0; i < n_walkers; ++i)
+    if (!walkers[i].m_dev || !walkers[i].V_dev) return MOTO_ERR_ARG;
+  *out = nullptr;
+  moto_batch* b = new moto_batch();
+  b->n = n_walkers;
+  b->dtype = dtype;
+  b->nstreams = std::min(n_streams, n_walkers);
+  b->p = *params;
+  b->ctx = new moto_ctx*[n_walkers]();
+  b->m = new void*[n_walkers];
+  b->V = new void*[n_walkers];
+  b->streams = new cudaStream_t[b->nstreams]();
+  b->join = new cudaEvent_t[b->nstreams]();
+  DevState** sts = new DevState*[n_walkers];
+  int rc = MOTO_OK;
+  for (int i = 0; i < n_walkers && !rc; ++i) {
+    moto_model mw = *model;
+    mw.L1 = walkers[i].L1;
+    mw.L2 = walkers[i].L2;
+    rc = moto_create(&mw, dtype, params, &b->ctx[i]);
+    if (!rc) {
+      b->m[i] = walkers[i].m_dev;
+      b->V[i] = walkers[i].V_dev;
+      sts[i] = b->ctx[i]->st;
+    }
+  }
+  if (!rc) {
+    bool ok = cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < b->nstreams; ++k)
+      ok = cudaStreamCreateWithFlags(&b->streams[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->sts_dev, sizeof(DevState*) * n_walkers) == cudaSuccess &&
+         cudaMalloc(&b->flags_dev, 3 * sizeof(int) * n_walkers) == cudaSuccess &&
+         cudaMalloc(&b->rec_scratch, 6 * sizeof(double) * n_walkers) == cudaSuccess &&
+         cudaMallocHost(&b->flags_host, 3 * sizeof(int) * n_walkers) == cudaSuccess &&
+         cudaMemcpy(b->sts_dev, sts, sizeof(DevState*) * n_walkers, cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) rc = MOTO_ERR_NOMEM;
+  }
+  delete[] sts;
+  if (rc) {
+    batch_free(b);
+    return rc;
+  }
+  *out = b;
+  return MOTO_OK;
+}
+
+void moto_batch_destroy(moto_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  batch_free(b);
+}
+
+int moto_batch_ascend(moto_batch* b, int check_every, double* rec_dev, int* status_host, int* steps_host,
+                      void* stream) {
+  if (!b || !rec_dev) return MOTO_ERR_ARG;
+  CK(cudaStreamSynchronize(S(stream)));
+  if (b->dtype == MOTO_F32)
+    return batch_run<float>(b, true, b->p.max_steps, check_every, rec_dev, 6, status_host, steps_host);
+  return batch_run<double>(b, true, b->p.max_steps, check_every, rec_dev, 6, status_host, steps_host);
+}
+
+int moto_batch_descend(moto_batch* b, void* const* m_plus, void* const* m_minus, double* out_dev, int* status_host,
+                       void* stream) {
+  if (!b || !m_plus || !m_minus || !out_dev) return MOTO_ERR_ARG;
+  for (int i = 0; i < b->n; ++i)
+    if (!m_plus[i] || !m_minus[i]) return MOTO_ERR_ARG;
+  CK(cudaStreamSynchronize(S(stream)));
+  // the walkers' spins and first modes are the saddles and their v1
+  void** saddle = new void*[b->n];
+  for (int i = 0; i < b->n; ++i) saddle[i] = b->m[i];
+  int result = MOTO_OK;
+  int* st_side = new int[b->n];
+  for (int side = 0; side < 2 && result >= 0; ++side) {
+    const double sign = side == 0 ? 1.0 : -1.0;
+    void* const* dst = side == 0 ? m_plus : m_minus;
+    for (int i = 0; i < b->n; ++i) {
+      moto_ctx* c = b->ctx[i];
+      if (b->dtype == MOTO_F32)
+        launch_descent_seed<float>((const float*)saddle[i], (const float*)b->V[i], b->p.eta_theta, sign,
+                                   (float*)dst[i], c->N, c->part, c->counter, c->dsm + kTmp, b->master);
+      else
+        launch_descent_seed<double>((const double*)saddle[i], (const double*)b->V[i], b->p.eta_theta, sign,
+                                    (double*)dst[i], c->N, c->part, c->counter, c->dsm + kTmp, b->master);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      result = MOTO_ERR_CUDA;
+      break;
+    }
+    // descend the copies: point the walkers at them for this side
+    for (int i = 0; i < b->n; ++i) b->m[i] = dst[i];
+    const int rc = b->dtype == MOTO_F32
+                       ? batch_run<float>(b, false, b->p.descent_max_steps, 25, nullptr, 0, st_side, nullptr)
+                       : batch_run<double>(b, false, b->p.descent_max_steps, 25, nullptr, 0, st_side, nullptr);
+    for (int i = 0; i < b->n; ++i) b->m[i] = saddle[i];
+    if (rc < 0) {
+      result = rc;
+      break;
+    }
+    for (int i = 0; i < b->n; ++i) {
+      moto_ctx* c = b->ctx[i];
+      double* o = out_dev + 6 * (size_t)i;
+      if (moto_energy(c, dst[i], o + 2 * side, b->master) || moto_topo_charge(c, dst[i], o + 2 * side + 1, b->master)) {
+        result = MOTO_ERR_CUDA;
+        break;
+      }
+      store_iters_kernel<<<1, 32, 0, b->master>>>(c->st, o + 4 + side);
+      if (status_host) {
+        const int prev = side == 0 ? MOTO_OK : status_host[i];
+        int code = st_side[i];
+        if (prev < 0 || (prev == MOTO_NOT_CONVERGED && code == MOTO_OK)) code = prev;
+        status_host[i] = code;
+      }
+    }
+    if (rc == MOTO_NOT_CONVERGED && result == MOTO_OK) result = MOTO_NOT_CONVERGED;
+  }
+  delete[] st_side;
+  delete[] saddle;
+  if (cudaStreamSynchronize(b->master) != cudaSuccess) return MOTO_ERR_CUDA;
+  return result;
+}
+
+}  // extern "C"
