@@ -1,18 +1,20 @@
 // Eigenpairs of the projected block-Lanczos matrix T (n <= 96, symmetric, band
-// width b) on one block.  GB300 executes dependent FP64 chains slowly, so FP64
-// is kept where it buys accuracy and FP32 does the search:
-//   1. Householder reduction to tridiagonal form Q^T T Q = tridiag(d, e) in the
-//      context precision R (skipped for b = 1, where T is tridiagonal);
+// width b) on one block.  GB300 executes FP64 slowly (a thin pipe shared by the
+// SM, and dependent chains on one thread are slower still), so FP64 is kept
+// where it buys accuracy and the context precision R does the rest:
+//   1. Householder reduction to tridiagonal form Q^T T Q = tridiag(d, e) in R
+//      (skipped for b = 1, where T is tridiagonal); three barriers per
+//      reflector: warp 0 forms it, every warp applies it to its rows;
 //   2. the lowest 16 eigenvalues located by FP32 bisection on the Sturm
 //      sequence of the characteristic polynomials
 //      p_r = (d_r - x) p_{r-1} - e_{r-1}^2 p_{r-2} (sign changes count the
 //      eigenvalues below x; rescaled to stay in range), one lane each;
-//   3. each located eigenvalue refined by FP64 inverse iteration on the
-//      tridiagonal matrix (LU with partial pivoting, three sweeps; vectors
-//      orthogonalised within clusters of close eigenvalues) and its FP64
-//      Rayleigh quotient;
-//   4. back-transformation of the k lowest eigenvectors (precision R) and, for
-//      them, FP64 Rayleigh quotients with the original T.
+//   3. each eigenvector of the tridiagonal matrix by inverse iteration in R
+//      (LU with partial pivoting, three sweeps), one lane each, vectors
+//      orthogonalised within clusters of close eigenvalues, and FP64
+//      Rayleigh quotients;
+//   4. back-transformation of the k lowest eigenvectors in R (one warp per
+//      vector) and, for them, FP64 Rayleigh quotients with the original T.
 // Golub & Van Loan, Matrix Computations, sec. 8.3 (tridiagonalisation), 8.4
 // (bisection), 8.2 (inverse iteration, Rayleigh quotient).
 #include "internal.h"
@@ -23,6 +25,30 @@ namespace {
 constexpr int kN = MOTO_MAX_BASIS;
 constexpr int kLdA = kN + 1;
 constexpr int kNE = 16;  // lowest Ritz values computed; higher entries of theta stay +inf
+constexpr int kIW = kN + 1;  // padded stride of the per-lane inverse-iteration arrays
+
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// start vector of inverse iteration: a fixed hash of (row, eigenvalue index)
+// in [0.75, 1.25)
+__device__ __forceinline__ float start_entry(int r, int i) {
+  unsigned h = (unsigned)r * 0x9E3779B1u ^ (unsigned)(i + 1) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  return 0.75f + 0.5f * (float)(h >> 8) * (1.0f / 16777216.0f);
+}
+
+template <typename R>
+size_t eig_smem_bytes() {
+  return (3 * kN + (size_t)kNE * kN) * sizeof(double) +
+         ((size_t)kN * kLdA + 2 * kN + 5 * (size_t)kNE * kIW + (size_t)kNE * kN) * sizeof(R) + (size_t)kNE * kIW;
+}
 }  // namespace
 
 template <typename R>
@@ -33,13 +59,17 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   double* d = sm;                              // diagonal
   double* e = d + kN;                          // off-diagonal
   double* lam = e + kN;                        // eigenvalues
-  double* vec = lam + kN;                      // kNE x n eigenvectors (tridiagonal basis, then T basis)
+  double* vec = lam + kN;                      // kNE x n eigenvectors of the tridiagonal matrix
   R* A = reinterpret_cast<R*>(vec + (size_t)kNE * kN);  // n x (n+1), Householder vectors below the subdiagonal
   R* beta = A + (size_t)kN * kLdA;             // reflector scales
-  R* pv = beta + kN;                           // work vector p / w
-  __shared__ double red[32];
+  R* pv = beta + kN;                           // p = b A22 v
+  R* iw = pv + kN;                             // inverse iteration: [dg, su, s2, lm, x] x kNE x kIW
+  R* vr = iw + 5 * (size_t)kNE * kIW;          // kNE x n vectors in R for the back-transformation
+  unsigned char* piv = reinterpret_cast<unsigned char*>(vr + (size_t)kNE * kN);  // pivot flags
   __shared__ float shift[kNE];
-  __shared__ R sh_alpha, sh_beta, sh_K;
+  __shared__ float df[kN], ef[kN], e2f[kN];
+  __shared__ R sh_alpha, sh_beta;
+  __shared__ double sh_tn;
   const int n = st->nT;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int wp = tid >> 5, ln = tid & 31, nw = nth >> 5;
@@ -56,31 +86,32 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   if (band > 1) {
     for (int j = 0; j + 2 < n; ++j) {
       const int m0 = j + 1;
-      double s = 0.0;
-      for (int r = m0 + tid; r < n; r += nth) s += (double)A[r * kLdA + j] * A[r * kLdA + j];
-      double v1[1] = {s};
-      block_sum<1>(v1, red);
-      if (tid == 0) {
-        const R norm2 = (R)v1[0];
-        const R x0 = A[m0 * kLdA + j];
-        if (norm2 - x0 * x0 <= (R)1e-30 * (norm2 + (R)1e-30)) {
-          sh_beta = 0;
-          sh_alpha = x0;
-        } else {
-          const R alpha = -copysign(sqrt(norm2), x0);
-          const R v0 = x0 - alpha;
-          const R vtv = v0 * v0 + (norm2 - x0 * x0);
-          sh_alpha = alpha;
-          sh_beta = (R)2 / vtv;
-          A[m0 * kLdA + j] = v0;
+      if (wp == 0) {  // reflector of column j below the diagonal
+        R s = 0;
+        for (int r = m0 + ln; r < n; r += 32) {
+          const R a = A[r * kLdA + j];
+          s += a * a;
+        }
+        const R norm2 = warp_sum_r(s);
+        if (ln == 0) {
+          const R x0 = A[m0 * kLdA + j];
+          if (norm2 - x0 * x0 <= (R)1e-30 * (norm2 + (R)1e-30)) {
+            sh_beta = 0;
+            sh_alpha = x0;
+          } else {
+            const R alpha = -copysign(sqrt(norm2), x0);
+            const R v0 = x0 - alpha;
+            const R vtv = v0 * v0 + (norm2 - x0 * x0);
+            sh_alpha = alpha;
+            sh_beta = (R)2 / vtv;
+            A[m0 * kLdA + j] = v0;
+          }
+          e[j] = (double)sh_alpha;
+          beta[j] = sh_beta;
         }
       }
       __syncthreads();
       const R b = sh_beta;
-      if (tid == 0) {
-        e[j] = (double)sh_alpha;
-        beta[j] = b;
-      }
       if (b == (R)0) {
         __syncthreads();
         continue;
@@ -88,23 +119,22 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
       for (int r = m0 + wp; r < n; r += nw) {  // p = b A22 v, a warp per row
         R a = 0;
         for (int c2 = m0 + ln; c2 < n; c2 += 32) a += A[r * kLdA + c2] * A[c2 * kLdA + j];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        a = warp_sum_r(a);
         if (ln == 0) pv[r] = b * a;
       }
       __syncthreads();
-      double q = 0.0;
-      for (int r = m0 + tid; r < n; r += nth) q += (double)A[r * kLdA + j] * pv[r];
-      double v2[1] = {q};
-      block_sum<1>(v2, red);
-      if (tid == 0) sh_K = (R)(0.5 * (double)b * v2[0]);
-      __syncthreads();
-      const R K = sh_K;
-      for (int r = m0 + tid; r < n; r += nth) pv[r] -= K * A[r * kLdA + j];  // w = p - K v
-      __syncthreads();
-      const int m = n - m0;
-      for (int idx = tid; idx < m * m; idx += nth) {
-        const int r = m0 + idx / m, c2 = m0 + idx % m;
-        A[r * kLdA + c2] -= A[r * kLdA + j] * pv[c2] + pv[r] * A[c2 * kLdA + j];
+      // K = b v^T p / 2, summed by every warp in the same order; the update
+      // A22 -= v w^T + w v^T with w = p - K v formed on the fly
+      R q = 0;
+      for (int r = m0 + ln; r < n; r += 32) q += A[r * kLdA + j] * pv[r];
+      const R K = (R)0.5 * b * warp_sum_r(q);
+      for (int r = m0 + wp; r < n; r += nw) {
+        const R vr_ = A[r * kLdA + j];
+        const R wr = pv[r] - K * vr_;
+        for (int c2 = m0 + ln; c2 < n; c2 += 32) {
+          const R vc = A[c2 * kLdA + j];
+          A[r * kLdA + c2] -= vr_ * (pv[c2] - K * vc) + wr * vc;
+        }
       }
       __syncthreads();
     }
@@ -124,32 +154,42 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   __syncthreads();
 
   // ---- 2. FP32 bisection for the lowest ne eigenvalues --------------------------
-  double tn = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
-    tn = fmax(tn, fabs(d[i]) + r);
+  for (int r = tid; r < n; r += nth) {
+    df[r] = (float)d[r];
+    ef[r] = (float)fabs(e[r]);
+    e2f[r] = (float)(e[r] * e[r]);
   }
-  tn = fmax(tn, 1e-300);
+  if (wp == 0) {  // |T| estimate (largest row sum of the tridiagonal matrix)
+    double t = 0.0;
+    for (int i = ln; i < n; i += 32) {
+      const double rs = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+      t = fmax(t, fabs(d[i]) + rs);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (ln == 0) sh_tn = fmax(t, 1e-300);
+  }
+  __syncthreads();
+  const double tn = sh_tn;
   const int ne = n < kNE ? n : kNE;
   if (tid < ne) {
     const int i = tid;
     float lo = 1e30f, hi = -1e30f;
     for (int r = 0; r < n; ++r) {
-      const float rr = (float)((r > 0 ? fabs(e[r - 1]) : 0.0) + (r + 1 < n ? fabs(e[r]) : 0.0));
-      lo = fminf(lo, (float)d[r] - rr);
-      hi = fmaxf(hi, (float)d[r] + rr);
+      const float rr = (r > 0 ? ef[r - 1] : 0.f) + (r + 1 < n ? ef[r] : 0.f);
+      lo = fminf(lo, df[r] - rr);
+      hi = fmaxf(hi, df[r] + rr);
     }
     lo -= 1e-6f * (float)tn;
     hi += 1e-6f * (float)tn;
     float a = lo, bb = hi;
     for (int itn = 0; itn < 64 && (bb - a) > 4e-7f * fmaxf(fabsf(a), fabsf(bb)) + 1e-30f; ++itn) {
       const float x = 0.5f * (a + bb);
-      float pm = 1.f, p = (float)d[0] - x;
+      float pm = 1.f, p = df[0] - x;
       if (p == 0.f) p = -1e-30f;
       int cnt = (p < 0.f) ? 1 : 0;
       for (int r = 1; r < n; ++r) {
-        const float er = (float)e[r - 1];
-        float pn = ((float)d[r] - x) * p - er * er * pm;
+        float pn = (df[r] - x) * p - e2f[r - 1] * pm;
         if (pn == 0.f) pn = -copysignf(1e-30f, p);
         cnt += ((pn < 0.f) != (p < 0.f)) ? 1 : 0;
         pm = p;
@@ -170,30 +210,34 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   }
   __syncthreads();
 
-  // ---- 3. FP64 inverse iteration + Rayleigh quotient, one vector per warp lane 0
-  for (int i = wp; i < ne; i += nw) {
-    if (ln != 0) continue;
-    double dg[kN], su[kN], s2[kN], lm[kN], x[kN];
-    bool pivot[kN];
-    const double sigma = (double)shift[i];
-    const double tiny = 1e-14 * tn;
+  // ---- 3. inverse iteration (precision R), one lane per eigenvalue -------------
+  if (tid < ne) {
+    const int i = tid;
+    R* dg = iw + (size_t)i * kIW;
+    R* su = dg + (size_t)kNE * kIW;
+    R* s2 = su + (size_t)kNE * kIW;
+    R* lm = s2 + (size_t)kNE * kIW;
+    R* x = lm + (size_t)kNE * kIW;
+    unsigned char* pivot = piv + (size_t)i * kIW;
+    const R sigma = (R)shift[i];
+    const R tiny = (R)((sizeof(R) == 4 ? 1e-7 : 1e-14) * tn);
     for (int r = 0; r < n; ++r) {
-      dg[r] = d[r] - sigma;
-      su[r] = (r + 1 < n) ? e[r] : 0.0;
-      s2[r] = 0.0;
+      dg[r] = (R)d[r] - sigma;
+      su[r] = (r + 1 < n) ? (R)e[r] : (R)0;
+      s2[r] = 0;
     }
     for (int r = 0; r + 1 < n; ++r) {
-      const double sub = e[r];
+      const R sub = (R)e[r];
       if (fabs(dg[r]) >= fabs(sub)) {
-        pivot[r] = false;
-        const double l = (dg[r] != 0.0) ? sub / dg[r] : 0.0;
+        pivot[r] = 0;
+        const R l = (dg[r] != (R)0) ? sub / dg[r] : (R)0;
         lm[r] = l;
         dg[r + 1] -= l * su[r];
       } else {
-        pivot[r] = true;
-        const double l = dg[r] / sub;
+        pivot[r] = 1;
+        const R l = dg[r] / sub;
         lm[r] = l;
-        const double d1 = dg[r + 1], u1 = su[r + 1], old_su = su[r];
+        const R d1 = dg[r + 1], u1 = su[r + 1], old_su = su[r];
         dg[r] = sub;
         su[r] = d1;
         s2[r] = u1;
@@ -202,12 +246,12 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
       }
     }
     for (int r = 0; r < n; ++r)
-      if (fabs(dg[r]) < tiny) dg[r] = (dg[r] < 0.0 ? -tiny : tiny);
-    for (int r = 0; r < n; ++r) x[r] = 1.0 + 0.5 * sin(0.7 * r + 0.3 * i);
+      if (fabs(dg[r]) < tiny) dg[r] = (dg[r] < (R)0 ? -tiny : tiny);
+    for (int r = 0; r < n; ++r) x[r] = (R)start_entry(r, i);
     for (int sweep = 0; sweep < 3; ++sweep) {
       for (int r = 0; r + 1 < n; ++r) {
         if (pivot[r]) {
-          const double t = x[r];
+          const R t = x[r];
           x[r] = x[r + 1];
           x[r + 1] = t - lm[r] * x[r + 1];
         } else {
@@ -215,17 +259,17 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
         }
       }
       for (int r = n - 1; r >= 0; --r) {
-        double a = x[r];
+        R a = x[r];
         if (r + 1 < n) a -= su[r] * x[r + 1];
         if (r + 2 < n) a -= s2[r] * x[r + 2];
         x[r] = a / dg[r];
       }
-      double nn = 0.0;
+      R nn = 0;
       for (int r = 0; r < n; ++r) nn += x[r] * x[r];
-      nn = 1.0 / sqrt(nn);
+      nn = (R)1 / sqrt(nn);
       for (int r = 0; r < n; ++r) x[r] *= nn;
     }
-    for (int r = 0; r < n; ++r) vec[i * kN + r] = x[r];
+    for (int r = 0; r < n; ++r) vec[i * kN + r] = (double)x[r];
   }
   __syncthreads();
   // clusters: orthogonalise (modified Gram-Schmidt), then Rayleigh quotients
@@ -277,36 +321,38 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   }
   __syncthreads();
 
-  // ---- 4. back-transformation x <- H_0 ... H_{n-3} x, then FP64 Rayleigh
-  //         quotients with the original T for the k vectors -----------------------
-  int kk = k < ne ? k : ne;
+  // ---- 4. back-transformation x <- H_0 ... H_{n-3} x in R (a warp per vector,
+  //         the reflectors read-only), then FP64 Rayleigh quotients with the
+  //         original T ---------------------------------------------------------------
+  const int kk = k < ne ? k : ne;
   if (band > 1) {
-    for (int j = n - 3; j >= 0; --j) {
-      const R b = beta[j];
-      if (b == (R)0) continue;
-      const int m0 = j + 1;
-      for (int vi = wp; vi < kk; vi += nw) {
-        double* x = vec + vi * kN;
-        double dot = 0.0;
-        for (int r = m0 + ln; r < n; r += 32) dot += (double)A[r * kLdA + j] * x[r];
-        dot = warp_sum(dot) * (double)b;
-        for (int r = m0 + ln; r < n; r += 32) x[r] -= dot * (double)A[r * kLdA + j];
-      }
-      __syncthreads();
-    }
     for (int vi = wp; vi < kk; vi += nw) {
-      const double* x = vec + vi * kN;
+      R* x = vr + (size_t)vi * kN;
+      for (int r = ln; r < n; r += 32) x[r] = (R)vec[vi * kN + r];
+      __syncwarp();
+      for (int j = n - 3; j >= 0; --j) {
+        const R b = beta[j];
+        if (b == (R)0) continue;
+        const int m0 = j + 1;
+        R dot = 0;
+        for (int r = m0 + ln; r < n; r += 32) dot += A[r * kLdA + j] * x[r];
+        dot = warp_sum_r(dot) * b;
+        for (int r = m0 + ln; r < n; r += 32) x[r] -= dot * A[r * kLdA + j];
+        __syncwarp();
+      }
       double a = 0.0, nn = 0.0;
       for (int r = ln; r < n; r += 32) {
         double t = 0.0;
         const int c0 = r - band < 0 ? 0 : r - band, c1 = r + band + 1 > n ? n : r + band + 1;
-        for (int c2 = c0; c2 < c1; ++c2) t += 0.5 * (Tm[(size_t)r * ldT + c2] + Tm[(size_t)c2 * ldT + r]) * x[c2];
-        a += x[r] * t;
-        nn += x[r] * x[r];
+        for (int c2 = c0; c2 < c1; ++c2)
+          t += 0.5 * (Tm[(size_t)r * ldT + c2] + Tm[(size_t)c2 * ldT + r]) * (double)x[c2];
+        a += (double)x[r] * t;
+        nn += (double)x[r] * (double)x[r];
       }
       a = warp_sum(a);
       nn = warp_sum(nn);
       if (ln == 0) lam[vi] = a / nn;
+      for (int r = ln; r < n; r += 32) vec[vi * kN + r] = (double)x[r];
     }
     __syncthreads();
   }
@@ -319,25 +365,22 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
 
 void launch_tridiag_eig(const double* T, int ldT, int band, int fp64, double* theta, double* Y, int k, DevState* st,
                         cudaStream_t s) {
-  auto bytes = [](size_t rsz) {
-    return (3 * kN + (size_t)kNE * kN) * sizeof(double) + ((size_t)kN * kLdA + 2 * kN) * rsz;
-  };
   if (fp64) {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(tridiag_eig_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bytes(sizeof(double)));
+                           (int)eig_smem_bytes<double>());
       attr = true;
     }
-    tridiag_eig_kernel<double><<<1, 256, bytes(sizeof(double)), s>>>(T, ldT, band, theta, Y, k, st);
+    tridiag_eig_kernel<double><<<1, 256, eig_smem_bytes<double>(), s>>>(T, ldT, band, theta, Y, k, st);
   } else {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(tridiag_eig_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)bytes(sizeof(float)));
+                           (int)eig_smem_bytes<float>());
       attr = true;
     }
-    tridiag_eig_kernel<float><<<1, 256, bytes(sizeof(float)), s>>>(T, ldT, band, theta, Y, k, st);
+    tridiag_eig_kernel<float><<<1, 256, eig_smem_bytes<float>(), s>>>(T, ldT, band, theta, Y, k, st);
   }
 }
 

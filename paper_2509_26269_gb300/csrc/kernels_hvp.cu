@@ -4,7 +4,7 @@
 // stencil.cuh for the formula and its reading of Eq. param-hamiltonian).
 //
 // A block stages a 32 x 64-site tile of v (plus a 2-site periodic halo) in
-// shared memory with coalesced loads.  A thread then owns a column strip of
+// shared memory with asynchronous copies, double-buffered over the vectors.  A thread then owns a column strip of
 // kStrip sites along a2: it walks the kStrip + 4 tile rows the strip needs,
 // reading each row once (five columns x - 2 .. x + 2 of the three components)
 // and scattering it into the accumulators of the (up to five) strip sites it is
@@ -115,6 +115,50 @@ struct SWalk<T, -1> {
 
 }  // namespace
 
+// 4-byte asynchronous global -> shared copy (cp.async, cached in L1)
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Starts the copy of vector v's halo'd tile into `tile` (one element per copy;
+// periodic wrap at the lattice edges).
+template <typename T>
+__device__ __forceinline__ void stage_tile(T* tile, const T* __restrict__ v, size_t N, int L1, int L2, int x0, int y0,
+                                           bool interior) {
+  for (int idx = threadIdx.x; idx < kSX * kSY; idx += blockDim.x) {
+    const int ly = idx / kSX, lx = idx - ly * kSX;
+    int gx = x0 + lx - 2, gy = y0 + ly - 2;
+    if (!interior) {
+      gx = wrap(gx, L1);
+      gy = wrap(gy, L2);
+    }
+    const size_t g = (size_t)gy * L1 + gx;
+    if constexpr (sizeof(T) == 4) {
+      cp_async4(tile + idx, v + g);
+      cp_async4(tile + (size_t)kSX * kSY + idx, v + N + g);
+      cp_async4(tile + 2 * (size_t)kSX * kSY + idx, v + 2 * N + g);
+    } else {
+      cp_async8(tile + idx, v + g);
+      cp_async8(tile + (size_t)kSX * kSY + idx, v + N + g);
+      cp_async8(tile + 2 * (size_t)kSX * kSY + idx, v + 2 * N + g);
+    }
+  }
+  cp_async_commit();
+}
+
+// Two tile buffers: the copy of vector j + 1 runs while vector j is computed.
 template <typename T>
 __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, const T* __restrict__ m,
                                                                  const T* __restrict__ s, const T* __restrict__ V,
@@ -122,7 +166,8 @@ __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, co
                                                                  const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tile = reinterpret_cast<T*>(smem_raw);  // [3][kSY][kSX]
+  T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][kSY][kSX]
+  constexpr size_t kTileElems = 3 * (size_t)kSX * kSY;
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int L1 = md.L1, L2 = md.L2;
@@ -133,42 +178,40 @@ __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, co
   const T twoD = (T)(2.0 * md.D), twoK = (T)(2.0 * md.K);
   const bool interior = x0 >= 2 && y0 >= 2 && x0 + kTX + 2 <= L1 && y0 + kTY + 2 <= L2;
   const int x = x0 + lane;
+  stage_tile(tiles, V, N, L1, L2, x0, y0, interior);
   for (int j = 0; j < nvec; ++j) {
-    const T* v = V + (size_t)j * ldv;
+    T* tile = tiles + (size_t)(j & 1) * kTileElems;
     T* hv = HV + (size_t)j * ldhv;
-    if (j > 0) __syncthreads();
-    for (int idx = threadIdx.x; idx < kSX * kSY; idx += blockDim.x) {
-      const int ly = idx / kSX, lx = idx - ly * kSX;
-      int gx = x0 + lx - 2, gy = y0 + ly - 2;
-      if (!interior) {
-        gx = wrap(gx, L1);
-        gy = wrap(gy, L2);
-      }
-      const size_t g = (size_t)gy * L1 + gx;
-      tile[idx] = __ldg(v + g);
-      tile[(size_t)kSX * kSY + idx] = __ldg(v + N + g);
-      tile[2 * (size_t)kSX * kSY + idx] = __ldg(v + 2 * N + g);
+    if (j + 1 < nvec) {
+      stage_tile(tiles + (size_t)((j + 1) & 1) * kTileElems, V + (size_t)(j + 1) * ldv, N, L1, L2, x0, y0, interior);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
     T ax[kStrip], ay[kStrip], az[kStrip];
 #pragma unroll
     for (int k = 0; k < kStrip; ++k) ax[k] = ay[k] = az[k] = (T)0;
     SWalk<T, kStrip + 3>::run(tile, wy * kStrip, lane, ax, ay, az, j0, j1, j2, twoD);
-    if (x >= L1) continue;
+    if (x < L1) {
 #pragma unroll
-    for (int k = 0; k < kStrip; ++k) {
-      const int y = y0 + wy * kStrip + k;
-      if (y >= L2) break;
-      const size_t i = (size_t)y * L1 + x;
-      const size_t ti = (size_t)(wy * kStrip + k + 2) * kSX + lane + 2;
-      const T vx = tile[ti], vy = tile[(size_t)kSX * kSY + ti], vz = tile[2 * (size_t)kSX * kSY + ti];
-      const T m0 = __ldg(m + i), m1 = __ldg(m + N + i), m2 = __ldg(m + 2 * N + i), si = __ldg(s + i);
-      const T hx = ax[k] - si * vx, hy = ay[k] - si * vy, hz = az[k] - twoK * vz - si * vz;
-      const T p = m0 * hx + m1 * hy + m2 * hz;
-      hv[i] = hx - p * m0;
-      hv[N + i] = hy - p * m1;
-      hv[2 * N + i] = hz - p * m2;
+      for (int k = 0; k < kStrip; ++k) {
+        const int y = y0 + wy * kStrip + k;
+        if (y >= L2) break;
+        const size_t i = (size_t)y * L1 + x;
+        const size_t ti = (size_t)(wy * kStrip + k + 2) * kSX + lane + 2;
+        const T vx = tile[ti], vy = tile[(size_t)kSX * kSY + ti], vz = tile[2 * (size_t)kSX * kSY + ti];
+        const T m0 = __ldg(m + i), m1 = __ldg(m + N + i), m2 = __ldg(m + 2 * N + i), si = __ldg(s + i);
+        const T hx = ax[k] - si * vx, hy = ay[k] - si * vy, hz = az[k] - twoK * vz - si * vz;
+        const T p = m0 * hx + m1 * hy + m2 * hz;
+        hv[i] = hx - p * m0;
+        hv[N + i] = hy - p * m1;
+        hv[2 * N + i] = hz - p * m2;
+      }
     }
+    // every warp is done with this buffer before the copy issued in the next
+    // iteration (for vector j + 2) overwrites it
+    __syncthreads();
   }
 }
 
@@ -176,7 +219,7 @@ template <typename T>
 void launch_hvp_strip(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
                       int nvec, const int* gate, int mask, cudaStream_t st) {
   const dim3 grid((md.L1 + kTX - 1) / kTX, (md.L2 + kTY - 1) / kTY);
-  const size_t smem = 3 * (size_t)kSX * kSY * sizeof(T);
+  const size_t smem = 2 * 3 * (size_t)kSX * kSY * sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(hvp_strip_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
