@@ -179,6 +179,27 @@ void P_tile(moto_ctx* c, int mode, const T* X, int nx, int u0, int nu, T* Y, int
   }
 }
 
+__global__ void set_status_kernel(DevState* st, int bits) {
+  if (threadIdx.x == 0) st->status |= bits;
+}
+
+// Cholesky QR, second pass: Gram of W R1^{-1} (read-only sweep) and the
+// final combination Q = (W R1^{-1}) R2^{-1} (projected), W R1^{-1} never stored.
+template <typename T>
+void P_chol2_gram(moto_ctx* c, const T* W, int b, const double* R1inv, double* S2, const int* gate, int mask,
+                  cudaStream_t st) {
+  PROF(kPkGram, (double)b * 3.0 * c->N * sizeof(T));
+  if (!launch_chol2<T>(W, c->ld, b, R1inv, nullptr, nullptr, 0, nullptr, c->N, S2, c->part, c->counter, gate, mask,
+                       true, st))
+    set_status_kernel<<<1, 1, 0, st>>>(c->st, kStatusNotSPD);
+}
+template <typename T>
+void P_combine2(moto_ctx* c, const T* W, int b, const double* R1inv, const double* R2inv, T* Q, const T* m,
+                const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkCombine, (2.0 * b + (m ? 1 : 0)) * 3.0 * c->N * sizeof(T));
+  launch_chol2<T>(W, c->ld, b, R1inv, R2inv, Q, c->ld, m, c->N, nullptr, nullptr, nullptr, gate, mask, false, st);
+}
+
 #define SMALL_WRAP(name)                                                 \
   template <typename... A>                                               \
   void P_##name(moto_ctx* c, A... args) {                                \
@@ -212,8 +233,8 @@ constexpr size_t kY = kTheta + MOTO_MAX_BASIS;                     // MAX_BASIS 
 constexpr size_t kC = kY + MOTO_MAX_BASIS * MOTO_MAX_K;            // MAX_BASIS * MAX_K
 constexpr size_t kC3 = kC + MOTO_MAX_BASIS * MOTO_MAX_K;           // 2K * K
 constexpr size_t kC2 = kC3 + 2 * MOTO_MAX_K * MOTO_MAX_K;          // MAX_BASIS * MAX_K (second CGS pass)
-constexpr size_t kA = kC2 + MOTO_MAX_BASIS * MOTO_MAX_K;           // K*K
-constexpr size_t kG = kA + MOTO_MAX_K * MOTO_MAX_K;                // K*K
+constexpr size_t kRinv2 = kC2 + MOTO_MAX_BASIS * MOTO_MAX_K;       // K*K (second Cholesky QR factor)
+constexpr size_t kG = kRinv2 + MOTO_MAX_K * MOTO_MAX_K;            // K*K
 constexpr size_t kRinv = kG + MOTO_MAX_K * MOTO_MAX_K;             // K*K
 constexpr size_t kRacc = kRinv + MOTO_MAX_K * MOTO_MAX_K;          // K*K
 constexpr size_t kEG = kRacc + MOTO_MAX_K * MOTO_MAX_K;            // 2: [E, gmax]
@@ -316,7 +337,6 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   const size_t n3 = c->n3, ld = c->ld;
   T* Q = static_cast<T*>(c->basis);
   T* W = static_cast<T*>(c->W);
-  T* Wt = static_cast<T*>(c->Wt);
   double* D = c->dsm;
   int* gate = &c->st->gate;
   const int mk = kGateKrylov | kGateDone;
@@ -326,9 +346,9 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   P_project<T>(c, m, v0, ld0, W, ld, b, N, gate, kGateDone, st);
   P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
   P_cholqr(c, D + kG, b, 0, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-  P_tile<T>(c, 3, W, b, 0, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
-  P_cholqr(c, D + kG, b, 1, -1, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-  P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q, ld, nullptr, N, gate, mk, st);
+  P_chol2_gram<T>(c, W, b, D + kRinv, D + kG, gate, mk, st);
+  P_cholqr(c, D + kG, b, 1, -1, D + kRinv2, D + kRacc, D + kT, kLd, c->st, rel, st);
+  P_combine2<T>(c, W, b, D + kRinv, D + kRinv2, Q, nullptr, gate, mk, st);
   // Block Lanczos step j, reorthogonalised twice: W = H Q_j; a local pass
   // against the last two blocks (G1 = [Q_{j-1} Q_j]^T W, whose Q_j rows give
   // T(j, j); W <- W - [Q_{j-1} Q_j] G1, with G2 = Q^T W over the whole basis in
@@ -349,10 +369,9 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
     P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC, W, D + kC2, gate, mk, st);
     P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-    P_tile<T>(c, 3, W, b, 0, b, Wt, b, D + kRinv, Wt, D + kG, gate, mk, st);
-    P_cholqr(c, D + kG, b, 1, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-    P_combine<T>(c, Wt, ld, b, nullptr, D + kRinv, b, nullptr, 0, 0.0, 1.0, Q + (size_t)(j + 1) * b * ld, ld, m, N,
-                 gate, mk, st);
+    P_chol2_gram<T>(c, W, b, D + kRinv, D + kG, gate, mk, st);
+    P_cholqr(c, D + kG, b, 1, j, D + kRinv2, D + kRacc, D + kT, kLd, c->st, rel, st);
+    P_combine2<T>(c, W, b, D + kRinv, D + kRinv2, Q + (size_t)(j + 1) * b * ld, m, gate, mk, st);
   }
   P_tridiag_eig(c, D + kT, kLd, b, lam, D + kY, nout, c->st, st);
   P_combine<T>(c, Q, ld, b * steps, &c->st->nT, D + kY, nout, nullptr, 0, 0.0, 1.0, V, ldv, nullptr, N,

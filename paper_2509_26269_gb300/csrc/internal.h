@@ -71,6 +71,14 @@ template <typename T>
 bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
                  const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
                  int mask, int* status, cudaStream_t st);
+// Cholesky QR applied twice without storing X R1^{-1} (kernels_vec.cu): with
+// gram, S2 = (X P1)^T (X P1); without, Q = (X P1) P2, projected on the tangent
+// planes of m when m != NULL.  X: nx <= 8 fields; P1, P2: nx x nx FP64.  Both
+// form X P1 with the same FMA chain, so they see the same rounded values.
+template <typename T>
+bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double* P2, T* Q, size_t ldq, const T* m,
+                  int N, double* S2, double* part, unsigned* counter, const int* gate, int mask, bool gram,
+                  cudaStream_t st);
 // Block Lanczos: T(j, j) = sym of block row jr of the local Gram G1 (b x b
 // blocks, row jr holding Q_j^T H Q_j).
 void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int ldT, DevState* st, cudaStream_t s);

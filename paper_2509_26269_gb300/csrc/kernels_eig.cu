@@ -5,10 +5,10 @@
 //   1. Householder reduction to tridiagonal form Q^T T Q = tridiag(d, e) in R
 //      (skipped for b = 1, where T is tridiagonal); three barriers per
 //      reflector: warp 0 forms it, every warp applies it to its rows;
-//   2. the lowest 16 eigenvalues located by FP32 bisection on the Sturm
+//   2. the lowest 16 eigenvalues located by FP32 multisection on the Sturm
 //      sequence of the characteristic polynomials
 //      p_r = (d_r - x) p_{r-1} - e_{r-1}^2 p_{r-2} (sign changes count the
-//      eigenvalues below x; rescaled to stay in range), one lane each;
+//      eigenvalues below x; rescaled to stay in range), 16 lanes each;
 //   3. each eigenvector of the tridiagonal matrix by inverse iteration in R
 //      (LU with partial pivoting, three sweeps), one lane each, vectors
 //      orthogonalised within clusters of close eigenvalues, and FP64
@@ -116,11 +116,15 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
         __syncthreads();
         continue;
       }
-      for (int r = m0 + wp; r < n; r += nw) {  // p = b A22 v, a warp per row
-        R a = 0;
-        for (int c2 = m0 + ln; c2 < n; c2 += 32) a += A[r * kLdA + c2] * A[c2 * kLdA + j];
-        a = warp_sum_r(a);
-        if (ln == 0) pv[r] = b * a;
+      for (int r = m0 + tid; r < n; r += nth) {  // p = b A22 v, a thread per row
+        R a0 = 0, a1 = 0;
+        int c2 = m0;
+        for (; c2 + 1 < n; c2 += 2) {
+          a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
+          a1 += A[r * kLdA + c2 + 1] * A[(c2 + 1) * kLdA + j];
+        }
+        if (c2 < n) a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
+        pv[r] = b * (a0 + a1);
       }
       __syncthreads();
       // K = b v^T p / 2, summed by every warp in the same order; the update
@@ -172,19 +176,24 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   __syncthreads();
   const double tn = sh_tn;
   const int ne = n < kNE ? n : kNE;
-  if (tid < ne) {
-    const int i = tid;
+  {
+    // multisection: half-warp h of warp w brackets eigenvalue 2w + h; its 16
+    // lanes count the eigenvalues below 16 interior points of the bracket
+    // (Sturm sequence), which shrinks the bracket 17-fold per round
+    const int half = ln >> 4, sl = ln & 15;
+    const int i = 2 * wp + half;
+    const bool act = i < ne;
     float lo = 1e30f, hi = -1e30f;
     for (int r = 0; r < n; ++r) {
       const float rr = (r > 0 ? ef[r - 1] : 0.f) + (r + 1 < n ? ef[r] : 0.f);
       lo = fminf(lo, df[r] - rr);
       hi = fmaxf(hi, df[r] + rr);
     }
-    lo -= 1e-6f * (float)tn;
-    hi += 1e-6f * (float)tn;
-    float a = lo, bb = hi;
-    for (int itn = 0; itn < 64 && (bb - a) > 4e-7f * fmaxf(fabsf(a), fabsf(bb)) + 1e-30f; ++itn) {
-      const float x = 0.5f * (a + bb);
+    float a = lo - 1e-6f * (float)tn, bb = hi + 1e-6f * (float)tn;
+    for (int round = 0; round < 24; ++round) {
+      const bool open = act && (bb - a) > 4e-7f * fmaxf(fabsf(a), fabsf(bb)) + 1e-30f;
+      if (!__any_sync(0xffffffffu, open)) break;
+      const float x = a + (bb - a) * (float)(sl + 1) * (1.0f / 17.0f);
       float pm = 1.f, p = df[0] - x;
       if (p == 0.f) p = -1e-30f;
       int cnt = (p < 0.f) ? 1 : 0;
@@ -201,12 +210,21 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
           pm *= sc;
         }
       }
-      if (cnt > i)
-        bb = x;
-      else
-        a = x;
+      const unsigned above = (__ballot_sync(0xffffffffu, cnt > i) >> (16 * half)) & 0xFFFFu;
+      if (open) {
+        // counts grow with x: the first point above eigenvalue i closes the bracket
+        const float w = bb - a;
+        if (above == 0u) {
+          a = a + w * (16.0f / 17.0f);
+        } else {
+          const int f = __ffs(above) - 1;
+          const float na = f == 0 ? a : a + w * (float)f * (1.0f / 17.0f);
+          bb = a + w * (float)(f + 1) * (1.0f / 17.0f);
+          a = na;
+        }
+      }
     }
-    shift[i] = 0.5f * (a + bb);
+    if (act && sl == 0) shift[i] = 0.5f * (a + bb);
   }
   __syncthreads();
 

@@ -4,7 +4,8 @@
 // stencil.cuh for the formula and its reading of Eq. param-hamiltonian).
 //
 // A block stages a 32 x 64-site tile of v (plus a 2-site periodic halo) in
-// shared memory with asynchronous copies, double-buffered over the vectors.  A thread then owns a column strip of
+// shared memory with asynchronous copies, double-buffered over the vectors,
+// and m, s of its sites once.  A thread then owns a column strip of
 // kStrip sites along a2: it walks the kStrip + 4 tile rows the strip needs,
 // reading each row once (five columns x - 2 .. x + 2 of the three components)
 // and scattering it into the accumulators of the (up to five) strip sites it is
@@ -159,6 +160,8 @@ __device__ __forceinline__ void stage_tile(T* tile, const T* __restrict__ v, siz
 }
 
 // Two tile buffers: the copy of vector j + 1 runs while vector j is computed.
+// m and s of the block's sites are staged once (they are read for every
+// vector in the output phase).
 template <typename T>
 __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, const T* __restrict__ m,
                                                                  const T* __restrict__ s, const T* __restrict__ V,
@@ -168,6 +171,7 @@ __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, co
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][kSY][kSX]
   constexpr size_t kTileElems = 3 * (size_t)kSX * kSY;
+  T* ms = tiles + 2 * kTileElems;  // [4][kTY][kTX]: m_x, m_y, m_z, s
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
   const int L1 = md.L1, L2 = md.L2;
@@ -178,6 +182,20 @@ __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, co
   const T twoD = (T)(2.0 * md.D), twoK = (T)(2.0 * md.K);
   const bool interior = x0 >= 2 && y0 >= 2 && x0 + kTX + 2 <= L1 && y0 + kTY + 2 <= L2;
   const int x = x0 + lane;
+  // m, s of the tile (sites outside the lattice are never read back)
+  for (int idx = threadIdx.x; idx < 4 * kTY * kTX; idx += blockDim.x) {
+    const int comp = idx / (kTY * kTX), rem = idx - comp * (kTY * kTX);
+    const int ly = rem / kTX, lx = rem - ly * kTX;
+    const int gx = x0 + lx, gy = y0 + ly;
+    if (gx < L1 && gy < L2) {
+      const size_t g = (size_t)gy * L1 + gx;
+      const T* src = comp < 3 ? m + (size_t)comp * N + g : s + g;
+      if constexpr (sizeof(T) == 4)
+        cp_async4(ms + idx, src);
+      else
+        cp_async8(ms + idx, src);
+    }
+  }
   stage_tile(tiles, V, N, L1, L2, x0, y0, interior);
   for (int j = 0; j < nvec; ++j) {
     T* tile = tiles + (size_t)(j & 1) * kTileElems;
@@ -196,12 +214,14 @@ __global__ void __launch_bounds__(32 * kWarpsY) hvp_strip_kernel(ModelDev md, co
     if (x < L1) {
 #pragma unroll
       for (int k = 0; k < kStrip; ++k) {
-        const int y = y0 + wy * kStrip + k;
+        const int ly = wy * kStrip + k;
+        const int y = y0 + ly;
         if (y >= L2) break;
         const size_t i = (size_t)y * L1 + x;
-        const size_t ti = (size_t)(wy * kStrip + k + 2) * kSX + lane + 2;
+        const size_t ti = (size_t)(ly + 2) * kSX + lane + 2;
         const T vx = tile[ti], vy = tile[(size_t)kSX * kSY + ti], vz = tile[2 * (size_t)kSX * kSY + ti];
-        const T m0 = __ldg(m + i), m1 = __ldg(m + N + i), m2 = __ldg(m + 2 * N + i), si = __ldg(s + i);
+        const int mi = ly * kTX + lane;
+        const T m0 = ms[mi], m1 = ms[kTY * kTX + mi], m2 = ms[2 * kTY * kTX + mi], si = ms[3 * kTY * kTX + mi];
         const T hx = ax[k] - si * vx, hy = ay[k] - si * vy, hz = az[k] - twoK * vz - si * vz;
         const T p = m0 * hx + m1 * hy + m2 * hz;
         hv[i] = hx - p * m0;
@@ -219,7 +239,7 @@ template <typename T>
 void launch_hvp_strip(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
                       int nvec, const int* gate, int mask, cudaStream_t st) {
   const dim3 grid((md.L1 + kTX - 1) / kTX, (md.L2 + kTY - 1) / kTY);
-  const size_t smem = 2 * 3 * (size_t)kSX * kSY * sizeof(T);
+  const size_t smem = (2 * 3 * (size_t)kSX * kSY + 4 * (size_t)kTY * kTX) * sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(hvp_strip_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

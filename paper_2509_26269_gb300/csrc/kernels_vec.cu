@@ -245,6 +245,213 @@ void launch_combine(const T* X, size_t ldx, int nx, const int* nx_dev, const dou
                                                  N, gate, mask);
 }
 
+namespace {
+constexpr int kUpdSelf = 36;  // upper-triangle entries of an 8 x 8 Gram
+}  // namespace
+
+// ===========================================================================
+// Cholesky QR applied twice without storing the first factor's product.
+// t = X P (X: nx <= 8 fields, P = R1^{-1}) is formed per element in registers
+// by t_c = fma(x_7, P[7][c], ... fma(x_0, P[0][c], 0)) (rows past nx are
+// zero), the same chain in both kernels below, so the Gram of the second pass
+// and the final combination see bit-identical t:
+//   chol2_gram: out = t^T t;
+//   combine2:   Q = t P2 (P2 = R2^{-1}), projected on the tangent planes of m
+//               when m is given.
+// ===========================================================================
+namespace {
+template <typename T>
+__device__ __forceinline__ T pre_mul(const T (&x)[8], const T* Ps, int c) {
+  T t = (T)0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) t = fma(x[r], Ps[r * 8 + c], t);
+  return t;
+}
+}  // namespace
+
+namespace {
+template <typename T>
+struct Vec16T;
+template <>
+struct Vec16T<float> {
+  typedef float4 V;
+  static constexpr int VE = 4;
+  static __device__ __forceinline__ void unpack(const float4& v, float (&a)[4]) {
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+  }
+};
+template <>
+struct Vec16T<double> {
+  typedef double2 V;
+  static constexpr int VE = 2;
+  static __device__ __forceinline__ void unpack(const double2& v, double (&a)[2]) {
+    a[0] = v.x;
+    a[1] = v.y;
+  }
+};
+}  // namespace
+
+// A thread owns VE consecutive elements (one 16-byte load per field).
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __restrict__ X, size_t ldx, int nx,
+                                                                 const double* __restrict__ P, size_t n,
+                                                                 double* out, double* part, unsigned* counter,
+                                                                 const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  typedef Vec16T<T> VTT;
+  typedef typename VTT::V V;
+  constexpr int VE = VTT::VE;
+  __shared__ __align__(16) T Ps[64];
+  __shared__ double red[kThreads / 32][kUpdSelf];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    const int r = i >> 3, c = i & 7;
+    Ps[i] = (r < nx && c < nx) ? (T)P[r * nx + c] : (T)0;
+  }
+  __syncthreads();
+  T sacc[kUpdSelf];
+#pragma unroll
+  for (int q = 0; q < kUpdSelf; ++q) sacc[q] = (T)0;
+  const size_t nv = (n + VE - 1) / VE;
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = v * VE;
+    const bool full = e + VE <= n;
+    T x[VE][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      T a[VE];
+#pragma unroll
+      for (int k = 0; k < VE; ++k) a[k] = (T)0;
+      if (r < nx) {
+        if (full) {
+          VTT::unpack(__ldg(reinterpret_cast<const V*>(X + (size_t)r * ldx + e)), a);
+        } else {
+#pragma unroll
+          for (int k = 0; k < VE; ++k) a[k] = e + k < n ? X[(size_t)r * ldx + e + k] : (T)0;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < VE; ++k) x[k][r] = a[k];
+    }
+#pragma unroll
+    for (int k = 0; k < VE; ++k) {
+      T t[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) t[c] = pre_mul<T>(x[k], Ps, c);
+      int q = 0;
+#pragma unroll
+      for (int c1 = 0; c1 < 8; ++c1)
+#pragma unroll
+        for (int c2 = c1; c2 < 8; ++c2, ++q) sacc[q] = fma(t[c1], t[c2], sacc[q]);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kUpdSelf; ++q) {
+    const double sq = warp_sum((double)sacc[q]);
+    if (lane == 0) red[wid][q] = sq;
+  }
+  __syncthreads();
+  if (threadIdx.x < kUpdSelf) {
+    double acc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
+    part[(size_t)blockIdx.x * kUpdSelf + threadIdx.x] = acc;
+  }
+  if (!grid_last_block(counter)) return;
+  if (threadIdx.x < kUpdSelf) {
+    double acc = 0.0;
+    for (int bb = 0; bb < (int)gridDim.x; ++bb) acc += __ldcg(part + (size_t)bb * kUpdSelf + threadIdx.x);
+    int c1 = 0, rem = threadIdx.x;
+    while (rem >= 8 - c1) {
+      rem -= 8 - c1;
+      ++c1;
+    }
+    const int c2 = c1 + rem;
+    if (c2 < nx) {
+      out[c1 * nx + c2] = acc;
+      out[c2 * nx + c1] = acc;
+    }
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) combine2_kernel(const T* __restrict__ X, size_t ldx, int nx,
+                                                            const double* __restrict__ P1,
+                                                            const double* __restrict__ P2, T* out, size_t ldo,
+                                                            const T* __restrict__ m, int N, const int* gate,
+                                                            int mask) {
+  if (gate && (*gate & mask)) return;
+  __shared__ __align__(16) T P1s[64], P2s[64];
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    const int r = i >> 3, c = i & 7;
+    P1s[i] = (r < nx && c < nx) ? (T)P1[r * nx + c] : (T)0;
+    P2s[i] = (r < nx && c < nx) ? (T)P2[r * nx + c] : (T)0;
+  }
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T q[8][3];
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+      T x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = r < nx ? __ldg(X + (size_t)r * ldx + (size_t)comp * N + i) : (T)0;
+      T t[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) t[c] = pre_mul<T>(x, P1s, c);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        T a = (T)0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) a = fma(t[r], P2s[r * 8 + c], a);
+        q[c][comp] = a;
+      }
+    }
+    T m0 = 0, m1 = 0, m2 = 0;
+    if (m) {
+      m0 = __ldg(m + i);
+      m1 = __ldg(m + N + i);
+      m2 = __ldg(m + 2 * (size_t)N + i);
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c >= nx) continue;
+      T a0 = q[c][0], a1 = q[c][1], a2 = q[c][2];
+      if (m) {
+        const T p = m0 * a0 + m1 * a1 + m2 * a2;
+        a0 -= p * m0;
+        a1 -= p * m1;
+        a2 -= p * m2;
+      }
+      out[(size_t)c * ldo + i] = a0;
+      out[(size_t)c * ldo + N + i] = a1;
+      out[(size_t)c * ldo + 2 * (size_t)N + i] = a2;
+    }
+  }
+}
+
+template <typename T>
+bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double* P2, T* Q, size_t ldq, const T* m,
+                  int N, double* S2, double* part, unsigned* counter, const int* gate, int mask, bool gram,
+                  cudaStream_t st) {
+  if (nx < 1 || nx > 8) return false;
+  if (gram) {
+    constexpr int VE = Vec16T<T>::VE;
+    if (((uintptr_t)X % 16) || (ldx % VE)) return false;
+    const size_t n = 3 * (size_t)N;
+    size_t g = ((n + VE - 1) / VE + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)kSMs * 4;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    chol2_gram_kernel<T><<<(int)g, kThreads, 0, st>>>(X, ldx, nx, P1, n, S2, part, counter, gate, mask);
+  } else {
+    combine2_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask);
+  }
+  return true;
+}
+
 // ===========================================================================
 // projection and Ritz finishing
 // ===========================================================================
@@ -1204,6 +1411,8 @@ void launch_saddle_test(const double* eg_out, const double* fmax, const double* 
 #define INST(T)                                                                                                   \
   template void launch_gram<T>(const T*, size_t, int, const T*, size_t, int, size_t, double*, double*, unsigned*, \
                                const int*, int, cudaStream_t);                                                    \
+  template bool launch_chol2<T>(const T*, size_t, int, const double*, const double*, T*, size_t, const T*, int,  \
+                                double*, double*, unsigned*, const int*, int, bool, cudaStream_t);             \
   template void launch_combine<T>(const T*, size_t, int, const int*, const double*, int, const T*, size_t,        \
                                   double, double, T*, size_t, const T*, int, const int*, int, cudaStream_t);      \
   template void launch_project<T>(const T*, const T*, size_t, T*, size_t, int, int, const int*, int,              \
