@@ -114,7 +114,7 @@ void P_project(moto_ctx* c, const T* m, const T* in, size_t ldi, T* out, size_t 
 template <typename T>
 void P_finish(moto_ctx* c, const T* m, T* V, size_t ldv, int k, int N, double* part, unsigned* counter, double* scal,
               const int* gate, int mask, cudaStream_t st) {
-  PROF(kPkVec, (3.0 + 12.0 * k) * N * sizeof(T));
+  PROF(kPkVec, (6.0 + 9.0 * k) * N * sizeof(T));
   launch_finish<T>(m, V, ldv, k, N, part, counter, scal, gate, mask, st);
 }
 template <typename T>
@@ -349,11 +349,11 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   P_chol2_gram<T>(c, W, b, D + kRinv, D + kG, gate, mk, st);
   P_cholqr(c, D + kG, b, 1, -1, D + kRinv2, D + kRacc, D + kT, kLd, c->st, rel, st);
   P_combine2<T>(c, W, b, D + kRinv, D + kRinv2, Q, nullptr, gate, mk, st);
-  // Block Lanczos step j, reorthogonalised twice: W = H Q_j; a local pass
-  // against the last two blocks (G1 = [Q_{j-1} Q_j]^T W, whose Q_j rows give
-  // T(j, j); W <- W - [Q_{j-1} Q_j] G1, with G2 = Q^T W over the whole basis in
-  // the same sweep); a full pass W <- W - Q G2 with S = W^T W in the same
-  // sweep; Cholesky QR of W (twice) gives Q_{j+1} and R = T(j+1, j).  The new
+  // Block Lanczos step j, reorthogonalised twice: W = H Q_j; A = Q_j^T W gives
+  // T(j, j) = sym(A); a local pass W <- W - Q_j T(j, j) - Q_{j-1} R_j^T (the
+  // three-term recurrence), with G2 = Q^T W over the whole basis in the same
+  // sweep; a full pass W <- W - Q G2 with S = W^T W in the same sweep;
+  // Cholesky QR of W (twice) gives Q_{j+1} and R_{j+1} = T(j+1, j).  The new
   // block is re-projected on the tangent planes in its final combination (a
   // small beta would otherwise magnify rounding-level normal components step
   // after step).  The basis is read twice per step.
@@ -361,12 +361,12 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
     T* Qj = Q + (size_t)j * b * ld;
     const int nq = (j + 1) * b;
     const int jl = j > 0 ? 1 : 0;  // local block rows: Q_{j-1} (if any), Q_j
-    T* Qloc = Q + (size_t)(j - jl) * b * ld;
     P_hvp<T>(c, c->md, m, s, Qj, ld, W, ld, b, gate, mk, st);
-    P_tile<T>(c, 0, Qloc, (jl + 1) * b, 0, 0, W, b, nullptr, nullptr, D + kC, gate, mk, st);
-    P_arnoldi_diag(c, D + kC, b, jl, j, D + kT, kLd, c->st, st);
+    P_tile<T>(c, 0, Qj, b, 0, 0, W, b, nullptr, nullptr, D + kC, gate, mk, st);
+    // T(j, j) = sym(Q_j^T H Q_j); local coefficients [R_j^T; T(j, j)]
+    P_lanczos_coeffs(c, D + kC, b, j, D + kT, kLd, D + kC3, c->st, st);
     if (j == steps - 1) break;
-    P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC, W, D + kC2, gate, mk, st);
+    P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC3, W, D + kC2, gate, mk, st);
     P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
     P_chol2_gram<T>(c, W, b, D + kRinv, D + kG, gate, mk, st);

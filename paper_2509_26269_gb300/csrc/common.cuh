@@ -105,14 +105,34 @@ __device__ __forceinline__ bool grid_last_block(unsigned* counter) {
   return last;
 }
 
-// Inside the last block: tot[j] = sum_b part[b * nv + j] in b order (the
-// sequential order per entry makes the result independent of which block came
-// last).  Threads split the entries.
+// Inside the last block: tot[j] = sum_b part[b * nv + j] in an order fixed by
+// (nblocks, nv, blockDim), so the result does not depend on which block came
+// last.  Few blocks: a thread per entry adds the blocks in index order (loads
+// issued eight at a time); many blocks and few entries: a warp per entry, lane
+// l adding blocks l, l + 32, ... in order, then a fixed shuffle tree.
 __device__ __forceinline__ void grid_sum_entries(const double* part, int nblocks, int nv, double* tot) {
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    double a = 0.0;
-    for (int b = 0; b < nblocks; ++b) a += __ldcg(part + (size_t)b * nv + j);
-    tot[j] = a;
+  if (nblocks <= 256 || nv >= (int)blockDim.x) {
+    for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+      double a = 0.0;
+      int b = 0;
+      for (; b + 8 <= nblocks; b += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (size_t)(b + u) * nv + j);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a += v[u];
+      }
+      for (; b < nblocks; ++b) a += __ldcg(part + (size_t)b * nv + j);
+      tot[j] = a;
+    }
+  } else {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = wid; j < nv; j += nw) {
+      double a = 0.0;
+      for (int b = lane; b < nblocks; b += 32) a += __ldcg(part + (size_t)b * nv + j);
+      a = warp_sum(a);
+      if (lane == 0) tot[j] = a;
+    }
   }
 }
 

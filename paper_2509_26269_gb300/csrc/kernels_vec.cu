@@ -360,9 +360,11 @@ __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __rest
     part[(size_t)blockIdx.x * kUpdSelf + threadIdx.x] = acc;
   }
   if (!grid_last_block(counter)) return;
+  __syncthreads();
+  grid_sum_entries(part, gridDim.x, kUpdSelf, red[0]);
+  __syncthreads();
   if (threadIdx.x < kUpdSelf) {
-    double acc = 0.0;
-    for (int bb = 0; bb < (int)gridDim.x; ++bb) acc += __ldcg(part + (size_t)bb * kUpdSelf + threadIdx.x);
+    const double acc = red[0][threadIdx.x];
     int c1 = 0, rem = threadIdx.x;
     while (rem >= 8 - c1) {
       rem -= 8 - c1;
@@ -488,8 +490,8 @@ __device__ __forceinline__ void amax_merge(double& a, double& ai, double& av, do
   }
 }
 
-// pass 1: V_c <- P(V_c); partials per block and vector: |V_c|^2, max |entry|,
-// its flat index, its signed value.  Per-thread shares are kept in the field
+// pass 1: partials per block and vector of P(V_c) (computed, not stored):
+// |P V_c|^2, max |entry|, its flat index, its signed value.  Per-thread shares are kept in the field
 // precision (a thread sees ~40 entries; comparisons of |entries| are exact in
 // either precision) and promoted to FP64 for the cross-thread reductions.
 template <typename A>
@@ -502,13 +504,14 @@ __device__ __forceinline__ void amax_merge_t(A& a, int& ai, A& av, A b, int bi, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__ m, T* V, size_t ldv, int k, int N,
-                                                           double* part, unsigned* counter, double* scal,
-                                                           const int* gate, int mask) {
+__global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__ m, const T* __restrict__ V,
+                                                           size_t ldv, int k, int N, double* part, unsigned* counter,
+                                                           double* scal, const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
   T nrm_t[MOTO_MAX_K], amx_t[MOTO_MAX_K], aval_t[MOTO_MAX_K];
   int aidx_t[MOTO_MAX_K];
-  for (int c = 0; c < k; ++c) {
+#pragma unroll
+  for (int c = 0; c < MOTO_MAX_K; ++c) {
     nrm_t[c] = (T)0;
     amx_t[c] = (T)-1;
     aidx_t[c] = 0x7fffffff;
@@ -516,34 +519,28 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
-    for (int c = 0; c < k; ++c) {
-      T* v = V + (size_t)c * ldv;
-      T a0 = v[i], a1 = v[N + i], a2 = v[2 * (size_t)N + i];
+#pragma unroll
+    for (int c = 0; c < MOTO_MAX_K; ++c) {
+      if (c >= k) break;
+      const T* v = V + (size_t)c * ldv;
+      T a0 = __ldg(v + i), a1 = __ldg(v + N + i), a2 = __ldg(v + 2 * (size_t)N + i);
       const T p = m0 * a0 + m1 * a1 + m2 * a2;
       a0 -= p * m0;
       a1 -= p * m1;
       a2 -= p * m2;
-      v[i] = a0;
-      v[N + i] = a1;
-      v[2 * (size_t)N + i] = a2;
       nrm_t[c] += a0 * a0 + a1 * a1 + a2 * a2;
       amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a0), i, a0);
       amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a1), N + i, a1);
       amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a2), 2 * N + i, a2);
     }
   }
-  double nrm[MOTO_MAX_K], amx[MOTO_MAX_K], aidx[MOTO_MAX_K], aval[MOTO_MAX_K];
-  for (int c = 0; c < k; ++c) {
-    nrm[c] = (double)nrm_t[c];
-    amx[c] = (double)amx_t[c];
-    aidx[c] = aidx_t[c] == 0x7fffffff ? 1e300 : (double)aidx_t[c];
-    aval[c] = (double)aval_t[c];
-  }
   __shared__ double sh[kThreads / 32][4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c = 0; c < k; ++c) {
-    double s = warp_sum(nrm[c]);
-    double a = amx[c], ai = aidx[c], av = aval[c];
+#pragma unroll
+  for (int c = 0; c < MOTO_MAX_K; ++c) {
+    if (c >= k) break;
+    double s = warp_sum((double)nrm_t[c]);
+    double a = (double)amx_t[c], ai = aidx_t[c] == 0x7fffffff ? 1e300 : (double)aidx_t[c], av = (double)aval_t[c];
     for (int o = 16; o > 0; o >>= 1) {
       const double b = __shfl_xor_sync(0xffffffffu, a, o);
       const double bi = __shfl_xor_sync(0xffffffffu, ai, o);
@@ -572,25 +569,57 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
     __syncthreads();
   }
   if (!grid_last_block(counter)) return;
-  if (threadIdx.x < k) {
-    const int c = threadIdx.x;
+  // warp c reduces vector c: lane l takes blocks l, l + 32, ... in order; the
+  // sums meet in a fixed shuffle tree, the largest entry in any order (ties go
+  // to the lowest index, a total order)
+  if (wid < k) {
+    const int c = wid;
     double S = 0.0, A = -1.0, AI = 1e300, AV = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
       const double* p = part + ((size_t)b * MOTO_MAX_K + c) * 4;
       S += __ldcg(p);
       amax_merge(A, AI, AV, __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3));
     }
-    const double nrm_ = sqrt(S);
-    scal[c] = (nrm_ > 0.0 ? 1.0 / nrm_ : 0.0) * (AV < 0.0 ? -1.0 : 1.0);
+    S = warp_sum(S);
+    for (int o = 16; o > 0; o >>= 1) {
+      const double b = __shfl_xor_sync(0xffffffffu, A, o);
+      const double bi = __shfl_xor_sync(0xffffffffu, AI, o);
+      const double bv = __shfl_xor_sync(0xffffffffu, AV, o);
+      amax_merge(A, AI, AV, b, bi, bv);
+    }
+    if (lane == 0) {
+      const double nrm_ = sqrt(S);
+      scal[c] = (nrm_ > 0.0 ? 1.0 / nrm_ : 0.0) * (AV < 0.0 ? -1.0 : 1.0);
+    }
   }
   if (threadIdx.x == 0) *counter = 0u;
 }
 
+// pass 2: V_c <- scal_c P(V_c) (the projection recomputed exactly as in pass 1)
 template <typename T>
-__global__ void scale_kernel(T* V, size_t ldv, int k, size_t n, const double* scal, const int* gate, int mask) {
+__global__ void __launch_bounds__(kThreads) finish2_kernel(const T* __restrict__ m, T* V, size_t ldv, int k, int N,
+                                                           const double* scal, const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
-    for (int c = 0; c < k; ++c) V[(size_t)c * ldv + e] *= (T)scal[c];
+  __shared__ T sc[MOTO_MAX_K];
+  if (threadIdx.x < MOTO_MAX_K) sc[threadIdx.x] = threadIdx.x < k ? (T)scal[threadIdx.x] : (T)0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+#pragma unroll
+    for (int c = 0; c < MOTO_MAX_K; ++c) {
+      if (c >= k) break;
+      T* v = V + (size_t)c * ldv;
+      T a0 = v[i], a1 = v[N + i], a2 = v[2 * (size_t)N + i];
+      const T p = m0 * a0 + m1 * a1 + m2 * a2;
+      a0 -= p * m0;
+      a1 -= p * m1;
+      a2 -= p * m2;
+      const T f = sc[c];
+      v[i] = a0 * f;
+      v[N + i] = a1 * f;
+      v[2 * (size_t)N + i] = a2 * f;
+    }
+  }
 }
 
 template <typename T>
@@ -598,7 +627,7 @@ void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, uns
                    const int* gate, int mask, cudaStream_t st) {
   const int g = stream_grid(N);
   finish1_kernel<T><<<g, kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask);
-  scale_kernel<T><<<stream_grid(3 * (size_t)N), kThreads, 0, st>>>(V, ldv, k, 3 * (size_t)N, scal, gate, mask);
+  finish2_kernel<T><<<g, kThreads, 0, st>>>(m, V, ldv, k, N, scal, gate, mask);
 }
 
 // ===========================================================================
