@@ -35,6 +35,7 @@ K_MODES, BLOCK, STEPS = 8, 8, 12
 HVP_PER_STEP = BLOCK * STEPS
 METRIC = "spin-HVP Gspin/s"
 UNIT = "Gspin-HVP/s"
+TILE_CLASSES = ("gram", "reorth_gram", "reorth_update")
 WORKLOAD = "roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12)"
 
 
@@ -242,8 +243,12 @@ def run_ours(args, rank, world, local):
     prof = mo.moto_profile_end(ctx.handle)
     torch.cuda.synchronize()
     launches = sum(v[0] for v in prof.values()) + 1  # + the charge kernel
-    dom = max(prof, key=lambda k: prof[k][1])
-    n_l, dom_ms, dom_bytes = prof[dom]
+    # the streaming tile kernel runs the local Grams and both sweeps over the
+    # Krylov basis (three profiler classes, one kernel)
+    kernels = {k: v for k, v in prof.items() if k not in TILE_CLASSES}
+    kernels["tile2d"] = tuple(sum(prof[k][i] for k in TILE_CLASSES) for i in range(3))
+    dom = max(kernels, key=lambda k: kernels[k][1])
+    n_l, dom_ms, dom_bytes = kernels[dom]
     peak, peak_kind = measured_peaks()
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
     hvp = prof["hvp"]

@@ -276,7 +276,9 @@ const char* moto_status_string(int code);
  * solver sequences enqueue, tagged with a kernel class
  *   0 HVP, 1 Gram (skinny X^T Y), 2 field combination, 3 energy/gradient
  *   stencil, 4 single-block FP64 steps, 5 other field kernels, 6 the
- *   projected-matrix eigensolver
+ *   projected-matrix eigensolver, 7 block Lanczos local pass + Gram against
+ *   the basis (read-only sweep), 8 block Lanczos full update + Cholesky Gram,
+ *   9 second Cholesky QR Gram
  * and the algorithmic bytes of the launch (every field read or written once).
  * moto_profile_end synchronises, writes per class (nkinds entries each,
  * NULL to skip) the number of launches, the summed event time in ms and the

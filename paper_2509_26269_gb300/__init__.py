@@ -98,7 +98,8 @@ EXPORTED = (
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
-PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig")
+PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
+                 "chol2_gram")
 
 
 # ---------------------------------------------------------------------------

@@ -72,7 +72,19 @@ struct ProfScope {
 #define PROF(kind, bytes) ProfScope MOTO_CAT(prof_scope_, __LINE__)(c, (kind), (double)(bytes), st)
 
 // kernel classes of the profiler
-enum { kPkHvp = 0, kPkGram = 1, kPkCombine = 2, kPkStencil = 3, kPkSmall = 4, kPkVec = 5, kPkEig = 6, kPkCount = 7 };
+enum {
+  kPkHvp = 0,
+  kPkGram = 1,
+  kPkCombine = 2,
+  kPkStencil = 3,
+  kPkSmall = 4,
+  kPkVec = 5,
+  kPkEig = 6,
+  kPkReorthGram = 7,
+  kPkReorthUpd = 8,
+  kPkChol2 = 9,
+  kPkCount = 10
+};
 
 namespace {
 // Profiled launch wrappers: same arguments as the launchers, plus the context.
@@ -146,29 +158,36 @@ void P_retract(moto_ctx* c, T* m, T* d, const DevState* dst, int N, const int* g
 // mode 1 only X rows u0 .. u0 + nu - 1 take part in the update.
 template <typename T>
 void P_tile(moto_ctx* c, int mode, const T* X, int nx, int u0, int nu, T* Y, int ny, const double* C, T* Yout,
-            double* out, const int* gate, int mask, cudaStream_t st) {
+            double* out, const int* gate, int mask, cudaStream_t st, const double* Cadd = nullptr, int uadd = 0,
+            int nadd = 0) {
   const size_t ld = c->ld;
   const int N = c->N;
   bool done;
   {
     const double f = 3.0 * N * sizeof(T);
-    const double fields = (mode == 0) ? nx + ny : (mode == 3 ? nx + ny : nx + 2.0 * ny);
-    PROF(kPkGram, f * fields);
+    const double fields = (mode == 0 || (mode == 1 && !Yout)) ? nx + ny : (mode == 3 ? nx + ny : nx + 2.0 * ny);
+    PROF(mode == 1 ? kPkReorthGram : (mode == 2 ? kPkReorthUpd : kPkGram), f * fields);
     set_gram_status(&c->st->status);
     done = launch_tile<T>(mode, X, ld, nx, u0, nu, Y, ld, ny, c->n3, C, Yout, ld, out, c->part, c->counter, gate,
-                          mask, &c->st->status, st);
+                          mask, &c->st->status, st, Cadd, uadd, nadd);
   }
   if (done) return;
   switch (mode) {
     case 0:
       P_gram<T>(c, X, ld, nx, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
       break;
-    case 1:
-      P_combine<T>(c, X + (size_t)u0 * ld, ld, nu, nullptr, C, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate, mask,
+    case 1: {
+      // unstored update: the updated fields go to the scratch block
+      T* U = Yout ? Y : static_cast<T*>(c->Wt);
+      P_combine<T>(c, X + (size_t)u0 * ld, ld, nu, nullptr, C, ny, Y, ld, 1.0, -1.0, U, ld, nullptr, N, gate, mask,
                    st);
-      P_gram<T>(c, X, ld, nx, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
+      P_gram<T>(c, X, ld, nx, U, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
       break;
+    }
     case 2:
+      if (Cadd)
+        P_combine<T>(c, X + (size_t)uadd * ld, ld, nadd, nullptr, Cadd, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate,
+                     mask, st);
       P_combine<T>(c, X, ld, nx, nullptr, C, ny, Y, ld, 1.0, -1.0, Y, ld, nullptr, N, gate, mask, st);
       P_gram<T>(c, Y, ld, ny, Y, ld, ny, c->n3, out, c->part, c->counter, gate, mask, st);
       break;
@@ -188,7 +207,7 @@ __global__ void set_status_kernel(DevState* st, int bits) {
 template <typename T>
 void P_chol2_gram(moto_ctx* c, const T* W, int b, const double* R1inv, double* S2, const int* gate, int mask,
                   cudaStream_t st) {
-  PROF(kPkGram, (double)b * 3.0 * c->N * sizeof(T));
+  PROF(kPkChol2, (double)b * 3.0 * c->N * sizeof(T));
   if (!launch_chol2<T>(W, c->ld, b, R1inv, nullptr, nullptr, 0, nullptr, c->N, S2, c->part, c->counter, gate, mask,
                        true, st))
     set_status_kernel<<<1, 1, 0, st>>>(c->st, kStatusNotSPD);
@@ -350,13 +369,14 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   P_cholqr(c, D + kG, b, 1, -1, D + kRinv2, D + kRacc, D + kT, kLd, c->st, rel, st);
   P_combine2<T>(c, W, b, D + kRinv, D + kRinv2, Q, nullptr, gate, mk, st);
   // Block Lanczos step j, reorthogonalised twice: W = H Q_j; A = Q_j^T W gives
-  // T(j, j) = sym(A); a local pass W <- W - Q_j T(j, j) - Q_{j-1} R_j^T (the
-  // three-term recurrence), with G2 = Q^T W over the whole basis in the same
-  // sweep; a full pass W <- W - Q G2 with S = W^T W in the same sweep;
-  // Cholesky QR of W (twice) gives Q_{j+1} and R_{j+1} = T(j+1, j).  The new
-  // block is re-projected on the tangent planes in its final combination (a
-  // small beta would otherwise magnify rounding-level normal components step
-  // after step).  The basis is read twice per step.
+  // T(j, j) = sym(A); the local pass W1 = W - Q_j T(j, j) - Q_{j-1} R_j^T (the
+  // three-term recurrence) is formed in registers only, for G2 = Q^T W1 over
+  // the whole basis (a read-only sweep); the full pass then writes
+  // W <- W - [Q_{j-1}, Q_j] C3 - Q G2 (= W1 - Q G2) with S = W^T W in the same
+  // sweep; Cholesky QR of W (twice) gives Q_{j+1} and R_{j+1} = T(j+1, j).  The
+  // new block is re-projected on the tangent planes in its final combination
+  // (a small beta would otherwise magnify rounding-level normal components
+  // step after step).  The basis is read twice per step, W written once.
   for (int j = 0; j < steps; ++j) {
     T* Qj = Q + (size_t)j * b * ld;
     const int nq = (j + 1) * b;
@@ -366,8 +386,8 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
     // T(j, j) = sym(Q_j^T H Q_j); local coefficients [R_j^T; T(j, j)]
     P_lanczos_coeffs(c, D + kC, b, j, D + kT, kLd, D + kC3, c->st, st);
     if (j == steps - 1) break;
-    P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC3, W, D + kC2, gate, mk, st);
-    P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st);
+    P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC3, nullptr, D + kC2, gate, mk, st);
+    P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st, D + kC3, (j - jl) * b, (jl + 1) * b);
     P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
     P_chol2_gram<T>(c, W, b, D + kRinv, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 1, j, D + kRinv2, D + kRacc, D + kT, kLd, c->st, rel, st);

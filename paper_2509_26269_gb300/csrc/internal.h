@@ -64,13 +64,15 @@ int gram_blocks();
 //   2: Y <- Y - X C, out = Y^T Y;  3: Yout <- X C, out = Yout^T Yout
 // over n elements (fields X at stride ldx, Y at ldy; updated fields go to Yout
 // at stride ldo, Yout == Y for modes 1 and 2; C is nu x ny in mode 1, nx x ny
-// in modes 2 and 3).  Returns false (nothing launched) when a base address or
-// stride breaks the TMA alignment rules; the caller then uses combine + the
-// plain Gram kernel.
+// in modes 2 and 3).  Modes 1 and 3 with Yout == nullptr store nothing: the
+// Gram sees the updated fields, memory keeps the old ones.  Mode 2 may add Cadd
+// (nadd x ny) to rows uadd .. uadd + nadd - 1 of C.  Returns false (nothing
+// launched) when a base address or stride breaks the TMA alignment rules; the
+// caller then uses combine + the plain Gram kernel.
 template <typename T>
 bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
                  const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
-                 int mask, int* status, cudaStream_t st);
+                 int mask, int* status, cudaStream_t st, const double* Cadd = nullptr, int uadd = 0, int nadd = 0);
 // Cholesky QR applied twice without storing X R1^{-1} (kernels_vec.cu): with
 // gram, S2 = (X P1)^T (X P1); without, Q = (X P1) P2, projected on the tangent
 // planes of m when m != NULL.  X: nx <= 8 fields; P1, P2: nx x nx FP64.  Both

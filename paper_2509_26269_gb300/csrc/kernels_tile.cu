@@ -11,9 +11,11 @@
 // warp always touch eight different bank groups.  Modes:
 //
 //   0 (kGram)    : out = X^T Y
-//   1 (kUpdGram) : Y <- Y - X[u0, u0 + nu) C, then out = X^T Y
-//   2 (kUpdSelf) : Y <- Y - X C, then out = Y^T Y
-//   3 (kMulSelf) : Z <- X C,     then out = Z^T Z
+//   1 (kUpdGram) : Y <- Y - X[u0, u0 + nu) C, then out = X^T Y (the updated
+//                  Y may stay unstored: the Gram reads it from the stage)
+//   2 (kUpdSelf) : Y <- Y - X C, then out = Y^T Y (C may be the sum of two
+//                  coefficient blocks, a local one added to some of its rows)
+//   3 (kMulSelf) : Z <- X C,     then out = Z^T Z (Z may stay unstored)
 //
 // C is nu x ny (FP64 in global memory, T in shared memory).  Updated fields are
 // written back with coalesced vector stores; in mode 1 they also replace Y in
@@ -241,8 +243,9 @@ __device__ __forceinline__ void update_rows_d(double (&y)[8][EL], uint32_t xa, i
 template <typename T, int MODE, int R, int CW, int NRL, int TB>
 __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     tile2d_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int nx, int ny,
-                  int u0, int nu, size_t n, const double* __restrict__ C, T* __restrict__ Yout, size_t ldo, double* out,
-                  double* part, unsigned* counter, int nst, int tps, const int* gate, int mask, int* status) {
+                  int u0, int nu, size_t n, const double* __restrict__ C, const double* __restrict__ Cadd, int uadd,
+                  int nadd, T* __restrict__ Yout, size_t ldo, double* out, double* part, unsigned* counter, int nst,
+                  int tps, const int* gate, int mask, int* status) {
   if (gate && (*gate & mask)) return;
   typedef TileT<T> TT;
   typedef typename TT::Acc Acc;
@@ -287,7 +290,8 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   if (MODE != 0)
     for (int i = threadIdx.x; i < nu * 8; i += blockDim.x) {
       const int r = i >> 3, c = i & 7;
-      const double cf = c < ny ? C[r * ny + c] : 0.0;
+      double cf = c < ny ? C[r * ny + c] : 0.0;
+      if (Cadd && c < ny && r >= uadd && r < uadd + nadd) cf += Cadd[(r - uadd) * ny + c];
       Cs[i] = (T)(MODE == 3 ? cf : -cf);
     }
   if (threadIdx.x == 0) {
@@ -405,7 +409,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           if (c < ny) {
-            Lane<T, EL>::store_global(Yout + (size_t)c * ldo + el, el, n, yv[c]);
+            if (MODE == 2 || Yout) Lane<T, EL>::store_global(Yout + (size_t)c * ldo + el, el, n, yv[c]);
             if (MODE == 1) Lane<T, EL>::store_smem(ya + (uint32_t)c * TB, yv[c]);
           }
         }
@@ -575,7 +579,7 @@ int tile_bytes(int nx) {
 
 template <typename T, int MODE, int R, int CW, int NRL, int TB>
 void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
-                 const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
+                 const double* C, const double* Cadd, int uadd, int nadd, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
                  int mask, int* status, cudaStream_t st) {
   constexpr int TE = TB / (int)sizeof(T);
   const int nxp = (nx + 7) & ~7;
@@ -602,16 +606,16 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   if (want > cap) want = cap;
   const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
   const int grid = (int)(ngroups < want ? (ngroups > 0 ? ngroups : 1) : want);
-  tile2d_kernel<T, MODE, R, CW, NRL, TB><<<grid, kThrT, smem, st>>>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out,
+  tile2d_kernel<T, MODE, R, CW, NRL, TB><<<grid, kThrT, smem, st>>>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out,
                                                                     part, counter, nst, tps, gate, mask, status);
 }
 
 template <typename T, int MODE, int TB>
 void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
-                   const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter,
+                   const double* C, const double* Cadd, int uadd, int nadd, T* Yout, size_t ldo, double* out, double* part, unsigned* counter,
                    const int* gate, int mask, int* status, cudaStream_t st) {
 #define TL(RR, CC, NN)                                                                                           \
-  tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out, part, counter, gate, mask, \
+  tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, gate, mask, \
                                        status, st)
   if constexpr (MODE >= 2) {
     TL(1, 4, 16);
@@ -634,10 +638,12 @@ void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny,
 template <typename T>
 bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
                  const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
-                 int mask, int* status, cudaStream_t st) {
+                 int mask, int* status, cudaStream_t st, const double* Cadd, int uadd, int nadd) {
   auto al = [](const void* p) { return ((uintptr_t)p % 16) == 0; };
   if ((ldx * sizeof(T)) % 16 || (ldy * sizeof(T)) % 16 || !al(X) || (mode != 3 && !al(Y))) return false;
-  if (mode != 0 && ((ldo * sizeof(T)) % 16 || !al(Yout))) return false;
+  if (mode == 2 && !Yout) return false;
+  if (mode != 0 && Yout && ((ldo * sizeof(T)) % 16 || !al(Yout))) return false;
+  if (Cadd && (mode != 2 || uadd < 0 || nadd < 0 || uadd + nadd > nx)) return false;
   if (nx < 1 || nx > MOTO_MAX_BASIS || ny < 1 || ny > 8 || n >= (1ull << 31)) return false;
   if (mode == 1 && (u0 < 0 || nu < 0 || u0 + nu > nx)) return false;
   if (mode >= 2) {
@@ -652,7 +658,7 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
   } else {
     my = mx;
   }
-#define TD(M, B) tile_dispatch<T, M, B>(mx, my, nx, ny, u0, nu, n, C, Yout, ldo, out, part, counter, gate, mask, status, st)
+#define TD(M, B) tile_dispatch<T, M, B>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, gate, mask, status, st)
   if constexpr (sizeof(T) == 8) {
     switch (mode) {
       case 0: TD(0, 512); break;
@@ -678,9 +684,9 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
 
 template bool launch_tile<float>(int, const float*, size_t, int, int, int, const float*, size_t, int, size_t,
                                  const double*, float*, size_t, double*, double*, unsigned*, const int*, int, int*,
-                                 cudaStream_t);
+                                 cudaStream_t, const double*, int, int);
 template bool launch_tile<double>(int, const double*, size_t, int, int, int, const double*, size_t, int, size_t,
                                   const double*, double*, size_t, double*, double*, unsigned*, const int*, int, int*,
-                                  cudaStream_t);
+                                  cudaStream_t, const double*, int, int);
 
 }  // namespace moto

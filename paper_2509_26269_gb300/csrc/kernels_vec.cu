@@ -251,95 +251,126 @@ constexpr int kUpdSelf = 36;  // upper-triangle entries of an 8 x 8 Gram
 
 // ===========================================================================
 // Cholesky QR applied twice without storing the first factor's product.
-// t = X P (X: nx <= 8 fields, P = R1^{-1}) is formed per element in registers
-// by t_c = fma(x_7, P[7][c], ... fma(x_0, P[0][c], 0)) (rows past nx are
-// zero), the same chain in both kernels below, so the Gram of the second pass
-// and the final combination see bit-identical t:
+// t = X P (X: nx <= 8 fields, P = R1^{-1}, upper triangular) is formed per
+// element in registers by t_c = fma(x_c, P[c][c], ... fma(x_0, P[0][c], 0))
+// (rows past nx are zero), the same chain in both kernels below, so the Gram
+// of the second pass and the final combination see bit-identical t (a packed
+// fma.rn.f32x2 rounds each half exactly like fma.rn.f32):
 //   chol2_gram: out = t^T t;
-//   combine2:   Q = t P2 (P2 = R2^{-1}), projected on the tangent planes of m
-//               when m is given.
+//   combine2:   Q = t P2 (P2 = R2^{-1}, upper triangular), projected on the
+//               tangent planes of m when m is given.
 // ===========================================================================
 namespace {
+__device__ __forceinline__ float2 ffma2v(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
+// t = x P over the upper triangle: t[c] takes rows r = 0 .. c in order
 template <typename T>
-__device__ __forceinline__ T pre_mul(const T (&x)[8], const T* Ps, int c) {
-  T t = (T)0;
+__device__ __forceinline__ void tri_mul(const T (&x)[8], const T* Ps, T (&t)[8]) {
 #pragma unroll
-  for (int r = 0; r < 8; ++r) t = fma(x[r], Ps[r * 8 + c], t);
-  return t;
+  for (int c = 0; c < 8; ++c) t[c] = (T)0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = r; c < 8; ++c) t[c] = fma(x[r], Ps[r * 8 + c], t[c]);
+}
+// P rows are re-read from shared memory (volatile loads: hoisting all 36
+// entries into registers out of a streaming loop would cost more than the
+// broadcast loads)
+__device__ __forceinline__ void tri_mul2(const float2 (&x)[8], const float* Ps, float2 (&t)[8]) {
+  const uint32_t pa = (uint32_t)__cvta_generic_to_shared(Ps);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) t[c] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float p[8];
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(p[0]), "=f"(p[1]), "=f"(p[2]), "=f"(p[3])
+                 : "r"(pa + 32u * r));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(p[4]), "=f"(p[5]), "=f"(p[6]), "=f"(p[7])
+                 : "r"(pa + 32u * r + 16u));
+#pragma unroll
+    for (int c = r; c < 8; ++c) t[c] = ffma2v(x[r], make_float2(p[c], p[c]), t[c]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_tri(T* Ps, const double* P, int nx) {
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
+    const int r = i >> 3, c = i & 7;
+    Ps[i] = (r < nx && c < nx && r <= c) ? (T)P[r * nx + c] : (T)0;
+  }
 }
 }  // namespace
 
-namespace {
-template <typename T>
-struct Vec16T;
-template <>
-struct Vec16T<float> {
-  typedef float4 V;
-  static constexpr int VE = 4;
-  static __device__ __forceinline__ void unpack(const float4& v, float (&a)[4]) {
-    a[0] = v.x;
-    a[1] = v.y;
-    a[2] = v.z;
-    a[3] = v.w;
-  }
-};
-template <>
-struct Vec16T<double> {
-  typedef double2 V;
-  static constexpr int VE = 2;
-  static __device__ __forceinline__ void unpack(const double2& v, double (&a)[2]) {
-    a[0] = v.x;
-    a[1] = v.y;
-  }
-};
-}  // namespace
-
-// A thread owns VE consecutive elements (one 16-byte load per field).
+// FP32: a thread owns element pairs (8-byte loads, packed FMAs for t, the
+// next pair loading while one is multiplied); FP64: single elements.
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __restrict__ X, size_t ldx, int nx,
                                                                  const double* __restrict__ P, size_t n,
                                                                  double* out, double* part, unsigned* counter,
                                                                  const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
-  typedef Vec16T<T> VTT;
-  typedef typename VTT::V V;
-  constexpr int VE = VTT::VE;
   __shared__ __align__(16) T Ps[64];
   __shared__ double red[kThreads / 32][kUpdSelf];
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-    const int r = i >> 3, c = i & 7;
-    Ps[i] = (r < nx && c < nx) ? (T)P[r * nx + c] : (T)0;
-  }
+  stage_tri(Ps, P, nx);
   __syncthreads();
   T sacc[kUpdSelf];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if constexpr (sizeof(T) == 4) {
+    // the next element pair is in flight while one is multiplied
 #pragma unroll
-  for (int q = 0; q < kUpdSelf; ++q) sacc[q] = (T)0;
-  const size_t nv = (n + VE - 1) / VE;
-  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nv; v += (size_t)gridDim.x * blockDim.x) {
-    const size_t e = v * VE;
-    const bool full = e + VE <= n;
-    T x[VE][8];
+    for (int q = 0; q < kUpdSelf; ++q) sacc[q] = 0.f;
+    const size_t np = (n + 1) / 2;
+    auto load = [&](size_t v, float2 (&x)[8]) {
+      const size_t e = 2 * v;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      T a[VE];
-#pragma unroll
-      for (int k = 0; k < VE; ++k) a[k] = (T)0;
-      if (r < nx) {
-        if (full) {
-          VTT::unpack(__ldg(reinterpret_cast<const V*>(X + (size_t)r * ldx + e)), a);
-        } else {
-#pragma unroll
-          for (int k = 0; k < VE; ++k) a[k] = e + k < n ? X[(size_t)r * ldx + e + k] : (T)0;
+      for (int r = 0; r < 8; ++r) {
+        x[r] = make_float2(0.f, 0.f);
+        if (r < nx && v < np) {
+          if (e + 2 <= n)
+            x[r] = __ldg(reinterpret_cast<const float2*>(X + (size_t)r * ldx + e));
+          else
+            x[r].x = X[(size_t)r * ldx + e];
         }
       }
+    };
+    auto accumulate = [&](const float2 (&x)[8]) {
+      float2 t[8];
+      tri_mul2(x, Ps, t);
+      int q = 0;
 #pragma unroll
-      for (int k = 0; k < VE; ++k) x[k][r] = a[k];
+      for (int c1 = 0; c1 < 8; ++c1)
+#pragma unroll
+        for (int c2 = c1; c2 < 8; ++c2, ++q) sacc[q] = fmaf(t[c1].y, t[c2].y, fmaf(t[c1].x, t[c2].x, sacc[q]));
+    };
+    size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    float2 xa[8], xb[8];
+    load(v, xa);
+    load(v + stride, xb);
+    for (; v < np; v += 2 * stride) {
+      accumulate(xa);  // xb in flight
+      load(v + 2 * stride, xa);
+      if (v + stride >= np) break;
+      accumulate(xb);  // xa in flight
+      load(v + 3 * stride, xb);
     }
+  } else {
 #pragma unroll
-    for (int k = 0; k < VE; ++k) {
+    for (int q = 0; q < kUpdSelf; ++q) sacc[q] = (T)0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += stride) {
+      T x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) x[r] = r < nx ? __ldg(X + (size_t)r * ldx + e) : (T)0;
       T t[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) t[c] = pre_mul<T>(x[k], Ps, c);
+      tri_mul<T>(x, Ps, t);
       int q = 0;
 #pragma unroll
       for (int c1 = 0; c1 < 8; ++c1)
@@ -347,12 +378,20 @@ __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __rest
         for (int c2 = c1; c2 < 8; ++c2, ++q) sacc[q] = fma(t[c1], t[c2], sacc[q]);
     }
   }
+  // warp sums in the field precision (a fixed butterfly over 32 partials of
+  // a few tens of products each), one FP64 conversion per entry and warp;
+  // block and grid sums in FP64
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kUpdSelf; ++q) {
-    const double sq = warp_sum((double)sacc[q]);
-    if (lane == 0) red[wid][q] = sq;
+    T v = sacc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    sacc[q] = v;
   }
+#pragma unroll
+  for (int q = 0; q < kUpdSelf; ++q)
+    if (lane == (q & 31)) red[wid][q] = (double)sacc[q];
   __syncthreads();
   if (threadIdx.x < kUpdSelf) {
     double acc = 0.0;
@@ -379,7 +418,10 @@ __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __rest
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-template <typename T>
+// Site-based: a thread loads all its fields first (24 per site), then forms
+// t and Q per component.  PAIR (FP32, N even): two adjacent sites per thread
+// with 8-byte loads and packed FMAs.
+template <typename T, bool PAIR>
 __global__ void __launch_bounds__(kThreads) combine2_kernel(const T* __restrict__ X, size_t ldx, int nx,
                                                             const double* __restrict__ P1,
                                                             const double* __restrict__ P2, T* out, size_t ldo,
@@ -387,49 +429,84 @@ __global__ void __launch_bounds__(kThreads) combine2_kernel(const T* __restrict_
                                                             int mask) {
   if (gate && (*gate & mask)) return;
   __shared__ __align__(16) T P1s[64], P2s[64];
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) {
-    const int r = i >> 3, c = i & 7;
-    P1s[i] = (r < nx && c < nx) ? (T)P1[r * nx + c] : (T)0;
-    P2s[i] = (r < nx && c < nx) ? (T)P2[r * nx + c] : (T)0;
-  }
+  stage_tri(P1s, P1, nx);
+  stage_tri(P2s, P2, nx);
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    T q[8][3];
+  if constexpr (PAIR) {
+    const int np = N / 2;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < np; v += gridDim.x * blockDim.x) {
+      const size_t i = 2 * (size_t)v;
+      float2 x[3][8];
 #pragma unroll
-    for (int comp = 0; comp < 3; ++comp) {
-      T x[8];
+      for (int comp = 0; comp < 3; ++comp)
 #pragma unroll
-      for (int r = 0; r < 8; ++r) x[r] = r < nx ? __ldg(X + (size_t)r * ldx + (size_t)comp * N + i) : (T)0;
-      T t[8];
+        for (int r = 0; r < 8; ++r)
+          x[comp][r] = r < nx ? __ldg(reinterpret_cast<const float2*>(X + (size_t)r * ldx + (size_t)comp * N + i))
+                              : make_float2(0.f, 0.f);
+      float2 mm[3];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) t[c] = pre_mul<T>(x, P1s, c);
+      for (int comp = 0; comp < 3; ++comp)
+        mm[comp] = m ? __ldg(reinterpret_cast<const float2*>(m + (size_t)comp * N + i)) : make_float2(0.f, 0.f);
+      float2 q[3][8];
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        float2 t[8];
+        tri_mul2(x[comp], P1s, t);
+        tri_mul2(t, P2s, q[comp]);
+      }
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        T a = (T)0;
-#pragma unroll
-        for (int r = 0; r < 8; ++r) a = fma(t[r], P2s[r * 8 + c], a);
-        q[c][comp] = a;
+        if (c >= nx) continue;
+        float2 a0 = q[0][c], a1 = q[1][c], a2 = q[2][c];
+        if (m) {
+          const float2 p = make_float2(mm[0].x * a0.x + mm[1].x * a1.x + mm[2].x * a2.x,
+                                       mm[0].y * a0.y + mm[1].y * a1.y + mm[2].y * a2.y);
+          a0.x -= p.x * mm[0].x;
+          a0.y -= p.y * mm[0].y;
+          a1.x -= p.x * mm[1].x;
+          a1.y -= p.y * mm[1].y;
+          a2.x -= p.x * mm[2].x;
+          a2.y -= p.y * mm[2].y;
+        }
+        *reinterpret_cast<float2*>(out + (size_t)c * ldo + i) = a0;
+        *reinterpret_cast<float2*>(out + (size_t)c * ldo + N + i) = a1;
+        *reinterpret_cast<float2*>(out + (size_t)c * ldo + 2 * (size_t)N + i) = a2;
       }
     }
-    T m0 = 0, m1 = 0, m2 = 0;
-    if (m) {
-      m0 = __ldg(m + i);
-      m1 = __ldg(m + N + i);
-      m2 = __ldg(m + 2 * (size_t)N + i);
-    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+      T x[3][8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (c >= nx) continue;
-      T a0 = q[c][0], a1 = q[c][1], a2 = q[c][2];
+      for (int comp = 0; comp < 3; ++comp)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) x[comp][r] = r < nx ? __ldg(X + (size_t)r * ldx + (size_t)comp * N + i) : (T)0;
+      T m0 = 0, m1 = 0, m2 = 0;
       if (m) {
-        const T p = m0 * a0 + m1 * a1 + m2 * a2;
-        a0 -= p * m0;
-        a1 -= p * m1;
-        a2 -= p * m2;
+        m0 = __ldg(m + i);
+        m1 = __ldg(m + N + i);
+        m2 = __ldg(m + 2 * (size_t)N + i);
       }
-      out[(size_t)c * ldo + i] = a0;
-      out[(size_t)c * ldo + N + i] = a1;
-      out[(size_t)c * ldo + 2 * (size_t)N + i] = a2;
+      T q[3][8];
+#pragma unroll
+      for (int comp = 0; comp < 3; ++comp) {
+        T t[8];
+        tri_mul<T>(x[comp], P1s, t);
+        tri_mul<T>(t, P2s, q[comp]);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c >= nx) continue;
+        T a0 = q[0][c], a1 = q[1][c], a2 = q[2][c];
+        if (m) {
+          const T p = m0 * a0 + m1 * a1 + m2 * a2;
+          a0 -= p * m0;
+          a1 -= p * m1;
+          a2 -= p * m2;
+        }
+        out[(size_t)c * ldo + i] = a0;
+        out[(size_t)c * ldo + N + i] = a1;
+        out[(size_t)c * ldo + 2 * (size_t)N + i] = a2;
+      }
     }
   }
 }
@@ -440,16 +517,24 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
                   cudaStream_t st) {
   if (nx < 1 || nx > 8) return false;
   if (gram) {
-    constexpr int VE = Vec16T<T>::VE;
-    if (((uintptr_t)X % 16) || (ldx % VE)) return false;
+    if (((uintptr_t)X % (2 * sizeof(T))) || (ldx % 2)) return false;
     const size_t n = 3 * (size_t)N;
-    size_t g = ((n + VE - 1) / VE + kThreads - 1) / kThreads;
-    const size_t cap = (size_t)kSMs * 4;
+    size_t g = ((sizeof(T) == 4 ? (n + 1) / 2 : n) + kThreads - 1) / kThreads;
+    const size_t cap = (size_t)kSMs * 2;  // one wave at two blocks per SM
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     chol2_gram_kernel<T><<<(int)g, kThreads, 0, st>>>(X, ldx, nx, P1, n, S2, part, counter, gate, mask);
   } else {
-    combine2_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask);
+    const bool pair = sizeof(T) == 4 && N % 2 == 0 && ldx % 2 == 0 && ldq % 2 == 0 && (uintptr_t)X % 8 == 0 &&
+                      (uintptr_t)Q % 8 == 0 && (!m || (uintptr_t)m % 8 == 0);
+    if constexpr (sizeof(T) == 4) {
+      if (pair) {
+        combine2_kernel<T, true><<<stream_grid(N / 2), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate,
+                                                                          mask);
+        return true;
+      }
+    }
+    combine2_kernel<T, false><<<stream_grid(N), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask);
   }
   return true;
 }
@@ -539,19 +624,22 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
 #pragma unroll
   for (int c = 0; c < MOTO_MAX_K; ++c) {
     if (c >= k) break;
-    double s = warp_sum((double)nrm_t[c]);
-    double a = (double)amx_t[c], ai = aidx_t[c] == 0x7fffffff ? 1e300 : (double)aidx_t[c], av = (double)aval_t[c];
+    // warp level in the field precision: the sum by a fixed butterfly, the
+    // largest entry (ties: lowest index) in any order
+    T sT = nrm_t[c], aT = amx_t[c], avT = aval_t[c];
+    int aiT = aidx_t[c];
     for (int o = 16; o > 0; o >>= 1) {
-      const double b = __shfl_xor_sync(0xffffffffu, a, o);
-      const double bi = __shfl_xor_sync(0xffffffffu, ai, o);
-      const double bv = __shfl_xor_sync(0xffffffffu, av, o);
-      amax_merge(a, ai, av, b, bi, bv);
+      sT += __shfl_xor_sync(0xffffffffu, sT, o);
+      const T b = __shfl_xor_sync(0xffffffffu, aT, o);
+      const int bi = __shfl_xor_sync(0xffffffffu, aiT, o);
+      const T bv = __shfl_xor_sync(0xffffffffu, avT, o);
+      amax_merge_t<T>(aT, aiT, avT, b, bi, bv);
     }
     if (lane == 0) {
-      sh[wid][0] = s;
-      sh[wid][1] = a;
-      sh[wid][2] = ai;
-      sh[wid][3] = av;
+      sh[wid][0] = (double)sT;
+      sh[wid][1] = (double)aT;
+      sh[wid][2] = aiT == 0x7fffffff ? 1e300 : (double)aiT;
+      sh[wid][3] = (double)avT;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -635,23 +723,21 @@ void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, uns
 // ===========================================================================
 __global__ void lanczos_coeffs_kernel(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st) {
   if (st->gate & (kGateKrylov | kGateDone)) return;
-  if (threadIdx.x != 0) return;
+  // one thread per (r, c) of a b x b block
+  const int r = threadIdx.x >> 3, c = threadIdx.x & 7;
+  if (r >= b || c >= b) return;
   // T(j, j) = sym(A)
-  for (int r = 0; r < b; ++r)
-    for (int c = 0; c < b; ++c) T[(size_t)(j * b + r) * ldT + j * b + c] = 0.5 * (A[r * b + c] + A[c * b + r]);
-  // C3 rows: [R_j^T (for Q_{j-1}); A (for Q_j)],   R_j = T(j, j-1)
-  int row = 0;
-  if (j > 0) {
-    for (int r = 0; r < b; ++r, ++row)
-      for (int c = 0; c < b; ++c) C3[row * b + c] = T[(size_t)(j * b + c) * ldT + (j - 1) * b + r];
-  }
-  for (int r = 0; r < b; ++r, ++row)
-    for (int c = 0; c < b; ++c) C3[row * b + c] = T[(size_t)(j * b + r) * ldT + j * b + c];
+  const double a = 0.5 * (A[r * b + c] + A[c * b + r]);
+  T[(size_t)(j * b + r) * ldT + j * b + c] = a;
+  // C3 rows: [R_j^T (for Q_{j-1}); T(j, j) (for Q_j)],   R_j = T(j, j-1)
+  const int row0 = j > 0 ? b : 0;
+  if (j > 0) C3[r * b + c] = T[(size_t)(j * b + c) * ldT + (j - 1) * b + r];
+  C3[(row0 + r) * b + c] = a;
 }
 
 void launch_lanczos_coeffs(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st,
                            cudaStream_t s) {
-  lanczos_coeffs_kernel<<<1, 32, 0, s>>>(A, b, j, T, ldT, C3, st);
+  lanczos_coeffs_kernel<<<1, 64, 0, s>>>(A, b, j, T, ldT, C3, st);
 }
 
 __global__ void arnoldi_diag_kernel(const double* G1, int b, int jr, int j, double* T, int ldT, DevState* st) {
