@@ -48,7 +48,7 @@ namespace moto {
 using namespace tma;
 
 namespace {
-constexpr int kPairs = 4;  // consumer warp pairs per block
+constexpr int kPairs = 5;  // consumer warp pairs per block
 constexpr int kConsumers = 2 * kPairs;
 constexpr int kThrT = 32 * (kConsumers + 1);
 // 9 warps per block: three of them share one scheduler's 64 KB register file
@@ -254,17 +254,22 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   constexpr int HB = TB / 2;  // bytes of a row a warp of the pair owns
   constexpr int EL = TE / 64;  // elements of a lane in the update layout
   constexpr int NCH = HB / 16;  // 16-byte chunks of a half row
-  static_assert(EL == 1 || EL == 2, "a lane owns 4 to 16 bytes of a row");
+  static_assert(EL == 1 || EL == 2 || (EL == 4 && MODE == 0), "a lane owns 4 to 16 bytes of a row");
   static_assert(EL * (int)sizeof(T) >= 4 && EL * (int)sizeof(T) <= 16, "lane share");
   constexpr bool kGramMode = (MODE <= 1);
   constexpr bool kF32 = sizeof(T) == 4;
   constexpr int NR = kGramMode ? R : 1, NC = kGramMode ? CW : 1;
+  // Gram layout: NRL row lanes x NCG column groups, the remaining lanes split
+  // the chunks of a tile (KS lanes per output, summed at the end)
+  constexpr int NCG = 8 / CW, KS = 32 / (NRL * NCG);
+  static_assert(KS >= 1 && NRL * NCG * KS == 32, "Gram lane layout");
   constexpr int NS = (kF32 && NR * NC <= 8) ? 2 : 1;  // accumulator sets
   constexpr int ND = kGramMode ? (kF32 ? NR * NC : 1) : kSelf;  // FP64 totals
   constexpr int kFlushT = kFlushE / (TE / 2);
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kMaxStages];
   __shared__ __align__(8) uint64_t empty[kMaxStages];
+  __shared__ int tile_of[kMaxStages];  // tile of the stage's latest fill
   __shared__ __align__(16) T Cs[MOTO_MAX_BASIS * 8];
   __shared__ int abort_flag;
 
@@ -280,12 +285,13 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int na = kGramMode ? nx : ny;
 
-  // the block's contiguous range of stage groups (tps tiles each; tiles past
-  // the end of the fields read zeros and store nothing)
+  // stage groups (tps tiles each) interleaved over the blocks: group g goes
+  // to block g mod gridDim.x, so the blocks stream neighbouring tiles of each
+  // field at the same time (DRAM pages are shared between SMs rather than
+  // opened for one 256-byte row each); tiles past the end of the fields read
+  // zeros and store nothing
   const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
-  const size_t t_begin = ngroups * blockIdx.x / gridDim.x;
-  const size_t t_end = ngroups * (blockIdx.x + 1) / gridDim.x;
-  const int ntile = (int)(t_end - t_begin);
+  const int ntile = (int)(ngroups > blockIdx.x ? (ngroups - blockIdx.x + gridDim.x - 1) / gridDim.x : 0);
 
   if (MODE != 0)
     for (int i = threadIdx.x; i < nu * 8; i += blockDim.x) {
@@ -298,6 +304,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     for (int s = 0; s < nst; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 2);
+      tile_of[s] = -1;
     }
     abort_flag = 0;
     fence_async_shared();
@@ -329,9 +336,10 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         }
         if (*(volatile int*)&abort_flag) break;
         unsigned char* buf = ring_ptr + (size_t)s * stage_bytes;
+        *(volatile int*)&tile_of[s] = it;
         mbar_expect_tx(&full[s], tx_bytes);
         for (int q = 0; q < tps; ++q) {
-          const int x = (int)(((t_begin + it) * tps + q) * TE);
+          const int x = (int)(((blockIdx.x + (size_t)it * gridDim.x) * tps + q) * TE);
           tma_load_2d(buf + (size_t)q * tile_b, &tmX, x, 0, &full[s]);
           if (MODE != 3) tma_load_2d(buf + (size_t)q * tile_b + yoff, &tmY, x, 0, &full[s]);
         }
@@ -342,13 +350,14 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     // Gram layout: byte offsets of the lane's rows, chunk skew
     uint32_t xrow[NR], yrow[NC];
     {
-      const int rl = lane % NRL, cl = lane / NRL;
+      const int rl = lane % NRL, cl = (lane / NRL) % NCG;
 #pragma unroll
       for (int i = 0; i < NR; ++i) xrow[i] = (uint32_t)min(rl + NRL * i, na - 1) * TB;
 #pragma unroll
       for (int j = 0; j < NC; ++j) yrow[j] = yoff + (uint32_t)min(cl * CW + j, ny - 1) * TB;
     }
     const int skew = lane & 7;
+    const int ks = lane / (NRL * NCG);  // the lane's share of the chunks
     float sacc[(MODE >= 2 && kF32) ? kSelf : 1];
 #pragma unroll
     for (int i = 0; i < ((MODE >= 2 && kF32) ? kSelf : 1); ++i) sacc[i] = 0.f;
@@ -356,8 +365,25 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     const uint32_t hoff = (uint32_t)g * HB;
     const uint32_t lane_b = hoff + (uint32_t)lane * EL * sizeof(T);  // update layout: the lane's bytes of a row
     int since = 0;
+    // When the ring has a multiple of kPairs stages a stage always goes to the
+    // same pair, whose previous fill of it the pair itself consumed, so the
+    // parity wait cannot confuse fills.  Otherwise a pair may reach a stage two
+    // fills ahead of the producer: it first waits until the producer has
+    // started the fill of its own tile (which happens only after the previous
+    // fill was consumed), which makes the parity wait unambiguous.
+    const bool shared_stages = (nst % kPairs) != 0;
     for (int it = pw; it < ntile; it += kPairs) {
       const int s = it % nst;
+      if (shared_stages) {
+        int spins = 0;
+        while (*(volatile int*)&tile_of[s] != it && !*(volatile int*)&abort_flag && ++spins < (1 << 22))
+          __nanosleep(32);
+        if (spins >= (1 << 22)) {
+          atomicExch(&abort_flag, 1);
+          if (status) atomicOr(status, kStatusTimeout);
+        }
+      }
+      if (*(volatile int*)&abort_flag) break;
       if (!mbar_wait(&full[s], (unsigned)((it / nst) & 1))) {
         atomicExch(&abort_flag, 1);
         if (status) atomicOr(status, kStatusTimeout);
@@ -367,7 +393,8 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
       const uint32_t sb = ring + (uint32_t)s * stage_bytes + (uint32_t)qt * tile_b;
       if (MODE != 0) {
         const uint32_t xa = sb + lane_b, ya = sb + yoff + lane_b;
-        const size_t el = ((t_begin + it) * tps + qt) * TE + (size_t)g * (TE / 2) + (size_t)lane * EL;
+        const size_t el =
+            ((blockIdx.x + (size_t)it * gridDim.x) * tps + qt) * TE + (size_t)g * (TE / 2) + (size_t)lane * EL;
         T yv[8][EL];
         if constexpr (kF32) {
           float2 p[4][EL];
@@ -434,10 +461,12 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         if (MODE == 1) __syncwarp();
       }
       if constexpr (kGramMode) {
-        // Gram phase: acc[.][i][j] += <X row i, Y row j> over the tile, the
-        // lane's walk over the chunks starting at chunk `skew`
+        // Gram phase: acc[.][i][j] += <X row i, Y row j> over the lane's
+        // chunks of the tile (every KS-th), its walk starting at chunk `skew`
+        // (the KS lanes of an output share the skew, so together they cover
+        // every chunk once)
 #pragma unroll 4
-        for (int k = 0; k < NCH; ++k) {
+        for (int k = ks; k < NCH; k += KS) {
           const uint32_t co = sb + hoff + (uint32_t)(((k + skew) & (NCH - 1)) << 4);
           VT xv[NR], yw[NC];
 #pragma unroll
@@ -497,7 +526,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   if (w < kConsumers) {
     double* rw = red + (size_t)w * nout;
     if constexpr (kGramMode) {
-      const int rl = lane % NRL, cl = lane / NRL;
+      const int rl = lane % NRL, cl = (lane / NRL) % NCG, ks = lane / (NRL * NCG);
 #pragma unroll
       for (int i = 0; i < NR; ++i)
 #pragma unroll
@@ -506,7 +535,10 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
           double v = TT::to_d(acc[0][i][j]);
           if (NS == 2) v += TT::to_d(acc[NS - 1][i][j]);
           if constexpr (kF32) v += dacc[i * NC + j];
-          if (r < na && c < ny) rw[r * ny + c] = v;
+          // the KS lanes of an output, in a fixed order
+#pragma unroll
+          for (int o = NRL * NCG; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (ks == 0 && r < na && c < ny) rw[r * ny + c] = v;
         }
     } else {
       int q = 0;
@@ -570,10 +602,13 @@ bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld, in
 
 // Row bytes of a tile: 512 while eight stages still fit (few fields: a copy
 // then moves enough bytes to stay at full rate), else 256; FP64 always 512
-// (a lane's share is one element).
+// (a lane's share is one element).  A Gram of at most 16 x 8 fields (FP32)
+// takes 1024-byte rows: one stage is then one tile of two copies of 8 KB or
+// more (stages of several small copies stream more slowly).
 template <typename T>
-int tile_bytes(int nx) {
+int tile_bytes(int mode, int nx, int ny) {
   if (sizeof(T) == 8) return 512;
+  if (mode == 0 && nx <= 16 && ny <= 8) return 1024;
   return ((nx + 7) / 8 * 8 + 8) * 512 * 8 <= (int)kDynBudget - 1024 ? 512 : 256;
 }
 
@@ -592,7 +627,6 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   const size_t stage_bytes = tps * tile_b;
   int nst = (int)((kDynBudget - 1024) / stage_bytes);
   if (nst > kMaxStages) nst = kMaxStages;
-  nst -= nst % kPairs;  // a stage always goes to the same warp pair
   const size_t smem = (size_t)nst * stage_bytes + 1024;
   static bool attr = false;
   if (!attr) {
@@ -622,9 +656,9 @@ void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny,
   } else if (nx <= 8) {
     TL(1, 2, 8);
   } else if (nx <= 16) {
-    TL(1, 4, 16);
+    TL(4, 4, 4);
   } else if (nx <= 32) {
-    TL(2, 4, 16);
+    TL(4, 4, 8);
   } else if (nx <= 64) {
     TL(4, 4, 16);
   } else {
@@ -650,7 +684,7 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
     u0 = 0;
     nu = nx;
   }
-  const int tb = tile_bytes<T>(nx);
+  const int tb = tile_bytes<T>(mode, nx, ny);
   CUtensorMap mx, my;
   if (!make_map<T>(&mx, X, n, nx, ldx, tb)) return false;
   if (mode != 3) {
@@ -667,6 +701,10 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
       default: TD(3, 512); break;
     }
   } else {
+    if (tb == 1024) {
+      TD(0, 1024);
+      return true;
+    }
     switch (mode * 2 + (tb == 512 ? 1 : 0)) {
       case 0: TD(0, 256); break;
       case 1: TD(0, 512); break;
