@@ -9,6 +9,16 @@
 
 namespace moto {
 
+// packed FP32 FMA on (x, y) pairs: each half rounds exactly like fma.rn.f32
+__device__ __forceinline__ float2 ffma2v(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
 // ===========================================================================
 // Gram:  out[r][c] = X_r . Y_c
 // ===========================================================================
@@ -261,14 +271,6 @@ constexpr int kUpdSelf = 36;  // upper-triangle entries of an 8 x 8 Gram
 //               tangent planes of m when m is given.
 // ===========================================================================
 namespace {
-__device__ __forceinline__ float2 ffma2v(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;"
-      : "=l"(d)
-      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
-        "l"(*reinterpret_cast<unsigned long long*>(&c)));
-  return *reinterpret_cast<float2*>(&d);
-}
 
 // t = x P over the upper triangle: t[c] takes rows r = 0 .. c in order
 template <typename T>
@@ -604,11 +606,20 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    // every load of the site first (predicated, not a loop exit), so that
+    // they are all in flight together
+    T va[MOTO_MAX_K][3];
+#pragma unroll
+    for (int c = 0; c < MOTO_MAX_K; ++c) {
+      const T* v = V + (size_t)c * ldv;
+      va[c][0] = c < k ? __ldg(v + i) : (T)0;
+      va[c][1] = c < k ? __ldg(v + N + i) : (T)0;
+      va[c][2] = c < k ? __ldg(v + 2 * (size_t)N + i) : (T)0;
+    }
 #pragma unroll
     for (int c = 0; c < MOTO_MAX_K; ++c) {
       if (c >= k) break;
-      const T* v = V + (size_t)c * ldv;
-      T a0 = __ldg(v + i), a1 = __ldg(v + N + i), a2 = __ldg(v + 2 * (size_t)N + i);
+      T a0 = va[c][0], a1 = va[c][1], a2 = va[c][2];
       const T p = m0 * a0 + m1 * a1 + m2 * a2;
       a0 -= p * m0;
       a1 -= p * m1;
