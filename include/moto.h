@@ -62,6 +62,13 @@ enum {
   MOTO_SOLVER_LOBPCG = 1
 };
 
+/* Outer-layer optimiser (Results, "Bilayer MMF": "LBFGS or CG"). */
+enum {
+  MOTO_OPT_LBFGS = 0,  /* tangent-space L-BFGS two-loop, step cap theta_max, no line search */
+  MOTO_OPT_CG = 1      /* nonlinear CG, Polak-Ribiere+ with restarts, spectral step
+                          s.y / y.y of the last step (gamma0 without one), step cap */
+};
+
 #define MOTO_MAX_K 8        /* modes per solve */
 #define MOTO_MAX_BASIS 96   /* Krylov basis vectors (block * steps) */
 #define MOTO_MAX_MEM 8      /* L-BFGS pairs */
@@ -98,6 +105,10 @@ typedef struct {
   double eta_theta;   /* largest per-spin rotation of a descent seed, rad       (0.1) */
   int max_steps;      /* ascent step cap                                       (300) */
   int descent_max_steps; /* descent step cap per side                          (5000) */
+  int optimizer;      /* MOTO_OPT_*, used by ascent and descent                (LBFGS) */
+  int subspace;       /* 1: reflect the force in all k Ritz vectors,
+                         F_mmf = F - 2 V (V^T F) (the paper's subspace variant
+                         for k > 1, P_min = V V^T); 0: in v1 only              (0) */
 } moto_params;
 
 /* Fills *p with the defaults listed above. */
@@ -215,7 +226,8 @@ int moto_ascend(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V_d
 
 /* Two-sided descent (Results, "Deterministic bidirectional saddle descent";
  * Algorithm 1): seeds m_saddle +- eta v1 with eta = eta_theta / max_i |v1_i|
- * (retracted), each relaxed by L-BFGS on g until max_i |g_i| <= tau_F or
+ * (retracted), each relaxed by the outer optimiser (params.optimizer) on g
+ * until max_i |g_i| <= tau_F or
  * descent_max_steps.  Writes m_plus_dev, m_minus_dev (3N each) and
  * out_dev (6 doubles): [E+, Q+, E-, Q-, steps+, steps-] with E in double
  * arithmetic.  Synchronises the stream.  Returns MOTO_OK if both sides

@@ -25,7 +25,21 @@ downhill).  Readings where the paper gives no rule:
   Ritz values of the inner solve.
 * [R9] eta scales v1 so that the largest per-spin rotation of the seed is
   0.1 rad; "+" is the side along the sign-fixed v1 (R4); each side is relaxed by
-  the same L-BFGS on G = g to max_i |F_i| <= tau_F (at most 5000 steps).
+  the same optimiser on G = g to max_i |F_i| <= tau_F (at most 5000 steps).
+* [R15] Subspace variant (Results, "Bilayer MMF": for k > 1 the projector
+  v v^T is replaced by P_min = V V^T): F_mmf = F - 2 V (V^T F) over the k
+  orthonormal Ritz vectors; off by default (v1 only), the saddle test is
+  unchanged.
+* [R16] Nonlinear CG (the paper's alternative optimiser, Fig. 2g-h): the
+  Polak-Ribiere+ direction p = -G + beta P p_prev with
+  beta = max(0, G.(G - P G_prev) / |G_prev|^2) (Nocedal & Wright, eqs.
+  5.44-5.45), transport by projection as for L-BFGS, a restart p = -G when p
+  is not a descent direction for G.  No line search (R6): the step is
+  alpha p with the spectral length alpha = s.y / y.y of the last step
+  (s = P d_prev, y = G - P G_prev, kept when s.y > 1e-12 |s||y|, else gamma0;
+  Barzilai & Borwein 1988, the same scale L-BFGS starts from), capped at
+  theta_max per spin.  (A fixed alpha = gamma0 was tried first: on the
+  32 x 32 workload it did not reach a saddle in 300 steps.)
 """
 from __future__ import annotations
 
@@ -51,6 +65,8 @@ class MMFParams:
     max_steps: int = 300
     eta_theta: float = 0.1         # rad
     descent_max_steps: int = 5000
+    optimizer: str = "lbfgs"       # "lbfgs" | "cg" (R16)
+    subspace: bool = False         # reflect all k modes (R15) instead of v1
 
 
 def _dot(a, b) -> float:
@@ -117,6 +133,52 @@ class LBFGS:
         return d
 
 
+class CG:
+    """Tangent-space nonlinear CG, Polak-Ribiere+ with restarts and a spectral
+    step length (reading R16)."""
+
+    def __init__(self, gamma0: float, theta_max: float):
+        self.gamma0 = gamma0
+        self.theta_max = theta_max
+        self.p_prev = None
+        self.d_prev = None
+        self.G_prev = None
+
+    def reset(self):
+        self.p_prev = None
+
+    def direction(self, m: np.ndarray, G: np.ndarray) -> np.ndarray:
+        alpha = self.gamma0
+        if self.p_prev is None:
+            p = -G
+        else:
+            y = G - spin.project(m, self.G_prev)
+            s = spin.project(m, self.d_prev)
+            beta = max(0.0, _dot(G, y) / _dot(self.G_prev, self.G_prev))
+            p = -G + beta * spin.project(m, self.p_prev)
+            if _dot(p, G) >= 0.0:
+                p = -G
+            sy = _dot(s, y)
+            if sy > 1e-12 * math.sqrt(_dot(s, s) * _dot(y, y)):
+                alpha = sy / _dot(y, y)
+        d = alpha * p
+        tmax = max_torque(d)
+        if tmax > self.theta_max:
+            d = d * (self.theta_max / tmax)
+        self.p_prev = p
+        self.d_prev = d
+        self.G_prev = G
+        return d
+
+
+def make_optimizer(p: "MMFParams"):
+    if p.optimizer == "lbfgs":
+        return LBFGS(p.lbfgs_mem, p.gamma0, p.theta_max)
+    if p.optimizer == "cg":
+        return CG(p.gamma0, p.theta_max)
+    raise ValueError(p.optimizer)
+
+
 def min_mode(model, m, s, start, p: MMFParams):
     """Inner layer: (ritz values ascending, [v_1..v_k]) from warm start(s)."""
     if p.solver == "lanczos":
@@ -146,6 +208,15 @@ def reflected_force(F: np.ndarray, v1: np.ndarray) -> np.ndarray:
     return F - 2.0 * _dot(F, v1) * v1
 
 
+def reflected_force_subspace(F: np.ndarray, V) -> np.ndarray:
+    """F_mmf = F - 2 V (V^T F) for orthonormal V (Results, Bilayer MMF, the
+    subspace variant with P_min = V V^T)."""
+    out = F.copy()
+    for v in V:
+        out = out - 2.0 * _dot(F, v) * v
+    return out
+
+
 def saddle_test(fmax: float, lam, tau_F: float) -> bool:
     """|F_mmf| <= tau_F and lambda_1 < 0 < lambda_2 (Algorithm 1)."""
     return fmax <= tau_F and lam[0] < 0.0 < lam[1]
@@ -155,7 +226,7 @@ def ascend(model, m0: np.ndarray, start: list, p: MMFParams) -> AscentResult:
     """Bilayer MMF from m0; ``start`` holds the k seeded start vectors of the
     first inner solve (later solves warm-start from the previous modes)."""
     m = m0.copy()
-    opt = LBFGS(p.lbfgs_mem, p.gamma0, p.theta_max)
+    opt = make_optimizer(p)
     V = [x.copy() for x in start]
     trace = []
     converged = False
@@ -166,7 +237,7 @@ def ascend(model, m0: np.ndarray, start: list, p: MMFParams) -> AscentResult:
         lam, V = min_mode(model, m, s, V, p)
         v1 = V[0]
         F = -g
-        Fm = reflected_force(F, v1)
+        Fm = reflected_force_subspace(F, V[:p.k]) if p.subspace else reflected_force(F, v1)
         fmax = max_torque(Fm)
         trace.append(dict(E=spin.energy(model, m), fmax=fmax, lam1=float(lam[0]), lam2=float(lam[1])))
         if saddle_test(fmax, lam, p.tau_F):
@@ -190,9 +261,9 @@ class DescentResult:
 
 
 def relax(model, m0: np.ndarray, p: MMFParams):
-    """RelaxDownhill: L-BFGS on G = g until max_i |F_i| <= tau_F."""
+    """RelaxDownhill: the optimiser on G = g until max_i |F_i| <= tau_F."""
     m = m0.copy()
-    opt = LBFGS(p.lbfgs_mem, p.gamma0, p.theta_max)
+    opt = make_optimizer(p)
     converged = False
     step = 0
     for step in range(p.descent_max_steps + 1):

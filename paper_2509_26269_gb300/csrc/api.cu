@@ -130,10 +130,22 @@ void P_finish(moto_ctx* c, const T* m, T* V, size_t ldv, int k, int N, double* p
   launch_finish<T>(m, V, ldv, k, N, part, counter, scal, gate, mask, st);
 }
 template <typename T>
-void P_mmf_force(moto_ctx* c, const T* g, const T* v1, const double* dot, double reflect, T* G, int N, double* part,
-                 unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
-  PROF(kPkVec, (v1 ? 9.0 : 6.0) * N * sizeof(T));
-  launch_mmf_force<T>(g, v1, dot, reflect, G, N, part, counter, fmax_out, gate, mask, st);
+void P_mmf_force(moto_ctx* c, const T* g, const T* V, size_t ldv, int nv, const double* dots, T* G, int N,
+                 double* part, unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, (6.0 + 3.0 * nv) * N * sizeof(T));
+  launch_mmf_force<T>(g, V, ldv, nv, dots, G, N, part, counter, fmax_out, gate, mask, st);
+}
+template <typename T>
+void P_cg_direction(moto_ctx* c, const T* m, const T* G, T* p, int N, const double* cg, double theta_max,
+                    double* part, unsigned* counter, DevState* dst, const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, 12.0 * N * sizeof(T));
+  launch_cg_direction<T>(m, G, p, N, cg, theta_max, part, counter, dst, gate, mask, st);
+}
+template <typename T>
+void P_cg_retract(moto_ctx* c, T* m, const T* G, T* p, T* d, const DevState* dst, int N, const int* gate, int mask,
+                  cudaStream_t st) {
+  PROF(kPkVec, 18.0 * N * sizeof(T));
+  launch_cg_retract<T>(m, G, p, d, dst, N, gate, mask, st);
 }
 template <typename T>
 void P_lbfgs_pair(moto_ctx* c, const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
@@ -234,6 +246,7 @@ SMALL_WRAP(lob_check)
 SMALL_WRAP(diag)
 SMALL_WRAP(lbfgs_solve)
 SMALL_WRAP(saddle_test)
+SMALL_WRAP(cg_coeffs)
 SMALL_WRAP(arnoldi_diag)
 #undef SMALL_WRAP
 void P_tridiag_eig(moto_ctx* c, const double* T, int ldT, int band, double* theta, double* Y, int k, DevState* dst,
@@ -268,7 +281,9 @@ constexpr size_t kLobG = kTmp + 8;                                 // 3K x 3K (L
 constexpr size_t kLobM = kLobG + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 3K
 constexpr size_t kLobC = kLobM + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 2K coefficient blocks
 constexpr size_t kLobAux = kLobC + 6 * MOTO_MAX_K * MOTO_MAX_K;    // 64 aux
-constexpr size_t kDsmSize = kLobAux + 64 * MOTO_MAX_K;
+constexpr size_t kMmfDots = kLobAux + 64 * MOTO_MAX_K;             // MAX_K: g . V_c (subspace force)
+constexpr size_t kCg = kMmfDots + MOTO_MAX_K;                      // 12: CG dots and coefficients
+constexpr size_t kDsmSize = kCg + 12;
 
 constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
 
@@ -342,6 +357,8 @@ int check_params(const moto_params* p) {
   if (!(p->theta_max > 0.0) || !(p->gamma0 > 0.0) || !(p->tau_F >= 0.0) || !(p->eta_theta > 0.0))
     return MOTO_ERR_ARG;
   if (p->max_steps < 0 || p->descent_max_steps < 0) return MOTO_ERR_ARG;
+  if (p->optimizer != MOTO_OPT_LBFGS && p->optimizer != MOTO_OPT_CG) return MOTO_ERR_ARG;
+  if (p->subspace != 0 && p->subspace != 1) return MOTO_ERR_ARG;
   return MOTO_OK;
 }
 
@@ -539,6 +556,8 @@ void moto_default_params(moto_params* p) {
   p->eta_theta = 0.1;
   p->max_steps = 300;
   p->descent_max_steps = 5000;
+  p->optimizer = MOTO_OPT_LBFGS;
+  p->subspace = 0;
 }
 
 const char* moto_status_string(int code) {
@@ -773,13 +792,31 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
   if (ascent) {
     const int nv = std::max(p->k, p->solver == MOTO_SOLVER_LANCZOS ? p->block : p->k);
     lowest_modes_impl<T>(c, m, s, p, V, n3, V, n3, nv, lam, st);
-    P_gram<T>(c, g, ld, 1, V, n3, 1, n3, &c->st->dot, c->part, c->counter, gate, md, st);
-    P_mmf_force<T>(c, g, V, &c->st->dot, 1.0, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
+    // G = -F_mmf = g - 2 V (V^T g) over v1 or the k lowest Ritz vectors
+    const int nr = p->subspace ? p->k : 1;
+    P_gram<T>(c, g, ld, 1, V, n3, nr, n3, D + kMmfDots, c->part, c->counter, gate, md, st);
+    P_mmf_force<T>(c, g, V, n3, nr, D + kMmfDots, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
   } else {
-    P_mmf_force<T>(c, g, nullptr, &c->st->dot, 0.0, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
+    P_mmf_force<T>(c, g, nullptr, n3, 0, D + kMmfDots, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
   }
-  P_saddle_test(c, D + kEG, D + kFmax, lam, p->tau_F, out6, status, c->st, ascent ? 1 : 0, st);
+  P_saddle_test(c, D + kEG, D + kFmax, lam, D + kMmfDots, p->tau_F, out6, status, c->st, ascent ? 1 : 0, st);
   if (!update) return;
+  if (p->optimizer == MOTO_OPT_CG) {
+    // nonlinear CG: the pair s = P d_prev, y = G - P G_prev (staging fields),
+    // the pair's Gram, G.G and y.G, beta and the spectral step, then the
+    // direction, the restart test and the capped step; p lives in the last
+    // ring field (the pair kernel writes ring slot 0 only while CG runs)
+    T* pdir = ring + (size_t)(2 * R - 1) * ld;
+    P_lbfgs_pair<T>(c, m, d, Gprev, Gcur, ring, ld, stage, c->st, N, gate, md, st);
+    P_gram<T>(c, stage, ld, 2, stage, ld, 2, n3, D + kCg, c->part, c->counter, gate, md, st);
+    P_gram<T>(c, Gcur, ld, 1, Gcur, ld, 1, n3, D + kCg + 4, c->part, c->counter, gate, md, st);
+    P_gram<T>(c, stage + ld, ld, 1, Gcur, ld, 1, n3, D + kCg + 5, c->part, c->counter, gate, md, st);
+    P_cg_coeffs(c, D + kCg, p->gamma0, c->st, st);
+    P_cg_direction<T>(c, m, Gcur, pdir, N, D + kCg, p->theta_max, c->part, c->counter, c->st, gate, md, st);
+    P_cg_retract<T>(c, m, Gcur, pdir, d, c->st, N, gate, md, st);
+    cudaMemcpyAsync(Gprev, Gcur, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    return;
+  }
   P_lbfgs_pair<T>(c, m, d, Gprev, Gcur, ring, ld, stage, c->st, N, gate, md, st);
   P_gram<T>(c, ring, ld, nb, stage, ld, 2, n3, D + kLbNew, c->part, c->counter, gate, md, st);
   P_gram<T>(c, ring, ld, nb, Gcur, ld, 1, n3, D + kLbNew + 2 * nb, c->part, c->counter, gate, md, st);

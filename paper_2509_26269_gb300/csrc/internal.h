@@ -136,9 +136,24 @@ void launch_lob_check(const double* Gw, int k, double tol, const double* theta, 
 void launch_diag(const double* src, int k, int mode, double* out, const DevState* st, int mask, cudaStream_t s);
 
 // ---- L-BFGS / MMF ----
+// G = g - 2 sum_c dots[c] V_c over nv fields of V (nv = 0: G = g), and
+// fmax_out = max_i |G_i|
 template <typename T>
-void launch_mmf_force(const T* g, const T* v1, const double* dot, double reflect, T* G, int N, double* part,
+void launch_mmf_force(const T* g, const T* V, size_t ldv, int nv, const double* dots, T* G, int N, double* part,
                       unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st);
+// Nonlinear CG (Polak-Ribiere+).  cg (doubles): [0..3] the Gram of the pair
+// (s.s, s.y, y.s, y.y), [4] G.G, [5] y.G, [6] |G_prev|^2 (kept), [7] beta,
+// [8] step length.  cg_coeffs forms beta and the length and sets
+// lb_have_prev; cg_direction writes p = -G + beta P p (p: the previous
+// direction on entry) and decides restart (pad[2]) and the capped scale;
+// cg_retract takes d = scale * (restart ? -G : p) and retracts.
+void launch_cg_coeffs(double* cg, double gamma0, DevState* dst, cudaStream_t st);
+template <typename T>
+void launch_cg_direction(const T* m, const T* G, T* p, int N, const double* cg, double theta_max, double* part,
+                         unsigned* counter, DevState* dst, const int* gate, int mask, cudaStream_t st);
+template <typename T>
+void launch_cg_retract(T* m, const T* G, T* p, T* d, const DevState* dst, int N, const int* gate, int mask,
+                       cudaStream_t st);
 template <typename T>
 void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
                        const DevState* dst, int N, const int* gate, int mask, cudaStream_t st);
@@ -153,7 +168,7 @@ void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int
 template <typename T>
 void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign, T* out, int N, double* part,
                          unsigned* counter, double* scal, cudaStream_t st);
-void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, double tau_F, double* out6,
-                        int* status_out, DevState* dst, int ascent, cudaStream_t st);
+void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
+                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, cudaStream_t st);
 
 }  // namespace moto

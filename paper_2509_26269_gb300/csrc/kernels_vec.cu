@@ -1179,20 +1179,24 @@ void launch_diag(const double* src, int k, int mode, double* out, const DevState
 // ===========================================================================
 // G = g - 2 reflect (g . v1) v1  (= -F_mmf for reflect = 1, F = -g);  max_i |G_i|.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict__ g, const T* __restrict__ v1,
-                                                             const double* dot, double reflect, T* G, int N,
+__global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict__ g, const T* __restrict__ V,
+                                                             size_t ldv, int nv, const double* dots, T* G, int N,
                                                              double* part, unsigned* counter, double* fmax_out,
                                                              const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
-  const T a = v1 ? (T)(2.0 * reflect * dot[0]) : (T)0;
+  __shared__ T a[MOTO_MAX_K];
+  if (threadIdx.x < MOTO_MAX_K) a[threadIdx.x] = (int)threadIdx.x < nv ? (T)(2.0 * dots[threadIdx.x]) : (T)0;
+  __syncthreads();
   double mx = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     T r[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t e = (size_t)c * N + i;
-      r[c] = g[e] - (v1 ? a * v1[e] : (T)0);
-      G[e] = r[c];
+      T v = g[e];
+      for (int q = 0; q < nv; ++q) v -= a[q] * V[(size_t)q * ldv + e];
+      r[c] = v;
+      G[e] = v;
     }
     mx = fmax(mx, (double)(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]));
   }
@@ -1210,10 +1214,101 @@ __global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict
 }
 
 template <typename T>
-void launch_mmf_force(const T* g, const T* v1, const double* dot, double reflect, T* G, int N, double* part,
+void launch_mmf_force(const T* g, const T* V, size_t ldv, int nv, const double* dots, T* G, int N, double* part,
                       unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
-  mmf_force_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(g, v1, dot, reflect, G, N, part, counter, fmax_out,
-                                                           gate, mask);
+  mmf_force_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(g, nv > 0 ? V : nullptr, ldv, nv, dots, G, N, part,
+                                                           counter, fmax_out, gate, mask);
+}
+
+// ---- nonlinear CG (Polak-Ribiere+, spectral step; see internal.h) ----
+__global__ void cg_coeffs_kernel(double* cg, double gamma0, DevState* dst) {
+  if (threadIdx.x != 0 || (dst->gate & kGateDone)) return;
+  double beta = 0.0, alpha = gamma0;
+  if (dst->lb_have_prev) {
+    beta = cg[6] > 0.0 ? fmax(0.0, cg[5] / cg[6]) : 0.0;  // G.(G - P G_prev) = G.y
+    const double ss = cg[0], sy = cg[1], yy = cg[3];
+    if (sy > 1e-12 * sqrt(ss * yy)) alpha = sy / yy;
+  }
+  cg[7] = beta;
+  cg[8] = alpha;
+  cg[6] = cg[4];  // |G|^2 becomes |G_prev|^2 of the next step
+  dst->lb_have_prev = 1;
+}
+
+void launch_cg_coeffs(double* cg, double gamma0, DevState* dst, cudaStream_t st) {
+  cg_coeffs_kernel<<<1, 32, 0, st>>>(cg, gamma0, dst);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) cg_direction_kernel(const T* __restrict__ m, const T* __restrict__ G,
+                                                                T* p, int N, const double* cg, double theta_max,
+                                                                double* part, unsigned* counter, DevState* dst,
+                                                                const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  const double beta_d = cg[7];
+  const T beta = (T)beta_d;
+  double v[3] = {0.0, 0.0, 0.0};  // p.G, max |p_i|^2, max |G_i|^2
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T gv[3], pv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gv[c] = G[(size_t)c * N + i];
+    if (beta_d != 0.0) {
+      const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+      T q[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[c] = p[(size_t)c * N + i];
+      const T pm = m0 * q[0] + m1 * q[1] + m2 * q[2];
+      const T mm[3] = {m0, m1, m2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pv[c] = -gv[c] + beta * (q[c] - pm * mm[c]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) pv[c] = -gv[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[(size_t)c * N + i] = pv[c];
+    v[0] += (double)(pv[0] * gv[0] + pv[1] * gv[1] + pv[2] * gv[2]);
+    v[1] = fmax(v[1], (double)(pv[0] * pv[0] + pv[1] * pv[1] + pv[2] * pv[2]));
+    v[2] = fmax(v[2], (double)(gv[0] * gv[0] + gv[1] * gv[1] + gv[2] * gv[2]));
+  }
+  __shared__ double red[3 * (kThreads / 32)];
+  double s1[1] = {v[0]};
+  block_sum<1>(s1, red);
+  const double m1 = block_max(v[1], red);
+  const double m2 = block_max(v[2], red);
+  if (threadIdx.x == 0) {
+    part[(size_t)blockIdx.x * 3 + 0] = s1[0];
+    part[(size_t)blockIdx.x * 3 + 1] = m1;
+    part[(size_t)blockIdx.x * 3 + 2] = m2;
+  }
+  if (!grid_last_block(counter)) return;
+  __shared__ double tot[1];
+  grid_sum_entries(part, gridDim.x, 3, red);  // red[0] is the p.G total (maxima below)
+  __syncthreads();
+  if (threadIdx.x == 0) tot[0] = red[0];
+  __syncthreads();
+  double a1 = 0.0, a2 = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    a1 = fmax(a1, __ldcg(part + (size_t)k * 3 + 1));
+    a2 = fmax(a2, __ldcg(part + (size_t)k * 3 + 2));
+  }
+  a1 = block_max(a1, red);
+  a2 = block_max(a2, red);
+  if (threadIdx.x == 0) {
+    const bool restart = !(tot[0] < 0.0);  // p is not a descent direction for G
+    const double alpha = cg[8];
+    const double t = sqrt(restart ? a2 : a1);
+    dst->pad[2] = restart ? 1 : 0;
+    dst->scale = (alpha * t > theta_max) ? theta_max / t : alpha;
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+void launch_cg_direction(const T* m, const T* G, T* p, int N, const double* cg, double theta_max, double* part,
+                         unsigned* counter, DevState* dst, const int* gate, int mask, cudaStream_t st) {
+  cg_direction_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, G, p, N, cg, theta_max, part, counter, dst, gate,
+                                                              mask);
 }
 
 // New pair at the current point: s = P d_prev, y = G - P G_prev, written into
@@ -1450,6 +1545,39 @@ void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int
   retract_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, d, dst, N, gate, mask);
 }
 
+template <typename T>
+__global__ void cg_retract_kernel(T* m, const T* __restrict__ G, T* p, T* d, const DevState* dst, int N,
+                                  const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  const bool restart = dst->pad[2] != 0;
+  const T sc = (T)dst->scale;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T dv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t e = (size_t)c * N + i;
+      T dir = p[e];
+      if (restart) {
+        dir = -G[e];
+        p[e] = dir;
+      }
+      dv[c] = dir * sc;
+      d[e] = dv[c];
+    }
+    T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
+    rodrigues(m0, m1, m2, dv[0], dv[1], dv[2]);
+    m[i] = m0;
+    m[N + i] = m1;
+    m[2 * (size_t)N + i] = m2;
+  }
+}
+
+template <typename T>
+void launch_cg_retract(T* m, const T* G, T* p, T* d, const DevState* dst, int N, const int* gate, int mask,
+                       cudaStream_t st) {
+  cg_retract_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, G, p, d, dst, N, gate, mask);
+}
+
 // Descent seed: out = Rodrigues(m, sign * eta * v1), eta = eta_theta / max|v1_i|.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) vmax_kernel(const T* v, int N, double* part, unsigned* counter,
@@ -1493,8 +1621,8 @@ void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign,
 }
 
 // Saddle / minimum test and the per-step output vector.
-__global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, double tau_F,
-                                   double* out6, int* status_out, DevState* dst, int ascent) {
+__global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
+                                   double tau_F, double* out6, int* status_out, DevState* dst, int ascent) {
   if (threadIdx.x != 0) return;
   if (dst->gate & kGateDone) {
     if (status_out) *status_out = 1;
@@ -1510,7 +1638,7 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
       out6[2] = lam[0];
       out6[3] = lam[1];
       out6[4] = gmax;
-      out6[5] = dst->dot;
+      out6[5] = -gdot[0];  // F . v1 = -g . v1
     }
   } else {
     conv = gmax <= tau_F;
@@ -1529,9 +1657,9 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
   if (status_out) *status_out = conv ? 1 : 0;
 }
 
-void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, double tau_F, double* out6,
-                        int* status_out, DevState* dst, int ascent, cudaStream_t st) {
-  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, tau_F, out6, status_out, dst, ascent);
+void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
+                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, cudaStream_t st) {
+  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, out6, status_out, dst, ascent);
 }
 
 #define INST(T)                                                                                                   \
@@ -1545,8 +1673,11 @@ void launch_saddle_test(const double* eg_out, const double* fmax, const double* 
                                   cudaStream_t);                                                                  \
   template void launch_finish<T>(const T*, T*, size_t, int, int, double*, unsigned*, double*, const int*, int,    \
                                  cudaStream_t);                                                                   \
-  template void launch_mmf_force<T>(const T*, const T*, const double*, double, T*, int, double*, unsigned*,       \
+  template void launch_mmf_force<T>(const T*, const T*, size_t, int, const double*, T*, int, double*, unsigned*,  \
                                     double*, const int*, int, cudaStream_t);                                      \
+  template void launch_cg_direction<T>(const T*, const T*, T*, int, const double*, double, double*, unsigned*,   \
+                                       DevState*, const int*, int, cudaStream_t);                                 \
+  template void launch_cg_retract<T>(T*, const T*, T*, T*, const DevState*, int, const int*, int, cudaStream_t);  \
   template void launch_lbfgs_pair<T>(const T*, const T*, const T*, const T*, T*, size_t, T*, const DevState*,     \
                                      int, const int*, int, cudaStream_t);                                         \
   template void launch_lbfgs_direction<T>(const T*, size_t, int, const double*, const T*, T*, int, double,        \
