@@ -288,6 +288,32 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": int(pin_m.numel() * 4),
            "d2h_bytes_per_step": int(pin_m.numel() * 4 + res_host.numel() * 8)}
 
+    trace = {"E": float(out[0]), "fmax": float(out[1]), "lam1": float(out[2]), "lam2": float(out[3]),
+             "Q": float(Q[0])}
+
+    # ---- outer-layer variants on the same workload (device-resident) ---------
+    # nonlinear CG instead of L-BFGS, and the subspace reflection over all k
+    # modes: a few steps each from the same start, CUDA-event timed
+    variants = {}
+    for vname, over in (("cg", {"optimizer": mo.MOTO_OPT_CG}), ("subspace_k8", {"subspace": 1})):
+        pv = mo.make_params(**{f: getattr(params, f) for f, _ in params._fields_})
+        for f, v in over.items():
+            setattr(pv, f, v)
+        m.copy_(m0)
+        V.copy_(V0)
+        mo.moto_lbfgs_reset(ctx.handle)
+        mo.moto_mmf_step(ctx.handle, m, pv, V, out, status)
+        torch.cuda.synchronize()
+        nv_steps = 3
+        e0.record()
+        for _ in range(nv_steps):
+            mo.moto_mmf_step(ctx.handle, m, pv, V, out, status)
+        e1.record()
+        torch.cuda.synchronize()
+        vms = e0.elapsed_time(e1) / nv_steps
+        variants[vname] = {"ms_per_step": vms, "value": L * L * HVP_PER_STEP / (vms * 1e-3) / 1e9, "unit": UNIT,
+                           "steps": nv_steps}
+
     line = None
     if rank == 0:
         cpu = cpu_baseline(m_host) if (world == 1 and not args.no_cpu_baseline) else None
@@ -304,11 +330,11 @@ def run_ours(args, rank, world, local):
             "hvp_gbs": hvp_gbs,
             "hvp_gspin_s": (L * L * HVP_PER_STEP) / (hvp[1] * 1e-3) / 1e9 if hvp[1] else 0.0,
             "e2e": e2e,
+            "variants": variants,
             "gpu_launches": launches * args.steps,
             "clocks": ck,
             "cpu_baseline": cpu,
-            "trace": {"E": float(out[0]), "fmax": float(out[1]), "lam1": float(out[2]), "lam2": float(out[3]),
-                      "Q": float(Q[0])},
+            "trace": trace,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
