@@ -314,6 +314,35 @@ def run_ours(args, rank, world, local):
         variants[vname] = {"ms_per_step": vms, "value": L * L * HVP_PER_STEP / (vms * 1e-3) / 1e9, "unit": UNIT,
                            "steps": nv_steps}
 
+    # ---- explorer front-end: a population of 24 masked perturbations of the
+    # state (disk mask of radius L/4 around the centre) and its pairwise L1
+    # distances, CUDA-event timed; bytes are the fields read and written
+    n_pop = 24
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4000 + walker)
+    delta = 0.2 * torch.randn((n_pop, 3, L, L), generator=gen, device="cuda", dtype=torch.float32)
+    i2, i1 = torch.meshgrid(torch.arange(L, device="cuda"), torch.arange(L, device="cuda"), indexing="ij")
+    mask = (((i1 - L / 2) ** 2 + (i2 - L / 2) ** 2) <= (L / 4) ** 2).to(torch.uint8).contiguous()
+    pop = torch.empty((n_pop, 3, L, L), device="cuda", dtype=torch.float32)
+    Dpop = torch.empty((n_pop, n_pop), device="cuda", dtype=torch.float64)
+    n3 = 3 * L * L
+    explorer = {}
+    for ename, call, nbytes in (
+            ("perturb", lambda: mo.moto_perturb(ctx.handle, m, mask, delta, n3, n_pop, pop, n3),
+             (3 + 2 * 3 * n_pop) * L * L * 4 + L * L),
+            ("pairwise_l1", lambda: mo.moto_pairwise_l1(ctx.handle, pop, n3, n_pop, Dpop),
+             n_pop * n3 * 4)):
+        call()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(3):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1) / 3
+        explorer[ename] = {"ms": ems, "GBps": nbytes / (ems * 1e-3) / 1e9, "population": n_pop}
+    del delta, pop
+
     line = None
     if rank == 0:
         cpu = cpu_baseline(m_host) if (world == 1 and not args.no_cpu_baseline) else None
@@ -331,6 +360,7 @@ def run_ours(args, rank, world, local):
             "hvp_gspin_s": (L * L * HVP_PER_STEP) / (hvp[1] * 1e-3) / 1e9 if hvp[1] else 0.0,
             "e2e": e2e,
             "variants": variants,
+            "explorer": explorer,
             "gpu_launches": launches * args.steps,
             "clocks": ck,
             "cpu_baseline": cpu,

@@ -72,6 +72,7 @@ enum {
 #define MOTO_MAX_K 8        /* modes per solve */
 #define MOTO_MAX_BASIS 96   /* Krylov basis vectors (block * steps) */
 #define MOTO_MAX_MEM 8      /* L-BFGS pairs */
+#define MOTO_MAX_POP 64     /* candidates of one pairwise-distance call */
 
 /* Spin Hamiltonian of Eq. param-hamiltonian (Methods, "Spin Hamiltonian and
  * manifold gradient"), read with ordered-pair sums (each bond counted twice):
@@ -186,6 +187,30 @@ int moto_lowest_modes(moto_ctx* ctx, const void* m_dev, const void* s_dev,
  * Berg-Luescher solid angle (up triangles (i, i+a1, i+a2), down triangles
  * (i+a1, i+a1+a2, i+a2)).  Q_dev: 1 double. */
 int moto_topo_charge(moto_ctx* ctx, const void* m_dev, double* Q_dev, void* stream);
+
+/* Masked perturbations of a reference configuration (Results,
+ * "Multi-objective initial-configuration explorer": x = x0 + P_Omega delta,
+ * followed by the spin-tangent retraction):
+ *   out_j = R_x0(P_Omega P_x0 delta_j),  j < count,
+ * i.e. on every active site the tangent part of delta_j at x0 rotates the spin
+ * (Rodrigues), and inactive sites keep x0 exactly.
+ *   x0_dev: unit spins (3N);  mask_dev: N bytes, nonzero = active (NULL: all);
+ *   delta_dev: count fields at element stride ld_delta (>= 3N when count > 1),
+ *   the caller's random draws;  out_dev: count fields at stride ld_out.
+ * count <= 65535.  Enqueues only. */
+int moto_perturb(moto_ctx* ctx, const void* x0_dev, const unsigned char* mask_dev, const void* delta_dev,
+                 size_t ld_delta, int count, void* out_dev, size_t ld_out, void* stream);
+
+/* Pairwise L1 distances of a population (the explorer's diversity objective;
+ * the population figures of Fig. 2e-f are its pair sum and its smallest
+ * off-diagonal entry):
+ *   D[a*count + b] = sum over the 3N elements e of |X_a[e] - X_b[e]|,
+ * 2 <= count <= MOTO_MAX_POP fields of X_dev at stride ldx >= 3N;
+ * D_dev: count x count doubles (symmetric, zero diagonal).  Sums in FP64 in a
+ * fixed order (FP32 fields: FP32 partial sums over a few hundred elements).
+ * Uses the context's reduction scratch: calls on one context must not overlap
+ * on the device.  Enqueues only. */
+int moto_pairwise_l1(moto_ctx* ctx, const void* X_dev, size_t ldx, int count, double* D_dev, void* stream);
 
 /* Skinny Gram product out[r * ny + c] = X_r . Y_c over the 3N elements of
  * nx <= MOTO_MAX_BASIS fields X_r (at X_dev + r * ldx) and ny <= MOTO_MAX_K

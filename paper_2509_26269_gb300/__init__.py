@@ -21,6 +21,7 @@ MOTO_ERR_ARG, MOTO_ERR_CUDA, MOTO_ERR_NUMERIC = -1, -2, -3
 MOTO_ERR_NONFINITE, MOTO_ERR_TIMEOUT, MOTO_ERR_NOMEM = -4, -5, -6
 MOTO_SOLVER_LANCZOS, MOTO_SOLVER_LOBPCG = 0, 1
 MOTO_OPT_LBFGS, MOTO_OPT_CG = 0, 1
+MOTO_MAX_POP = 64
 MOTO_MAX_K, MOTO_MAX_BASIS, MOTO_MAX_MEM = 8, 96, 8
 
 
@@ -78,6 +79,8 @@ def _load():
         "moto_profile_begin": (I, [P, I]),
         "moto_energy_grad_noalloc": (I, [ctypes.POINTER(moto_model), I, P, P, P, P, P]),
         "moto_gram": (I, [P, P, Z, I, P, Z, I, P, P]),
+        "moto_perturb": (I, [P, P, P, P, Z, I, P, Z, P]),
+        "moto_pairwise_l1": (I, [P, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
         "moto_batch_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params),
                                   ctypes.POINTER(moto_walker), I, I, ctypes.POINTER(P)]),
@@ -98,6 +101,7 @@ EXPORTED = (
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
+    "moto_perturb", "moto_pairwise_l1",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
@@ -203,6 +207,16 @@ def moto_lowest_modes(ctx, m, s, params, v0, V, lam, info=None, stream=None):
 def moto_gram(ctx, X, ldx, nx, Y, ldy, ny, out, stream=None):
     _check(_lib.moto_gram(ctx, _ptr(X), int(ldx), int(nx), _ptr(Y), int(ldy), int(ny), _ptr(out),
                           _stream(stream)), "moto_gram")
+
+
+def moto_perturb(ctx, x0, mask, delta, ld_delta, count, out, ld_out, stream=None):
+    _check(_lib.moto_perturb(ctx, _ptr(x0), _ptr(mask), _ptr(delta), int(ld_delta), int(count), _ptr(out),
+                             int(ld_out), _stream(stream)), "moto_perturb")
+
+
+def moto_pairwise_l1(ctx, X, ldx, count, D, stream=None):
+    _check(_lib.moto_pairwise_l1(ctx, _ptr(X), int(ldx), int(count), _ptr(D), _stream(stream)),
+           "moto_pairwise_l1")
 
 
 def moto_topo_charge(ctx, m, Q, stream=None):

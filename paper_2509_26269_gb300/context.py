@@ -9,7 +9,7 @@ import torch
 from . import (MOTO_F32, MOTO_F64, MOTO_MAX_BASIS, make_model, make_params, moto_ascend, moto_batch_ascend,
                moto_batch_create, moto_batch_descend, moto_batch_destroy, moto_create, moto_descend, moto_destroy,
                moto_energy, moto_energy_grad, moto_hvp, moto_lbfgs_reset, moto_lowest_modes, moto_mmf_step,
-               moto_topo_charge, moto_workspace_bytes)
+               moto_pairwise_l1, moto_perturb, moto_topo_charge, moto_workspace_bytes)
 
 
 class Context:
@@ -78,6 +78,22 @@ class Context:
         Q = torch.empty(1, dtype=torch.float64, device=self.device)
         moto_topo_charge(self.handle, m, Q)
         return Q
+
+    def perturb(self, x0, delta, mask=None):
+        """Masked perturbations R_x0(P_mask P_x0 delta_j) of x0 for a stack
+        delta (count, 3, L2, L1); mask: (L2, L1) uint8 or None (all sites)."""
+        count = delta.shape[0]
+        out = self.field(count)
+        n3 = 3 * self.N
+        moto_perturb(self.handle, x0, mask, delta, n3, count, out, n3)
+        return out
+
+    def pairwise_l1(self, X):
+        """count x count L1 distances of a stack X (count, 3, L2, L1)."""
+        count = X.shape[0]
+        D = torch.empty((count, count), dtype=torch.float64, device=self.device)
+        moto_pairwise_l1(self.handle, X, 3 * self.N, count, D)
+        return D
 
     def reset(self):
         moto_lbfgs_reset(self.handle)

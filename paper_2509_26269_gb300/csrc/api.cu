@@ -1025,6 +1025,38 @@ int moto_profile_end(moto_ctx* c, int nkinds, int* launches, double* ms, double*
 }  // extern "C"
 
 // ============================================================================
+// Explorer front-end
+// ============================================================================
+extern "C" int moto_perturb(moto_ctx* c, const void* x0, const unsigned char* mask, const void* delta,
+                            size_t ld_delta, int count, void* out, size_t ld_out, void* stream) {
+  if (!c || !x0 || !delta || !out || count < 0) return MOTO_ERR_ARG;
+  if (count == 0) return MOTO_OK;
+  if ((count > 1 && (ld_delta < c->n3 || ld_out < c->n3)) || count > 65535) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  if (c->dtype == MOTO_F32)
+    launch_perturb<float>((const float*)x0, mask, (const float*)delta, ld_delta, count, (float*)out, ld_out, c->N,
+                          st);
+  else
+    launch_perturb<double>((const double*)x0, mask, (const double*)delta, ld_delta, count, (double*)out, ld_out,
+                           c->N, st);
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+extern "C" int moto_pairwise_l1(moto_ctx* c, const void* X, size_t ldx, int count, double* D, void* stream) {
+  if (!c || !X || !D || count < 2 || count > MOTO_MAX_POP || ldx < c->n3) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  bool ok;
+  if (c->dtype == MOTO_F32)
+    ok = launch_pairwise_l1<float>((const float*)X, ldx, count, c->n3, c->part, c->part_len, c->counter, D, st);
+  else
+    ok = launch_pairwise_l1<double>((const double*)X, ldx, count, c->n3, c->part, c->part_len, c->counter, D, st);
+  if (!ok) return MOTO_ERR_ARG;
+  CK(cudaGetLastError());
+  return MOTO_OK;
+}
+
+// ============================================================================
 // Gram utility
 // ============================================================================
 extern "C" int moto_gram(moto_ctx* c, const void* X, size_t ldx, int nx, const void* Y, size_t ldy, int ny,

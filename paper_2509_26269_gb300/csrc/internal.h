@@ -168,6 +168,17 @@ void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int
 template <typename T>
 void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign, T* out, int N, double* part,
                          unsigned* counter, double* scal, cudaStream_t st);
+// ---- explorer front-end (kernels_explorer.cu) ----
+// out_j = R_x0(P_mask P_x0 delta_j), j < count (mask: N bytes, NULL = all)
+template <typename T>
+void launch_perturb(const T* x0, const unsigned char* mask, const T* delta, size_t ldd, int count, T* out,
+                    size_t ldo, int N, cudaStream_t st);
+// D (P x P) = pairwise L1 distances of P <= MOTO_MAX_POP fields of n
+// elements; false (nothing launched) when P or the scratch is out of range
+template <typename T>
+bool launch_pairwise_l1(const T* X, size_t ldx, int P, size_t n, double* part, size_t part_cap, unsigned* counter,
+                        double* D, cudaStream_t st);
+
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
                         double tau_F, double* out6, int* status_out, DevState* dst, int ascent, cudaStream_t st);
 
