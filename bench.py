@@ -343,6 +343,22 @@ def run_ours(args, rank, world, local):
         explorer[ename] = {"ms": ems, "GBps": nbytes / (ems * 1e-3) / 1e9, "population": n_pop}
     del delta, pop
 
+    # ---- dynamic certifier: LLG descent steps (Heun: two gradients each) from
+    # the two seeds of the current state and mode, 20 steps per side
+    pl = mo.make_params(**{f: getattr(params, f) for f, _ in params._fields_})
+    pl.descent, pl.llg_time, pl.llg_dt, pl.tau_F = mo.MOTO_DESCENT_LLG, 0.2, 0.01, 1e-30
+    mp_, mm_ = torch.empty_like(m), torch.empty_like(m)
+    dout = torch.empty(6, dtype=torch.float64, device="cuda")
+    v1 = V[0].contiguous()
+    e0.record()
+    mo.moto_descend(ctx.handle, m, v1, pl, mp_, mm_, dout)
+    e1.record()
+    torch.cuda.synchronize()
+    llg_steps = int(dout[4].item()) + int(dout[5].item())
+    llg = {"ms_per_step": e0.elapsed_time(e1) / max(llg_steps, 1), "steps": llg_steps,
+           "note": "one Heun step = two energy/gradient stencils + predictor + corrector; includes the seeds, "
+                   "the end energies and charges and two host reads of the status word"}
+
     line = None
     if rank == 0:
         cpu = cpu_baseline(m_host) if (world == 1 and not args.no_cpu_baseline) else None
@@ -361,6 +377,7 @@ def run_ours(args, rank, world, local):
             "e2e": e2e,
             "variants": variants,
             "explorer": explorer,
+            "llg_descent": llg,
             "gpu_launches": launches * args.steps,
             "clocks": ck,
             "cpu_baseline": cpu,

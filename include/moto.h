@@ -62,6 +62,13 @@ enum {
   MOTO_SOLVER_LOBPCG = 1
 };
 
+/* Relaxation of the two-sided descent (Supplementary Note 1 (iii): "a
+ * deterministic optimizer (e.g., L-BFGS/CG) or dynamic simulator"). */
+enum {
+  MOTO_DESCENT_OPT = 0,  /* the outer optimiser (params.optimizer) on g */
+  MOTO_DESCENT_LLG = 1   /* damped spin dynamics (Landau-Lifshitz-Gilbert, Heun) */
+};
+
 /* Outer-layer optimiser (Results, "Bilayer MMF": "LBFGS or CG"). */
 enum {
   MOTO_OPT_LBFGS = 0,  /* tangent-space L-BFGS two-loop, step cap theta_max, no line search */
@@ -110,6 +117,10 @@ typedef struct {
   int subspace;       /* 1: reflect the force in all k Ritz vectors,
                          F_mmf = F - 2 V (V^T F) (the paper's subspace variant
                          for k > 1, P_min = V V^T); 0: in v1 only              (0) */
+  int descent;        /* MOTO_DESCENT_*                                        (OPT) */
+  double llg_alpha;   /* Gilbert damping of the LLG descent                    (1.0) */
+  double llg_dt;      /* LLG time step, hbar/meV (0.6582 ps)                   (0.01) */
+  double llg_time;    /* LLG duration per side, hbar/meV            (75.96 = 50 ps) */
 } moto_params;
 
 /* Fills *p with the defaults listed above. */
@@ -251,9 +262,14 @@ int moto_ascend(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V_d
 
 /* Two-sided descent (Results, "Deterministic bidirectional saddle descent";
  * Algorithm 1): seeds m_saddle +- eta v1 with eta = eta_theta / max_i |v1_i|
- * (retracted), each relaxed by the outer optimiser (params.optimizer) on g
- * until max_i |g_i| <= tau_F or
- * descent_max_steps.  Writes m_plus_dev, m_minus_dev (3N each) and
+ * (retracted), each relaxed by the outer optimiser (params.optimizer) on g,
+ * or with params.descent = MOTO_DESCENT_LLG by damped spin dynamics
+ *   dm_i/dt = (m_i x g_i - alpha g_i) / (1 + alpha^2)
+ * (Landau-Lifshitz-Gilbert with h = -grad E, time in hbar/meV; Heun with
+ * renormalisation, step llg_dt, at most llg_time; Supplementary Note 2: alpha
+ * = 1 for 50 ps, its T = 1e-6 taken as zero), until max_i |g_i| <= tau_F or
+ * descent_max_steps (optimiser) / llg_time (LLG).  Writes m_plus_dev,
+ * m_minus_dev (3N each) and
  * out_dev (6 doubles): [E+, Q+, E-, Q-, steps+, steps-] with E in double
  * arithmetic.  Synchronises the stream.  Returns MOTO_OK if both sides
  * converged, MOTO_NOT_CONVERGED otherwise. */
@@ -296,7 +312,9 @@ void moto_batch_destroy(moto_batch* batch);
 int moto_batch_ascend(moto_batch* batch, int check_every, double* rec_dev, int* status_host, int* steps_host,
                       void* stream);
 
-/* Two-sided descent (as moto_descend) from every walker's current spins and
+/* Two-sided descent (as moto_descend, with the outer optimiser; a batch
+ * created with params.descent = MOTO_DESCENT_LLG is refused with
+ * MOTO_ERR_ARG) from every walker's current spins and
  * first mode: m_plus[i], m_minus[i] (3N each, device) receive the two
  * minima; out_dev (n x 6 doubles): [E+, Q+, E-, Q-, steps+, steps-]. */
 int moto_batch_descend(moto_batch* batch, void* const* m_plus, void* const* m_minus, double* out_dev,

@@ -40,6 +40,18 @@ downhill).  Readings where the paper gives no rule:
   Barzilai & Borwein 1988, the same scale L-BFGS starts from), capped at
   theta_max per spin.  (A fixed alpha = gamma0 was tried first: on the
   32 x 32 workload it did not reach a saddle in 300 steps.)
+* [R20] Dynamic certifier (Supplementary Note 1 (iii), "or dynamic simulator";
+  Supplementary Note 2: atomistic spin dynamics, Gilbert damping alpha = 1,
+  T = 1e-6, 50 ps): the Landau-Lifshitz-Gilbert equation in the
+  Landau-Lifshitz form with the effective field h_i = -grad_i E in meV and
+  time in units of hbar/meV (0.6582 ps):
+      dm_i/dt = (m_i x g_i - alpha g_i) / (1 + alpha^2),
+  g the Riemannian gradient (the tangent part of grad E; m x (m x h) = -h_t
+  for unit m).  Heun predictor-corrector with renormalisation after each
+  stage, step dt = 0.01 hbar/meV, at most 50 ps = 75.96 hbar/meV, stopped
+  early when max_i |g_i| <= tau_F.  T = 1e-6 of the paper is taken as zero
+  (no stochastic field; a thermal field of that size is far below the
+  exchange and would make the trajectory non-deterministic).
 """
 from __future__ import annotations
 
@@ -67,6 +79,10 @@ class MMFParams:
     descent_max_steps: int = 5000
     optimizer: str = "lbfgs"       # "lbfgs" | "cg" (R16)
     subspace: bool = False         # reflect all k modes (R15) instead of v1
+    descent: str = "optimizer"     # "optimizer" | "llg" (R20)
+    llg_alpha: float = 1.0         # Gilbert damping
+    llg_dt: float = 0.01           # hbar/meV
+    llg_time: float = 50.0 / 0.6582119569  # 50 ps in hbar/meV
 
 
 def _dot(a, b) -> float:
@@ -278,6 +294,39 @@ def relax(model, m0: np.ndarray, p: MMFParams):
     return m, converged, step
 
 
+def llg_rate(model, m: np.ndarray, alpha: float):
+    """dm/dt of the damped LLG equation (R20) and the gradient it used."""
+    g, _ = spin.riemann_grad(model, m)
+    mxg = np.stack([m[1] * g[2] - m[2] * g[1], m[2] * g[0] - m[0] * g[2], m[0] * g[1] - m[1] * g[0]])
+    return (mxg - alpha * g) / (1.0 + alpha * alpha), g
+
+
+def _unit(m: np.ndarray) -> np.ndarray:
+    return m / np.sqrt(np.sum(m * m, axis=0))[None]
+
+
+def llg_step(model, m: np.ndarray, alpha: float, dt: float):
+    """One Heun step with renormalisation (R20); returns (m_new, g at m)."""
+    k1, g = llg_rate(model, m, alpha)
+    mp = _unit(m + dt * k1)
+    k2, _ = llg_rate(model, mp, alpha)
+    return _unit(m + 0.5 * dt * (k1 + k2)), g
+
+
+def llg_relax(model, m0: np.ndarray, p: MMFParams):
+    """Damped spin dynamics until max_i |g_i| <= tau_F or llg_time (R20)."""
+    m = m0.copy()
+    nmax = int(math.ceil(p.llg_time / p.llg_dt - 1e-9))
+    for step in range(nmax + 1):
+        g, _ = spin.riemann_grad(model, m)
+        if max_torque(g) <= p.tau_F:
+            return m, True, step
+        if step == nmax:
+            break
+        m, _ = llg_step(model, m, p.llg_alpha, p.llg_dt)
+    return m, False, nmax
+
+
 def descent_seeds(m_saddle: np.ndarray, v1: np.ndarray, p: MMFParams):
     """x_saddle +- eta v1, retracted (reading R9)."""
     eta = p.eta_theta / max_torque(v1)
@@ -288,7 +337,10 @@ def descend(model, m_saddle: np.ndarray, v1: np.ndarray, p: MMFParams):
     """Two-sided descent: returns (DescentResult for +, DescentResult for -)."""
     out = []
     for seed in descent_seeds(m_saddle, v1, p):
-        m, conv, steps = relax(model, seed, p)
+        if p.descent == "llg":
+            m, conv, steps = llg_relax(model, seed, p)
+        else:
+            m, conv, steps = relax(model, seed, p)
         q = topo.topo_charge(m)
         out.append(DescentResult(m=m, E=spin.energy(model, m), Q=q, Qint=int(round(q)), converged=conv, steps=steps))
     return out[0], out[1]

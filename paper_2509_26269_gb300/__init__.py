@@ -21,6 +21,7 @@ MOTO_ERR_ARG, MOTO_ERR_CUDA, MOTO_ERR_NUMERIC = -1, -2, -3
 MOTO_ERR_NONFINITE, MOTO_ERR_TIMEOUT, MOTO_ERR_NOMEM = -4, -5, -6
 MOTO_SOLVER_LANCZOS, MOTO_SOLVER_LOBPCG = 0, 1
 MOTO_OPT_LBFGS, MOTO_OPT_CG = 0, 1
+MOTO_DESCENT_OPT, MOTO_DESCENT_LLG = 0, 1
 MOTO_MAX_POP = 64
 MOTO_MAX_K, MOTO_MAX_BASIS, MOTO_MAX_MEM = 8, 96, 8
 
@@ -38,7 +39,8 @@ class moto_params(ctypes.Structure):
         ("max_iter", ctypes.c_int), ("tol", ctypes.c_double), ("lbfgs_mem", ctypes.c_int),
         ("theta_max", ctypes.c_double), ("gamma0", ctypes.c_double), ("tau_F", ctypes.c_double),
         ("eta_theta", ctypes.c_double), ("max_steps", ctypes.c_int), ("descent_max_steps", ctypes.c_int),
-        ("optimizer", ctypes.c_int), ("subspace", ctypes.c_int),
+        ("optimizer", ctypes.c_int), ("subspace", ctypes.c_int), ("descent", ctypes.c_int),
+        ("llg_alpha", ctypes.c_double), ("llg_dt", ctypes.c_double), ("llg_time", ctypes.c_double),
     ]
 
 

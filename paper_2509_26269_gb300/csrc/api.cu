@@ -136,6 +136,18 @@ void P_mmf_force(moto_ctx* c, const T* g, const T* V, size_t ldv, int nv, const 
   launch_mmf_force<T>(g, V, ldv, nv, dots, G, N, part, counter, fmax_out, gate, mask, st);
 }
 template <typename T>
+void P_llg_predict(moto_ctx* c, const T* m, const T* g, T* mp, double alpha, double dt, int N, const int* gate,
+                   int mask, cudaStream_t st) {
+  PROF(kPkVec, 9.0 * N * sizeof(T));
+  launch_llg_predict<T>(m, g, mp, alpha, dt, N, gate, mask, st);
+}
+template <typename T>
+void P_llg_correct(moto_ctx* c, T* m, const T* g0, const T* mp, const T* g1, double alpha, double dt, int N,
+                   const int* gate, int mask, cudaStream_t st) {
+  PROF(kPkVec, 15.0 * N * sizeof(T));
+  launch_llg_correct<T>(m, g0, mp, g1, alpha, dt, N, gate, mask, st);
+}
+template <typename T>
 void P_cg_direction(moto_ctx* c, const T* m, const T* G, T* p, int N, const double* cg, double theta_max,
                     double* part, unsigned* counter, DevState* dst, const int* gate, int mask, cudaStream_t st) {
   PROF(kPkVec, 12.0 * N * sizeof(T));
@@ -359,6 +371,9 @@ int check_params(const moto_params* p) {
   if (p->max_steps < 0 || p->descent_max_steps < 0) return MOTO_ERR_ARG;
   if (p->optimizer != MOTO_OPT_LBFGS && p->optimizer != MOTO_OPT_CG) return MOTO_ERR_ARG;
   if (p->subspace != 0 && p->subspace != 1) return MOTO_ERR_ARG;
+  if (p->descent != MOTO_DESCENT_OPT && p->descent != MOTO_DESCENT_LLG) return MOTO_ERR_ARG;
+  if (!(p->llg_alpha >= 0.0) || !(p->llg_dt > 0.0) || !(p->llg_time >= 0.0)) return MOTO_ERR_ARG;
+  if (p->descent == MOTO_DESCENT_LLG && p->llg_time / p->llg_dt > 1e8) return MOTO_ERR_ARG;
   return MOTO_OK;
 }
 
@@ -558,6 +573,10 @@ void moto_default_params(moto_params* p) {
   p->descent_max_steps = 5000;
   p->optimizer = MOTO_OPT_LBFGS;
   p->subspace = 0;
+  p->descent = MOTO_DESCENT_OPT;
+  p->llg_alpha = 1.0;
+  p->llg_dt = 0.01;
+  p->llg_time = 50.0 / 0.6582119569;  // 50 ps in hbar/meV
 }
 
 const char* moto_status_string(int code) {
@@ -799,7 +818,8 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
   } else {
     P_mmf_force<T>(c, g, nullptr, n3, 0, D + kMmfDots, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
   }
-  P_saddle_test(c, D + kEG, D + kFmax, lam, D + kMmfDots, p->tau_F, out6, status, c->st, ascent ? 1 : 0, st);
+  P_saddle_test(c, D + kEG, D + kFmax, lam, D + kMmfDots, p->tau_F, out6, status, c->st, ascent ? 1 : 0,
+                update ? 0 : 1, st);
   if (!update) return;
   if (p->optimizer == MOTO_OPT_CG) {
     // nonlinear CG: the pair s = P d_prev, y = G - P G_prev (staging fields),
@@ -852,6 +872,46 @@ int run_opt(moto_ctx* c, T* m, const moto_params* p, T* V, double* trace, int ch
     opt_step<T>(c, m, p, V, o, nullptr, ascent, t < max_steps, st);
     if (cudaGetLastError() != cudaSuccess) return MOTO_ERR_CUDA;
     if ((t + 1) % check_every == 0 || t == max_steps) {
+      int rc = read_state(c, &h, st);
+      if (rc) return rc;
+      if (h.converged || status_code(h)) break;
+    }
+  }
+  if (steps_out) *steps_out = h.pad[1];
+  int sc = status_code(h);
+  if (sc) return sc;
+  return h.converged ? MOTO_OK : MOTO_NOT_CONVERGED;
+}
+
+// Damped spin dynamics (two-sided descent with params.descent = LLG): Heun
+// steps m -> m_pred (gradient at m) -> m (gradients at m and m_pred) until
+// max_i |g_i| <= tau_F or llg_time; the stopping test runs on the device
+// after the gradient at m, the host reads it every check_every steps.
+template <typename T>
+int run_llg(moto_ctx* c, T* m, const moto_params* p, int check_every, int* steps_out, cudaStream_t st) {
+  const size_t ld = c->ld;
+  const int N = c->N;
+  T* g0 = static_cast<T*>(c->g);
+  T* ring = static_cast<T*>(c->ring);
+  T* mp = ring;  // predictor spins and their gradient: ring fields 0, 1
+  T* g1 = ring + ld;
+  double* D = c->dsm;
+  int* gate = &c->st->gate;
+  const long nmax = (long)std::ceil(p->llg_time / p->llg_dt - 1e-9);
+  state_kernel<<<1, 32, 0, st>>>(c->st, 1);
+  DevState h;
+  memset(&h, 0, sizeof(h));
+  for (long t = 0; t <= nmax; ++t) {
+    P_energy_grad<T>(c, c->md, m, g0, nullptr, c->part, c->counter, D + kEG, &c->st->status, false, st);
+    P_saddle_test(c, D + kEG, D + kFmax, D + kTheta, D + kMmfDots, p->tau_F, D + kTmp, nullptr, c->st, 0,
+                  t == nmax ? 1 : 0, st);
+    if (t < nmax) {
+      P_llg_predict<T>(c, m, g0, mp, p->llg_alpha, p->llg_dt, N, gate, kGateDone, st);
+      P_energy_grad<T>(c, c->md, mp, g1, nullptr, c->part, c->counter, D + kTmp + 2, &c->st->status, false, st);
+      P_llg_correct<T>(c, m, g0, mp, g1, p->llg_alpha, p->llg_dt, N, gate, kGateDone, st);
+    }
+    if (cudaGetLastError() != cudaSuccess) return MOTO_ERR_CUDA;
+    if ((t + 1) % check_every == 0 || t == nmax) {
       int rc = read_state(c, &h, st);
       if (rc) return rc;
       if (h.converged || status_code(h)) break;
@@ -942,11 +1002,15 @@ int moto_descend(moto_ctx* c, const void* m_saddle, const void* v1, const moto_p
     if (c->dtype == MOTO_F32) {
       launch_descent_seed<float>((const float*)m_saddle, (const float*)v1, p->eta_theta, sign, (float*)mo, c->N,
                                  c->part, c->counter, c->dsm + kTmp, st);
-      rc = run_opt<float>(c, (float*)mo, p, nullptr, nullptr, 25, p->descent_max_steps, false, &steps, st);
+      rc = p->descent == MOTO_DESCENT_LLG
+               ? run_llg<float>(c, (float*)mo, p, 25, &steps, st)
+               : run_opt<float>(c, (float*)mo, p, nullptr, nullptr, 25, p->descent_max_steps, false, &steps, st);
     } else {
       launch_descent_seed<double>((const double*)m_saddle, (const double*)v1, p->eta_theta, sign, (double*)mo,
                                   c->N, c->part, c->counter, c->dsm + kTmp, st);
-      rc = run_opt<double>(c, (double*)mo, p, nullptr, nullptr, 25, p->descent_max_steps, false, &steps, st);
+      rc = p->descent == MOTO_DESCENT_LLG
+               ? run_llg<double>(c, (double*)mo, p, 25, &steps, st)
+               : run_opt<double>(c, (double*)mo, p, nullptr, nullptr, 25, p->descent_max_steps, false, &steps, st);
     }
     if (rc < 0) return rc;
     if (rc == MOTO_NOT_CONVERGED) result = MOTO_NOT_CONVERGED;
@@ -1265,6 +1329,7 @@ extern "C" {
 int moto_batch_create(const moto_model* model, int dtype, const moto_params* params, const moto_walker* walkers,
                       int n_walkers, int n_streams, moto_batch** out) {
   if (!model || !params || !walkers || !out || n_walkers < 1 || n_streams < 1) return MOTO_ERR_ARG;
+  if (params->descent != MOTO_DESCENT_OPT) return MOTO_ERR_ARG;  // batches descend with the optimiser
   for (int i = 0; i < n_walkers; ++i)
     if (!walkers[i].m_dev || !walkers[i].V_dev) return MOTO_ERR_ARG;
   *out = nullptr;

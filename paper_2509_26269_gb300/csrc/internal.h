@@ -179,7 +179,18 @@ template <typename T>
 bool launch_pairwise_l1(const T* X, size_t ldx, int P, size_t n, double* part, size_t part_cap, unsigned* counter,
                         double* D, cudaStream_t st);
 
+// Damped spin dynamics (Heun): predictor mp = unit(m + dt f(m, g)); corrector
+// m <- unit(m + dt/2 (f(m, g0) + f(mp, g1))), f(m, g) = (m x g - alpha g) /
+// (1 + alpha^2) with g the Riemannian gradient
+template <typename T>
+void launch_llg_predict(const T* m, const T* g, T* mp, double alpha, double dt, int N, const int* gate, int mask,
+                        cudaStream_t st);
+template <typename T>
+void launch_llg_correct(T* m, const T* g0, const T* mp, const T* g1, double alpha, double dt, int N,
+                        const int* gate, int mask, cudaStream_t st);
+
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
-                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, cudaStream_t st);
+                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, int last,
+                        cudaStream_t st);
 
 }  // namespace moto

@@ -1578,6 +1578,79 @@ void launch_cg_retract(T* m, const T* G, T* p, T* d, const DevState* dst, int N,
   cg_retract_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, G, p, d, dst, N, gate, mask);
 }
 
+// ---- damped spin dynamics (Landau-Lifshitz-Gilbert, Heun; see internal.h) ----
+template <typename T>
+__device__ __forceinline__ void llg_rate(const T (&m)[3], const T (&g)[3], T c1, T c2, T (&f)[3]) {
+  // f = (m x g - alpha g) / (1 + alpha^2) = c1 (m x g) - c2 g
+  f[0] = c1 * (m[1] * g[2] - m[2] * g[1]) - c2 * g[0];
+  f[1] = c1 * (m[2] * g[0] - m[0] * g[2]) - c2 * g[1];
+  f[2] = c1 * (m[0] * g[1] - m[1] * g[0]) - c2 * g[2];
+}
+template <typename T>
+__device__ __forceinline__ void unit3(T (&x)[3]) {
+  const T inv = (T)1 / sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  x[0] *= inv;
+  x[1] *= inv;
+  x[2] *= inv;
+}
+
+template <typename T>
+__global__ void llg_predict_kernel(const T* __restrict__ m, const T* __restrict__ g, T* mp, T c1, T c2, T dt, int N,
+                                   const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T mm[3], gg[3], f[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      mm[c] = m[(size_t)c * N + i];
+      gg[c] = g[(size_t)c * N + i];
+    }
+    llg_rate(mm, gg, c1, c2, f);
+    T x[3] = {mm[0] + dt * f[0], mm[1] + dt * f[1], mm[2] + dt * f[2]};
+    unit3(x);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mp[(size_t)c * N + i] = x[c];
+  }
+}
+
+template <typename T>
+__global__ void llg_correct_kernel(T* m, const T* __restrict__ g0, const T* __restrict__ mp,
+                                   const T* __restrict__ g1, T c1, T c2, T hdt, int N, const int* gate, int mask) {
+  if (gate && (*gate & mask)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    T mm[3], ga[3], mq[3], gb[3], f1[3], f2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t e = (size_t)c * N + i;
+      mm[c] = m[e];
+      ga[c] = g0[e];
+      mq[c] = mp[e];
+      gb[c] = g1[e];
+    }
+    llg_rate(mm, ga, c1, c2, f1);
+    llg_rate(mq, gb, c1, c2, f2);
+    T x[3] = {mm[0] + hdt * (f1[0] + f2[0]), mm[1] + hdt * (f1[1] + f2[1]), mm[2] + hdt * (f1[2] + f2[2])};
+    unit3(x);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[(size_t)c * N + i] = x[c];
+  }
+}
+
+template <typename T>
+void launch_llg_predict(const T* m, const T* g, T* mp, double alpha, double dt, int N, const int* gate, int mask,
+                        cudaStream_t st) {
+  const double d = 1.0 + alpha * alpha;
+  llg_predict_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, g, mp, (T)(1.0 / d), (T)(alpha / d), (T)dt, N, gate,
+                                                             mask);
+}
+template <typename T>
+void launch_llg_correct(T* m, const T* g0, const T* mp, const T* g1, double alpha, double dt, int N,
+                        const int* gate, int mask, cudaStream_t st) {
+  const double d = 1.0 + alpha * alpha;
+  llg_correct_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, g0, mp, g1, (T)(1.0 / d), (T)(alpha / d),
+                                                             (T)(0.5 * dt), N, gate, mask);
+}
+
 // Descent seed: out = Rodrigues(m, sign * eta * v1), eta = eta_theta / max|v1_i|.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) vmax_kernel(const T* v, int N, double* part, unsigned* counter,
@@ -1621,8 +1694,10 @@ void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign,
 }
 
 // Saddle / minimum test and the per-step output vector.
+// last: the final test of a run (no step follows it, so none is counted)
 __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
-                                   double tau_F, double* out6, int* status_out, DevState* dst, int ascent) {
+                                   double tau_F, double* out6, int* status_out, DevState* dst, int ascent,
+                                   int last) {
   if (threadIdx.x != 0) return;
   if (dst->gate & kGateDone) {
     if (status_out) *status_out = 1;
@@ -1651,15 +1726,16 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
   if (conv) {
     dst->gate |= kGateDone;
     dst->converged = 1;
-  } else {
+  } else if (!last) {
     dst->pad[1] += 1;  // outer steps taken
   }
   if (status_out) *status_out = conv ? 1 : 0;
 }
 
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
-                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, cudaStream_t st) {
-  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, out6, status_out, dst, ascent);
+                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, int last,
+                        cudaStream_t st) {
+  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, out6, status_out, dst, ascent, last);
 }
 
 #define INST(T)                                                                                                   \
@@ -1678,6 +1754,9 @@ void launch_saddle_test(const double* eg_out, const double* fmax, const double* 
   template void launch_cg_direction<T>(const T*, const T*, T*, int, const double*, double, double*, unsigned*,   \
                                        DevState*, const int*, int, cudaStream_t);                                 \
   template void launch_cg_retract<T>(T*, const T*, T*, T*, const DevState*, int, const int*, int, cudaStream_t);  \
+  template void launch_llg_predict<T>(const T*, const T*, T*, double, double, int, const int*, int, cudaStream_t); \
+  template void launch_llg_correct<T>(T*, const T*, const T*, const T*, double, double, int, const int*, int,     \
+                                      cudaStream_t);                                                             \
   template void launch_lbfgs_pair<T>(const T*, const T*, const T*, const T*, T*, size_t, T*, const DevState*,     \
                                      int, const int*, int, cudaStream_t);                                         \
   template void launch_lbfgs_direction<T>(const T*, size_t, int, const double*, const T*, T*, int, double,        \

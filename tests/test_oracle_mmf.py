@@ -226,3 +226,52 @@ def test_config1_subspace_ascent_reaches_an_index1_saddle():
     assert w[0] < 0.0 < w[1]
     assert res.lam[0] == pytest.approx(w[0], abs=1e-7)
     assert res.lam[1] == pytest.approx(w[1], abs=1e-7)
+
+
+def _free_spins_model(L, muB):
+    # no exchange, DMI or anisotropy: every spin precesses alone in the field
+    return Model(L, L, J=(0.0,), D=0.0, K=0.0, muB=muB)
+
+
+def test_llg_single_spin_matches_the_closed_form():
+    # a spin at polar angle theta0 in the field muB z (E = -muB m_z):
+    # tan(theta/2) = tan(theta0/2) exp(-alpha muB t / (1 + alpha^2)) and the
+    # azimuth turns at muB / (1 + alpha^2) (hbar/meV time units), the
+    # textbook solution of the Landau-Lifshitz-Gilbert equation in a static
+    # field; Heun's error is O(dt^2)
+    L, muB, alpha, dt, nsteps = 5, 0.7, 0.5, 1e-3, 2000
+    M = _free_spins_model(L, muB)
+    rng = inputs.gaussian_field(61, L, L)
+    m = rng / np.sqrt(np.sum(rng * rng, axis=0))[None]
+    th0 = np.arccos(m[2])
+    ph0 = np.arctan2(m[1], m[0])
+    x = m.copy()
+    for _ in range(nsteps):
+        x, _ = mmf.llg_step(M, x, alpha, dt)
+    t = nsteps * dt
+    th = 2.0 * np.arctan(np.tan(th0 / 2.0) * np.exp(-alpha * muB * t / (1.0 + alpha * alpha)))
+    np.testing.assert_allclose(np.arccos(np.clip(x[2], -1, 1)), th, atol=1e-6)
+    # m x g = muB sin(theta) phi_hat: the azimuth grows at muB / (1 + alpha^2)
+    dphi = np.angle(np.exp(1j * (np.arctan2(x[1], x[0]) - ph0)))
+    np.testing.assert_allclose(dphi, muB * t / (1.0 + alpha * alpha), atol=1e-6)
+    np.testing.assert_allclose(np.sum(x * x, axis=0), 1.0, atol=1e-14)
+
+
+def test_llg_damping_lowers_the_energy_and_precession_conserves_it():
+    p = inputs.WORKLOADS[1]
+    M = Model(16, 16, J=p["J"], D=p["D"], K=p["K"], muB=p["muB"])
+    m = inputs.add_noise(inputs.skyrmion(16, 16, 3.0), 0.05, 9)
+    E = [spin.energy(M, m)]
+    x = m.copy()
+    for _ in range(200):
+        x, _ = mmf.llg_step(M, x, 1.0, 0.01)
+        E.append(spin.energy(M, x))
+    assert np.all(np.diff(E) < 0.0)
+    # alpha = 0: energy drift is second order in dt
+    drift = []
+    for dt in (0.004, 0.002):
+        x = m.copy()
+        for _ in range(int(round(0.4 / dt))):
+            x, _ = mmf.llg_step(M, x, 0.0, dt)
+        drift.append(abs(spin.energy(M, x) - E[0]))
+    assert drift[1] < 0.35 * drift[0]
