@@ -36,6 +36,10 @@ HVP_PER_STEP = BLOCK * STEPS
 METRIC = "spin-HVP Gspin/s"
 UNIT = "Gspin-HVP/s"
 TILE_CLASSES = ("gram", "reorth_gram", "reorth_update")
+# DRAM bytes (read + write) per tile2d launch of one MMF step, measured with
+# ncu at 1024 x 1024 (profiles/traffic_mmf_step_1024.md); every launch scales
+# with the number of sites
+TILE_TRAFFIC_1024 = 507.7e6
 WORKLOAD = "roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12)"
 
 
@@ -368,7 +372,11 @@ def run_ours(args, rank, world, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single"}),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": TILE_TRAFFIC_1024 * (L / 1024) ** 2 if dom == "tile2d" else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at "
+                                           "1024x1024, scaled by sites",
+                         "peak_source": peak_kind,
                          "launches_in_step": n_l, "ms_in_step": dom_ms},
             "kernel_classes": {k: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] * 1e-3) / 1e9 if v[1] else 0.0)}
                                for k, v in prof.items()},
