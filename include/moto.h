@@ -80,6 +80,8 @@ enum {
 #define MOTO_MAX_BASIS 96   /* Krylov basis vectors (block * steps) */
 #define MOTO_MAX_MEM 8      /* L-BFGS pairs */
 #define MOTO_MAX_POP 64     /* candidates of one pairwise-distance call */
+#define MOTO_MAX_PAIRS 128  /* ordered pairs of a pair-list Hamiltonian */
+#define MOTO_MAX_REACH 8    /* largest |d1|, |d2| of a pair offset */
 
 /* Spin Hamiltonian of Eq. param-hamiltonian (Methods, "Spin Hamiltonian and
  * manifold gradient"), read with ordered-pair sums (each bond counted twice):
@@ -123,6 +125,14 @@ typedef struct {
   double llg_time;    /* LLG duration per side, hbar/meV            (75.96 = 50 ps) */
 } moto_params;
 
+/* One ordered pair (i, i + d) of a pair-list Hamiltonian, d = d1 a1 + d2 a2
+ * in index space. */
+typedef struct {
+  int d1, d2;
+  double J;      /* exchange, meV */
+  double D[3];   /* DMI vector (x, y, z), meV */
+} moto_pair;
+
 /* Fills *p with the defaults listed above. */
 void moto_default_params(moto_params* p);
 
@@ -132,6 +142,19 @@ void moto_default_params(moto_params* p);
  * MOTO_F64.  On success *out receives the context.  Must be called with the
  * target device current. */
 int moto_create(const moto_model* model, int dtype, const moto_params* params, moto_ctx** out);
+
+/* Replaces the context's exchange shells and Neel DMI by a general pair list
+ * (an extension for many-shell parameterisations with full DMI vectors, such
+ * as the paper's Pd/Fe/Ir(111) tables; K and muB of the model stay):
+ *   E = - sum_i sum_p [ J_p m_i . m_{i+d_p} + D_p . (m_i x m_{i+d_p}) ]
+ *       - muB sum_i m_iz - K sum_i m_iz^2.
+ * The list must be closed under d -> -d with J_{-d} = J_d and D_{-d} = -D_d
+ * (every bond counted twice, as in Eq. param-hamiltonian; checked exactly),
+ * have no d = 0, at most MOTO_MAX_PAIRS entries, |d1|, |d2| <= MOTO_MAX_REACH
+ * and L1, L2 >= 2 max(|d1|, |d2|) + 1.  Every later energy, gradient, HVP and
+ * solver call of the context uses it; n_pairs = 0 restores the shell model.
+ * Copies the list (synchronously); returns MOTO_ERR_ARG when a rule fails. */
+int moto_set_pairs(moto_ctx* ctx, const moto_pair* pairs, int n_pairs);
 
 /* Releases the context and its scratch (synchronises the device first). */
 void moto_destroy(moto_ctx* ctx);

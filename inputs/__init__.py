@@ -301,3 +301,23 @@ def workload5_state():
     p = WORKLOADS[5]
     m = biskyrmion(p["L1"], p["L2"], 8.0)
     return add_noise(m, 0.05, workload_seed(5, 0))
+
+
+def random_pairs(seed: int, reach: int, n_offsets: int):
+    """A pair list for the general pair-list Hamiltonian: up to n_offsets
+    distinct offsets (d1, d2) with |d1|, |d2| <= reach, each listed with its
+    negative; J ~ 0.3 N(0,1), D ~ 0.2 N(0,1)^3 for the first and (J, -D) for
+    the negative, so the list has the closure an ordered-pair sum needs."""
+    vals = normal(seed, 8 * n_offsets).reshape(n_offsets, 8)
+    seen, out = set(), []
+    for k in range(n_offsets):
+        d1 = int(round(vals[k, 0] * 10)) % (2 * reach + 1) - reach
+        d2 = int(round(vals[k, 1] * 10)) % (2 * reach + 1) - reach
+        if (d1, d2) == (0, 0) or (d1, d2) in seen or (-d1, -d2) in seen:
+            continue
+        seen.add((d1, d2))
+        J = 0.3 * float(vals[k, 2])
+        D = tuple(0.2 * float(x) for x in vals[k, 3:6])
+        out.append((d1, d2, J, D))
+        out.append((-d1, -d2, J, tuple(-x for x in D)))
+    return out

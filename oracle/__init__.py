@@ -20,6 +20,8 @@ computes, in float64 numpy, written from the paper's definitions:
   descent"; Algorithm 1).
 * ``topo``   -- lattice topological charge Q (Results, Pd/Fe/Ir(111) networks:
   Q = +1 skyrmion, -1 antiskyrmion).
+* ``pairs``  -- a general pair-list Hamiltonian (many shells, full DMI vectors)
+  with its derivatives, of which the shell model is one instance.
 * ``explorer`` -- masked perturbations x0 + P_Omega delta and the objectives
   of the initial-configuration explorer (Results, "Multi-objective
   initial-configuration explorer").
@@ -33,4 +35,4 @@ trajectory of the ascent itself, whose end point is pinned by the saddle
 signature of the dense spectrum (see ``mmf``).
 """
 from .model import Model, SHELLS, model_from_workload  # noqa: F401
-from . import spin, krylov, mmf, topo, explorer  # noqa: F401
+from . import spin, krylov, mmf, topo, explorer, pairs  # noqa: F401

@@ -23,6 +23,7 @@ MOTO_SOLVER_LANCZOS, MOTO_SOLVER_LOBPCG = 0, 1
 MOTO_OPT_LBFGS, MOTO_OPT_CG = 0, 1
 MOTO_DESCENT_OPT, MOTO_DESCENT_LLG = 0, 1
 MOTO_MAX_POP = 64
+MOTO_MAX_PAIRS, MOTO_MAX_REACH = 128, 8
 MOTO_MAX_K, MOTO_MAX_BASIS, MOTO_MAX_MEM = 8, 96, 8
 
 
@@ -42,6 +43,10 @@ class moto_params(ctypes.Structure):
         ("optimizer", ctypes.c_int), ("subspace", ctypes.c_int), ("descent", ctypes.c_int),
         ("llg_alpha", ctypes.c_double), ("llg_dt", ctypes.c_double), ("llg_time", ctypes.c_double),
     ]
+
+
+class moto_pair(ctypes.Structure):
+    _fields_ = [("d1", ctypes.c_int), ("d2", ctypes.c_int), ("J", ctypes.c_double), ("D", ctypes.c_double * 3)]
 
 
 class moto_walker(ctypes.Structure):
@@ -82,6 +87,7 @@ def _load():
         "moto_energy_grad_noalloc": (I, [ctypes.POINTER(moto_model), I, P, P, P, P, P]),
         "moto_gram": (I, [P, P, Z, I, P, Z, I, P, P]),
         "moto_perturb": (I, [P, P, P, P, Z, I, P, Z, P]),
+        "moto_set_pairs": (I, [P, ctypes.POINTER(moto_pair), I]),
         "moto_pairwise_l1": (I, [P, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
         "moto_batch_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params),
@@ -103,7 +109,7 @@ EXPORTED = (
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
-    "moto_perturb", "moto_pairwise_l1",
+    "moto_perturb", "moto_pairwise_l1", "moto_set_pairs",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
@@ -209,6 +215,16 @@ def moto_lowest_modes(ctx, m, s, params, v0, V, lam, info=None, stream=None):
 def moto_gram(ctx, X, ldx, nx, Y, ldy, ny, out, stream=None):
     _check(_lib.moto_gram(ctx, _ptr(X), int(ldx), int(nx), _ptr(Y), int(ldy), int(ny), _ptr(out),
                           _stream(stream)), "moto_gram")
+
+
+def moto_set_pairs(ctx, pairs):
+    """pairs: sequence of (d1, d2, J, (Dx, Dy, Dz)); empty restores the shells."""
+    arr = (moto_pair * max(len(pairs), 1))()
+    for i, (d1, d2, J, D) in enumerate(pairs):
+        arr[i].d1, arr[i].d2, arr[i].J = int(d1), int(d2), float(J)
+        for c in range(3):
+            arr[i].D[c] = float(D[c])
+    _check(_lib.moto_set_pairs(ctx, arr, len(pairs)), "moto_set_pairs")
 
 
 def moto_perturb(ctx, x0, mask, delta, ld_delta, count, out, ld_out, stream=None):

@@ -9,7 +9,7 @@ import torch
 from . import (MOTO_F32, MOTO_F64, MOTO_MAX_BASIS, make_model, make_params, moto_ascend, moto_batch_ascend,
                moto_batch_create, moto_batch_descend, moto_batch_destroy, moto_create, moto_descend, moto_destroy,
                moto_energy, moto_energy_grad, moto_hvp, moto_lbfgs_reset, moto_lowest_modes, moto_mmf_step,
-               moto_pairwise_l1, moto_perturb, moto_topo_charge, moto_workspace_bytes)
+               moto_pairwise_l1, moto_perturb, moto_set_pairs, moto_topo_charge, moto_workspace_bytes)
 
 
 class Context:
@@ -78,6 +78,11 @@ class Context:
         Q = torch.empty(1, dtype=torch.float64, device=self.device)
         moto_topo_charge(self.handle, m, Q)
         return Q
+
+    def set_pairs(self, pairs):
+        """Use a general pair-list Hamiltonian (``moto_set_pairs``): pairs is
+        a sequence of (d1, d2, J, (Dx, Dy, Dz)); [] restores the shells."""
+        moto_set_pairs(self.handle, list(pairs))
 
     def perturb(self, x0, delta, mask=None):
         """Masked perturbations R_x0(P_mask P_x0 delta_j) of x0 for a stack

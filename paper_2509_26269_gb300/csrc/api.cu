@@ -8,7 +8,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -16,6 +19,7 @@ using namespace moto;
 
 struct moto_ctx {
   ModelDev md;
+  double* pairs;  // pair-list storage, MOTO_MAX_PAIRS x [d1, d2, J, Dx, Dy, Dz]
   int dtype;
   size_t esize;
   moto_params p;  // sizing parameters given at creation
@@ -624,6 +628,7 @@ int moto_create(const moto_model* model, int dtype, const moto_params* params, m
   size_t part = std::max<size_t>(2 * tb, (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K);
   part = std::max<size_t>(part, (size_t)kSMs * 8 * MOTO_MAX_K * 4);
   part = std::max<size_t>(part, (size_t)kStreamBlocks * 9 * MOTO_MAX_K * MOTO_MAX_K * 2);
+  part = std::max<size_t>(part, 2 * (size_t)pair_blocks(c->md));
   c->part_len = part;
   struct A {
     void** p;
@@ -637,6 +642,7 @@ int moto_create(const moto_model* model, int dtype, const moto_params* params, m
       {&c->ring, vb * (2 * R + 5)},
       {&c->lob, vb * 12 * MOTO_MAX_K},  // two sets of [X, W, P, AX, AW, AP]
       {(void**)&c->dsm, kDsmSize * sizeof(double)},
+      {(void**)&c->pairs, (size_t)MOTO_MAX_PAIRS * 6 * sizeof(double)},
       {(void**)&c->part, part * sizeof(double)},
       {(void**)&c->counter, 64 * sizeof(unsigned)},
       {(void**)&c->st, sizeof(DevState)},
@@ -660,10 +666,50 @@ int moto_create(const moto_model* model, int dtype, const moto_params* params, m
 void moto_destroy(moto_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  void* ptrs[] = {c->basis, c->W, c->Wt, c->g, c->s, c->ring, c->lob, c->dsm, c->part, c->counter, c->st};
+  void* ptrs[] = {c->basis, c->W, c->Wt, c->g, c->s, c->ring, c->lob, c->dsm, c->pairs, c->part, c->counter, c->st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
+}
+
+int moto_set_pairs(moto_ctx* c, const moto_pair* pairs, int n) {
+  if (!c || n < 0 || n > MOTO_MAX_PAIRS || (n > 0 && !pairs)) return MOTO_ERR_ARG;
+  int reach = 0;
+  std::vector<double> rec((size_t)n * 6);
+  for (int p = 0; p < n; ++p) {
+    const moto_pair& a = pairs[p];
+    if (a.d1 == 0 && a.d2 == 0) return MOTO_ERR_ARG;
+    if (std::abs(a.d1) > MOTO_MAX_REACH || std::abs(a.d2) > MOTO_MAX_REACH) return MOTO_ERR_ARG;
+    if (!std::isfinite(a.J) || !std::isfinite(a.D[0]) || !std::isfinite(a.D[1]) || !std::isfinite(a.D[2]))
+      return MOTO_ERR_ARG;
+    reach = std::max(reach, std::max(std::abs(a.d1), std::abs(a.d2)));
+    // closure: the reversed pair with the same J and the opposite D
+    int partners = 0;
+    for (int q = 0; q < n; ++q) {
+      const moto_pair& b = pairs[q];
+      if (b.d1 == -a.d1 && b.d2 == -a.d2 && b.J == a.J && b.D[0] == -a.D[0] && b.D[1] == -a.D[1] &&
+          b.D[2] == -a.D[2])
+        ++partners;
+    }
+    int same = 0;
+    for (int q = 0; q < n; ++q)
+      if (pairs[q].d1 == a.d1 && pairs[q].d2 == a.d2) ++same;
+    if (partners != 1 || same != 1) return MOTO_ERR_ARG;
+    double* r = rec.data() + 6 * (size_t)p;
+    r[0] = a.d1;
+    r[1] = a.d2;
+    r[2] = a.J;
+    r[3] = a.D[0];
+    r[4] = a.D[1];
+    r[5] = a.D[2];
+  }
+  if (n > 0 && (c->md.L1 < 2 * reach + 1 || c->md.L2 < 2 * reach + 1)) return MOTO_ERR_ARG;
+  if (n > 0 && cudaMemcpy(c->pairs, rec.data(), rec.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return MOTO_ERR_CUDA;
+  c->md.pairs = n > 0 ? c->pairs : nullptr;
+  c->md.npairs = n;
+  c->md.reach = reach;
+  return MOTO_OK;
 }
 
 size_t moto_workspace_bytes(const moto_ctx* c) { return c ? c->bytes : 0; }

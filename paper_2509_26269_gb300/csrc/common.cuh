@@ -15,11 +15,16 @@ constexpr int kSMs = 152;             // GB300: 2 dies x 76 SMs
 constexpr int kStreamBlocks = 2 * kSMs;  // persistent-style grid of the vector kernels
 
 // Device copy of the model.  Shell offsets are compile-time constants in
-// stencil.cuh; only strengths and sizes travel here.
+// stencil.cuh; only strengths and sizes travel here.  A general pair-list
+// model (npairs > 0) replaces the shells and the Neel DMI: pairs holds
+// npairs records [d1, d2, J, Dx, Dy, Dz] in device memory, reach the largest
+// |d1|, |d2| (kernels_pairs.cu).
 struct ModelDev {
   int L1, L2, N, n_shells;
   double J[3];
   double D, K, muB;
+  const double* pairs = nullptr;
+  int npairs = 0, reach = 0;
 };
 
 // Status bits written by kernels into the context's status word.

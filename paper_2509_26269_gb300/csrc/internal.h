@@ -33,6 +33,15 @@ struct DevState {
 };
 
 int tile_blocks(const ModelDev& md);
+int pair_blocks(const ModelDev& md);
+// pair-list stencils (kernels_pairs.cu); launch_energy_grad, launch_hvp and
+// launch_euclid_hvp forward to them when md.npairs > 0
+template <typename T>
+void launch_pair_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
+                             double* out, int* status, bool fp64_arith, bool euclid, cudaStream_t st);
+template <typename T>
+void launch_pair_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
+                     int nvec, bool euclid, const int* gate, int mask, cudaStream_t st);
 
 // euclid: g receives grad E itself instead of the Riemannian gradient
 template <typename T>

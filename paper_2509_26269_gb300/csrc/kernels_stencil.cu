@@ -263,6 +263,10 @@ int tile_blocks(const ModelDev& md) {
 template <typename T>
 void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
                         int* status, bool fp64_arith, cudaStream_t st, bool euclid) {
+  if (md.npairs > 0) {
+    launch_pair_energy_grad<T>(md, m, g, s, part, counter, out, status, fp64_arith, euclid, st);
+    return;
+  }
   const int e = euclid ? 1 : 0;
   if (fp64_arith)
     energy_grad_kernel<T, double><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e);
@@ -272,12 +276,20 @@ void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part
 
 template <typename T>
 void launch_euclid_hvp(const ModelDev& md, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec, cudaStream_t st) {
+  if (md.npairs > 0) {
+    launch_pair_hvp<T>(md, nullptr, nullptr, V, ldv, HV, ldhv, nvec, true, nullptr, 0, st);
+    return;
+  }
   euclid_hvp_kernel<T><<<tile_grid(md), kThreads, 0, st>>>(md, V, ldv, HV, ldhv, nvec);
 }
 
 template <typename T>
 void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec,
                 const int* gate, int mask, cudaStream_t st) {
+  if (md.npairs > 0) {
+    launch_pair_hvp<T>(md, m, s, V, ldv, HV, ldhv, nvec, false, gate, mask, st);
+    return;
+  }
   launch_hvp_strip<T>(md, m, s, V, ldv, HV, ldhv, nvec, gate, mask, st);
 }
 
