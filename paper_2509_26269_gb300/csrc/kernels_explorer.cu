@@ -20,6 +20,8 @@ constexpr int kTE = 128;      // elements per staged tile
 constexpr int kSX = kTE + 1;  // staged row stride: rows of one column fall in different banks
 constexpr int kFlushT = 32;   // tiles between FP32 -> FP64 promotions
 constexpr int kPThreads = 256;
+// staged values per thread per tile: populations of up to 24 / up to 64
+constexpr int kPrefetchSmall = 24 * kTE / kPThreads, kPrefetchLarge = 4 * ((MOTO_MAX_POP + 3) / 4) * kTE / kPThreads;
 }  // namespace
 
 template <typename T>
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) perturb_kernel(const T* __restrict__
   }
 }
 
-template <typename T>
+template <typename T, int kPrefetch>
 __global__ void __launch_bounds__(kPThreads) pairwise_l1_kernel(const T* __restrict__ X, size_t ldx, int P,
                                                                 size_t n, double* part, unsigned* counter,
                                                                 double* D) {
@@ -93,15 +95,34 @@ __global__ void __launch_bounds__(kPThreads) pairwise_l1_kernel(const T* __restr
       dacc[r][c] = 0.0;
     }
   const size_t ntiles = (n + kTE - 1) / kTE;
+  const int total = 4 * nb * kTE;  // staged values per tile, <= kPrefetch * kPThreads
+  // the next tile's values wait in registers while the current one is used
+  T nxt[kPrefetch];
+  auto fetch = [&](size_t t) {
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int idx = tid + u * kPThreads;
+      if (idx < total) {
+        const int a = idx / kTE, e = idx - a * kTE;
+        const size_t g = t * kTE + e;
+        nxt[u] = (a < P && g < n) ? X[(size_t)a * ldx + g] : (T)0;
+      }
+    }
+  };
+  if (blockIdx.x < ntiles) fetch(blockIdx.x);
   int since = 0;
   for (size_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     __syncthreads();
-    for (int idx = tid; idx < 4 * nb * kTE; idx += blockDim.x) {
-      const int a = idx / kTE, e = idx - a * kTE;
-      const size_t g = t * kTE + e;
-      Xs[a * kSX + e] = (a < P && g < n) ? X[(size_t)a * ldx + g] : (T)0;
+#pragma unroll
+    for (int u = 0; u < kPrefetch; ++u) {
+      const int idx = tid + u * kPThreads;
+      if (idx < total) {
+        const int a = idx / kTE, e = idx - a * kTE;
+        Xs[a * kSX + e] = nxt[u];
+      }
     }
     __syncthreads();
+    if (t + gridDim.x < ntiles) fetch(t + gridDim.x);
     if (active) {
       for (int e = slice; e < kTE; e += nsl) {
         T xa[4], xb[4];
@@ -193,7 +214,10 @@ bool launch_pairwise_l1(const T* X, size_t ldx, int P, size_t n, double* part, s
   smem = std::max(smem, (size_t)nent * sizeof(double));
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(pairwise_l1_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(pairwise_l1_kernel<T, kPrefetchSmall>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         96 * 1024);
+    cudaFuncSetAttribute(pairwise_l1_kernel<T, kPrefetchLarge>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         96 * 1024);
     attr = true;
   }
   if (smem > 96 * 1024) return false;
@@ -201,7 +225,10 @@ bool launch_pairwise_l1(const T* X, size_t ldx, int P, size_t n, double* part, s
   size_t g = std::min<size_t>(ntiles, (size_t)kSMs * 2);
   g = std::min<size_t>(g, part_cap / (size_t)nent);
   if (g < 1) return false;
-  pairwise_l1_kernel<T><<<(int)g, kPThreads, smem, st>>>(X, ldx, P, n, part, counter, D);
+  if (4 * nb * kTE <= kPrefetchSmall * kPThreads)
+    pairwise_l1_kernel<T, kPrefetchSmall><<<(int)g, kPThreads, smem, st>>>(X, ldx, P, n, part, counter, D);
+  else
+    pairwise_l1_kernel<T, kPrefetchLarge><<<(int)g, kPThreads, smem, st>>>(X, ldx, P, n, part, counter, D);
   return true;
 }
 
