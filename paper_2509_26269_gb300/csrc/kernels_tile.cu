@@ -33,11 +33,14 @@
 // sum; per 16-byte chunk it loads its R rows of X and CW rows of Y and
 // multiplies them with packed FP32 FMAs (fma.rn.f32x2).  Update layout (modes
 // 1-3): a lane owns TB / 64 bytes of the tile of all 8 columns and loops over
-// the rows of X with one load of X and broadcast loads of the C row.  FP32 partial sums are promoted to FP64 every
-// 512 elements of a lane's share; warp and block partials are summed in FP64
-// in a fixed order, the block partials by the last block.  All waits are
+// the rows of X with one load of X and broadcast loads of the C row.  FP32
+// partial sums are flushed every 512 elements of a lane's share into a second
+// FP32 total (a lane sees a few thousand elements, so a few tens of flushes);
+// lane, warp and block totals are summed in FP64 in a fixed order, the block
+// partials by the last block.  All waits are
 // bounded (timeouts are reported, never hung).
 #include <cuda.h>
+#include <type_traits>
 #include <cudaTypedefs.h>
 
 #include "internal.h"
@@ -313,9 +316,12 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
 
   // FP64 totals of the lane's outputs (Gram layout, FP32) or of the self-Gram
   // entries (update layout)
-  double dacc[ND];
+  // FP32 fields: a second FP32 level collects the flushed partial sums (a
+  // lane sees at most a few tens of flushes); FP64 fields accumulate here
+  typedef typename std::conditional<kF32, float, double>::type DT;
+  DT dacc[ND];
 #pragma unroll
-  for (int i = 0; i < ND; ++i) dacc[i] = 0.0;
+  for (int i = 0; i < ND; ++i) dacc[i] = (DT)0;
   Acc acc[NS][NR][NC];
 #pragma unroll
   for (int s2 = 0; s2 < NS; ++s2)
@@ -483,8 +489,8 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
           for (int i = 0; i < NR; ++i)
 #pragma unroll
             for (int j = 0; j < NC; ++j) {
-              double a = TT::to_d(acc[0][i][j]);
-              if (NS == 2) a += TT::to_d(acc[NS - 1][i][j]);
+              DT a = (DT)acc[0][i][j].x + (DT)acc[0][i][j].y;
+              if (NS == 2) a += (DT)acc[NS - 1][i][j].x + (DT)acc[NS - 1][i][j].y;
               dacc[i * NC + j] += a;
               acc[0][i][j] = TT::zero();
               acc[NS - 1][i][j] = TT::zero();
@@ -492,7 +498,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         } else if constexpr (MODE >= 2 && kF32) {
 #pragma unroll
           for (int q = 0; q < kSelf; ++q) {
-            dacc[q] += (double)sacc[q];
+            dacc[q] += (DT)sacc[q];
             sacc[q] = 0.f;
           }
         }
@@ -506,7 +512,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     }
     if constexpr (MODE >= 2 && kF32) {
 #pragma unroll
-      for (int q = 0; q < kSelf; ++q) dacc[q] += (double)sacc[q];
+      for (int q = 0; q < kSelf; ++q) dacc[q] += (DT)sacc[q];
     }
   }
   __syncthreads();
@@ -534,7 +540,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
           const int r = rl + NRL * i, c = cl * CW + j;
           double v = TT::to_d(acc[0][i][j]);
           if (NS == 2) v += TT::to_d(acc[NS - 1][i][j]);
-          if constexpr (kF32) v += dacc[i * NC + j];
+          if constexpr (kF32) v += (double)dacc[i * NC + j];
           // the KS lanes of an output, in a fixed order
 #pragma unroll
           for (int o = NRL * NCG; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -546,7 +552,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
       for (int c1 = 0; c1 < 8; ++c1)
 #pragma unroll
         for (int c2 = c1; c2 < 8; ++c2, ++q) {
-          double v = dacc[q];
+          double v = (double)dacc[q];
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
           if (lane == 0 && c2 < ny) {
