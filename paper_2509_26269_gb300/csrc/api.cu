@@ -303,10 +303,17 @@ constexpr size_t kDsmSize = kCg + 12;
 
 constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
 
-#define CK(x)                                 \
-  do {                                        \
-    cudaError_t e_ = (x);                     \
-    if (e_ != cudaSuccess) return MOTO_ERR_CUDA; \
+// A failed CUDA call makes the entry point return MOTO_ERR_CUDA; with the
+// environment variable MOTO_DEBUG set, its error string and site go to stderr.
+inline int cuda_fail(cudaError_t e, const char* what, int line) {
+  static const bool dbg = getenv("MOTO_DEBUG") != nullptr;
+  if (dbg) fprintf(stderr, "moto: %s failed at api.cu:%d: %s\n", what, line, cudaGetErrorString(e));
+  return MOTO_ERR_CUDA;
+}
+#define CK(x)                                                    \
+  do {                                                           \
+    cudaError_t e_ = (x);                                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x, __LINE__);   \
   } while (0)
 
 inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
@@ -916,7 +923,8 @@ int run_opt(moto_ctx* c, T* m, const moto_params* p, T* V, double* trace, int ch
   for (int t = 0; t <= max_steps; ++t) {
     double* o = trace ? trace + 6 * (size_t)t : c->dsm + kTmp;
     opt_step<T>(c, m, p, V, o, nullptr, ascent, t < max_steps, st);
-    if (cudaGetLastError() != cudaSuccess) return MOTO_ERR_CUDA;
+    const cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) return cuda_fail(le, "a launch of the outer step", __LINE__);
     if ((t + 1) % check_every == 0 || t == max_steps) {
       int rc = read_state(c, &h, st);
       if (rc) return rc;
@@ -1315,11 +1323,12 @@ int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double
     cudaError_t ce = cudaStreamEndCapture(b->master, &graph);
     if (rc || ce != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
-      return rc ? rc : MOTO_ERR_CUDA;
+      return rc ? rc : cuda_fail(ce, "cudaStreamEndCapture", __LINE__);
     }
-    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
       cudaGraphDestroy(graph);
-      return MOTO_ERR_CUDA;
+      return cuda_fail(ce, "cudaGraphInstantiate", __LINE__);
     }
   }
   int rc = MOTO_OK;
@@ -1336,8 +1345,9 @@ int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double
         if (!b->flags_host[3 * i] && !status_of(b->flags_host[3 * i + 1])) all = false;
       if (all || t >= max_steps) break;
     }
-    if (cudaGraphLaunch(exec, b->master) != cudaSuccess) {
-      rc = MOTO_ERR_CUDA;
+    const cudaError_t le = cudaGraphLaunch(exec, b->master);
+    if (le != cudaSuccess) {
+      rc = cuda_fail(le, "cudaGraphLaunch", __LINE__);
       break;
     }
     ++t;

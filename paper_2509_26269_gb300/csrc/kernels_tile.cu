@@ -51,7 +51,11 @@ namespace moto {
 using namespace tma;
 
 namespace {
-constexpr int kPairs = 5;  // consumer warp pairs per block
+// consumer warp pairs per block: with the producer 11 warps, at most three on
+// one scheduler, so 168 registers a thread still fit its quarter of the
+// register file (six pairs would put four warps on one scheduler and cap the
+// threads at 128 registers)
+constexpr int kPairs = 5;
 constexpr int kConsumers = 2 * kPairs;
 constexpr int kThrT = 32 * (kConsumers + 1);
 // 9 warps per block: three of them share one scheduler's 64 KB register file
