@@ -26,6 +26,8 @@
  *   any launch.  Errors detected on the device (non-finite values, a Krylov
  *   breakdown, a timeout of a bounded wait) are written to the context's
  *   device status word and returned by moto_status(); they never trap.
+ *   MOTO_ERR_CUDA names no cause; with the environment variable MOTO_DEBUG
+ *   set, the failing CUDA call and its error string are printed to stderr.
  * Units.  Energies and model parameters in meV, forces (torques) in meV/rad,
  *   eigenvalues in meV (per rad^2), angles in rad.
  */
