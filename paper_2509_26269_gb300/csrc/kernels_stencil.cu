@@ -50,7 +50,9 @@ __global__ void __launch_bounds__(kThreads) energy_grad_kernel(ModelDev md, cons
   load_tile(m, md.N, md.L1, md.L2, x0, y0, tile);
   __syncthreads();
   const int lx = threadIdx.x & 31, wy = threadIdx.x >> 5;
-  double esum = 0.0, gmax = 0.0;
+  // the thread's few sites are summed in the arithmetic precision A, the
+  // block and the grid in FP64
+  A esumA = (A)0, gmaxA = (A)0;
   bool bad = false;
   const size_t N = md.N;
 #pragma unroll
@@ -74,11 +76,12 @@ __global__ void __launch_bounds__(kThreads) energy_grad_kernel(ModelDev md, cons
         g[2 * N + i] = (T)gzv;
       }
       if (s) s[i] = (T)si;
-      esum += 0.5 * ((double)si - md.muB * (double)mz);
-      gmax = fmax(gmax, (double)(gxv * gxv + gyv * gyv + gzv * gzv));
+      esumA += (A)0.5 * (si - (A)md.muB * mz);
+      gmaxA = fmax(gmaxA, gxv * gxv + gyv * gyv + gzv * gzv);
       bad |= !finite3(gxv, gyv, gzv);
     }
   }
+  double esum = (double)esumA, gmax = (double)gmaxA;
   __shared__ double red[16];
   double v[1] = {esum};
   block_sum<1>(v, red);

@@ -1187,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict
   __shared__ T a[MOTO_MAX_K];
   if (threadIdx.x < MOTO_MAX_K) a[threadIdx.x] = (int)threadIdx.x < nv ? (T)(2.0 * dots[threadIdx.x]) : (T)0;
   __syncthreads();
-  double mx = 0.0;
+  T mxt = (T)0;  // the largest |G_i|^2 in the field precision (a max is exact)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     T r[3];
 #pragma unroll
@@ -1198,10 +1198,10 @@ __global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict
       r[c] = v;
       G[e] = v;
     }
-    mx = fmax(mx, (double)(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]));
+    mxt = fmax(mxt, r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
   }
   __shared__ double red[8];
-  mx = block_max(mx, red);
+  double mx = block_max((double)mxt, red);
   if (threadIdx.x == 0) part[blockIdx.x] = mx;
   if (!grid_last_block(counter)) return;
   double b = 0.0;
@@ -1452,7 +1452,7 @@ __global__ void __launch_bounds__(kThreads) lbfgs_direction_kernel(const T* __re
   __shared__ T cf[2 * MOTO_MAX_MEM + 3];
   if (threadIdx.x < nb) cf[threadIdx.x] = (T)coef[threadIdx.x];
   __syncthreads();
-  double mx = 0.0;
+  T mxt = (T)0;  // the largest |d_i|^2 in the field precision (a max is exact)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     T a[3] = {0, 0, 0};
     for (int t = 0; t < nb; ++t) {
@@ -1471,10 +1471,10 @@ __global__ void __launch_bounds__(kThreads) lbfgs_direction_kernel(const T* __re
     d[i] = a[0];
     d[N + i] = a[1];
     d[2 * (size_t)N + i] = a[2];
-    mx = fmax(mx, (double)(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]));
+    mxt = fmax(mxt, a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
   }
   __shared__ double red[8];
-  mx = block_max(mx, red);
+  double mx = block_max((double)mxt, red);
   if (threadIdx.x == 0) part[blockIdx.x] = mx;
   if (!grid_last_block(counter)) return;
   double b = 0.0;
