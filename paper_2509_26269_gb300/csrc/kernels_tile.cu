@@ -1,6 +1,6 @@
 // Streaming kernels of the block-Krylov reorthogonalisation over element
 // tiles.  The fields of X (nx <= 96) and of Y (ny <= 8) are equally strided, so
-// each operand is a 2D tensor [fields][n].  A tile is TB bytes (256 or 512) of
+// each operand is a 2D tensor [fields][n].  A tile is TB bytes (256 to 1024) of
 // every field, moved by one TMA load per operand (cp.async.bulk.tensor.2d,
 // box [fields][TB]) into a dense [fields][TB] shared-memory stage; the TMA
 // unit zero-fills elements past n.  Rows of at least 256 contiguous bytes keep
@@ -58,10 +58,9 @@ namespace {
 constexpr int kPairs = 5;
 constexpr int kConsumers = 2 * kPairs;
 constexpr int kThrT = 32 * (kConsumers + 1);
-// 9 warps per block: three of them share one scheduler's 64 KB register file
 #define MOTO_TILE_MAXREG 168
 constexpr int kMaxStages = 32;
-constexpr int kFlushE = 512;  // elements between FP32 -> FP64 promotions
+constexpr int kFlushE = 512;  // elements between flushes of the FP32 partial sums
 constexpr int kSelf = 36;  // upper-triangle entries of an 8 x 8 Gram
 constexpr size_t kDynBudget = 219 * 1024;  // dynamic shared memory of the ring (1 KB of it alignment slack)
 
@@ -261,7 +260,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   constexpr int HB = TB / 2;  // bytes of a row a warp of the pair owns
   constexpr int EL = TE / 64;  // elements of a lane in the update layout
   constexpr int NCH = HB / 16;  // 16-byte chunks of a half row
-  static_assert(EL == 1 || EL == 2 || (EL == 4 && MODE == 0), "a lane owns 4 to 16 bytes of a row");
+  static_assert(EL == 1 || EL == 2 || (EL == 4 && MODE <= 1), "a lane owns 4 to 16 bytes of a row");
   static_assert(EL * (int)sizeof(T) >= 4 && EL * (int)sizeof(T) <= 16, "lane share");
   constexpr bool kGramMode = (MODE <= 1);
   constexpr bool kF32 = sizeof(T) == 4;
@@ -270,6 +269,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   // the chunks of a tile (KS lanes per output, summed at the end)
   constexpr int NCG = 8 / CW, KS = 32 / (NRL * NCG);
   static_assert(KS >= 1 && NRL * NCG * KS == 32, "Gram lane layout");
+  static_assert(NRL * NCG >= 8, "the KS lanes of an output share their chunk skew (lane & 7)");
   constexpr int NS = (kF32 && NR * NC <= 8) ? 2 : 1;  // accumulator sets
   constexpr int ND = kGramMode ? (kF32 ? NR * NC : 1) : kSelf;  // FP64 totals
   constexpr int kFlushT = kFlushE / (TE / 2);
@@ -475,7 +475,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         // chunks of the tile (every KS-th), its walk starting at chunk `skew`
         // (the KS lanes of an output share the skew, so together they cover
         // every chunk once)
-#pragma unroll 4
+#pragma unroll 8
         for (int k = ks; k < NCH; k += KS) {
           const uint32_t co = sb + hoff + (uint32_t)(((k + skew) & (NCH - 1)) << 4);
           VT xv[NR], yw[NC];
@@ -610,16 +610,18 @@ bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld, in
          CUDA_SUCCESS;
 }
 
-// Row bytes of a tile: 512 while eight stages still fit (few fields: a copy
-// then moves enough bytes to stay at full rate), else 256; FP64 always 512
-// (a lane's share is one element).  A Gram of at most 16 x 8 fields (FP32)
-// takes 1024-byte rows: one stage is then one tile of two copies of 8 KB or
-// more (stages of several small copies stream more slowly).
+// Row bytes of a tile.  FP64: 512 (a lane's share is one element).  FP32: a
+// Gram of at most 24 x 8 fields takes 1024-byte rows (one stage is then one
+// tile of two copies of 8 KB or more; stages of several small copies stream
+// more slowly); otherwise 512 while every consumer pair can still hold a stage
+// of its own (fewer, larger stages stream faster than more 256-byte ones),
+// else 256.
 template <typename T>
 int tile_bytes(int mode, int nx, int ny) {
   if (sizeof(T) == 8) return 512;
-  if (mode == 0 && nx <= 16 && ny <= 8) return 1024;
-  return ((nx + 7) / 8 * 8 + 8) * 512 * 8 <= (int)kDynBudget - 1024 ? 512 : 256;
+  if (mode <= 1 && nx <= 24 && ny <= 8) return 1024;
+  const int rows = (nx + 7) / 8 * 8 + (mode == 3 ? 0 : 8);
+  return (size_t)rows * 512 * kPairs <= kDynBudget - 1024 ? 512 : 256;
 }
 
 template <typename T, int MODE, int R, int CW, int NRL, int TB>
@@ -654,25 +656,56 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
                                                                     part, counter, nst, tps, gate, mask, status);
 }
 
+// Gram lane layouts (R rows x CW columns a lane, NRL row lanes): FP32 fits
+// the rows exactly where registers allow (NRL x R = the fields rounded up to
+// 8; padded rows cost their loads and FMAs like real ones), and only the
+// layouts that a row size can meet are instantiated for it.
 template <typename T, int MODE, int TB>
 void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
-                   const double* C, const double* Cadd, int uadd, int nadd, T* Yout, size_t ldo, double* out, double* part, unsigned* counter,
-                   const int* gate, int mask, int* status, cudaStream_t st) {
+                   const double* C, const double* Cadd, int uadd, int nadd, T* Yout, size_t ldo, double* out,
+                   double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st) {
 #define TL(RR, CC, NN)                                                                                           \
-  tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, gate, mask, \
-                                       status, st)
+  tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part,    \
+                                       counter, gate, mask, status, st)
+  const int nxp = (nx + 7) & ~7;
   if constexpr (MODE >= 2) {
     TL(1, 4, 16);
-  } else if (nx <= 8) {
-    TL(1, 2, 8);
-  } else if (nx <= 16) {
-    TL(4, 4, 4);
-  } else if (nx <= 32) {
-    TL(4, 4, 8);
-  } else if (nx <= 64) {
-    TL(4, 4, 16);
+  } else if constexpr (sizeof(T) == 8) {
+    if (nxp <= 8) {
+      TL(1, 2, 8);
+    } else if (nxp <= 16) {
+      TL(4, 4, 4);
+    } else if (nxp <= 32) {
+      TL(4, 4, 8);
+    } else if (nxp <= 64) {
+      TL(4, 4, 16);
+    } else {
+      TL(6, 4, 16);
+    }
+  } else if constexpr (TB == 1024) {  // at most 24 fields
+    if (nxp <= 8) {
+      TL(2, 4, 4);
+    } else if (nxp <= 16) {
+      TL(4, 4, 4);
+    } else {
+      TL(3, 4, 8);
+    }
+  } else if constexpr (TB == 512) {  // up to 72 fields
+    switch (nxp) {
+      case 8: case 16: case 24: case 32: TL(4, 4, 8); break;
+      case 40: TL(5, 4, 8); break;
+      case 48: TL(6, 4, 8); break;
+      case 56: TL(7, 4, 8); break;
+      case 64: TL(4, 4, 16); break;
+      case 72: case 80: TL(5, 4, 16); break;
+      default: TL(6, 4, 16); break;
+    }
   } else {
-    TL(6, 4, 16);
+    if (nxp <= 80) {
+      TL(5, 4, 16);
+    } else {
+      TL(6, 4, 16);
+    }
   }
 #undef TL
 }
@@ -712,7 +745,10 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
     }
   } else {
     if (tb == 1024) {
-      TD(0, 1024);
+      if (mode == 0)
+        TD(0, 1024);
+      else
+        TD(1, 1024);
       return true;
     }
     switch (mode * 2 + (tb == 512 ? 1 : 0)) {
