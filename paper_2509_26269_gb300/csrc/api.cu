@@ -298,7 +298,7 @@ constexpr size_t kLobM = kLobG + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 3K
 constexpr size_t kLobC = kLobM + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 2K coefficient blocks
 constexpr size_t kLobAux = kLobC + 6 * MOTO_MAX_K * MOTO_MAX_K;    // 64 aux
 constexpr size_t kMmfDots = kLobAux + 64 * MOTO_MAX_K;             // MAX_K: g . V_c (subspace force)
-constexpr size_t kCg = kMmfDots + MOTO_MAX_K;                      // 12: CG dots and coefficients
+constexpr size_t kCg = kMmfDots + MOTO_MAX_K;                      // 12: Gram of [G, s, y], |G_prev|^2, beta, alpha
 constexpr size_t kDsmSize = kCg + 12;
 
 constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
@@ -852,10 +852,12 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
   T* s = static_cast<T*>(c->s);
   const int R = p->lbfgs_mem + 1, nb = 2 * R + 1;
   T* ring = static_cast<T*>(c->ring);
+  // ring fields: the 2R pair slots, then G, the staged candidate pair (so
+  // that G, s, y are three equally strided fields), G_prev and d
   T* Gcur = ring + (size_t)(2 * R) * ld;
-  T* Gprev = Gcur + ld;
+  T* stage = Gcur + ld;
+  T* Gprev = stage + 2 * ld;
   T* d = Gprev + ld;
-  T* stage = d + ld;
   double* D = c->dsm;
   int* gate = &c->st->gate;
   const int md = kGateDone;
@@ -876,14 +878,12 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
   if (!update) return;
   if (p->optimizer == MOTO_OPT_CG) {
     // nonlinear CG: the pair s = P d_prev, y = G - P G_prev (staging fields),
-    // the pair's Gram, G.G and y.G, beta and the spectral step, then the
+    // one Gram of [G, s, y], beta and the spectral step, then the
     // direction, the restart test and the capped step; p lives in the last
     // ring field (the pair kernel writes ring slot 0 only while CG runs)
     T* pdir = ring + (size_t)(2 * R - 1) * ld;
     P_lbfgs_pair<T>(c, m, d, Gprev, Gcur, ring, ld, stage, c->st, N, gate, md, st);
-    P_gram<T>(c, stage, ld, 2, stage, ld, 2, n3, D + kCg, c->part, c->counter, gate, md, st);
-    P_gram<T>(c, Gcur, ld, 1, Gcur, ld, 1, n3, D + kCg + 4, c->part, c->counter, gate, md, st);
-    P_gram<T>(c, stage + ld, ld, 1, Gcur, ld, 1, n3, D + kCg + 5, c->part, c->counter, gate, md, st);
+    P_gram<T>(c, Gcur, ld, 3, Gcur, ld, 3, n3, D + kCg, c->part, c->counter, gate, md, st);
     P_cg_coeffs(c, D + kCg, p->gamma0, c->st, st);
     P_cg_direction<T>(c, m, Gcur, pdir, N, D + kCg, p->theta_max, c->part, c->counter, c->st, gate, md, st);
     P_cg_retract<T>(c, m, Gcur, pdir, d, c->st, N, gate, md, st);
@@ -891,8 +891,7 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
     return;
   }
   P_lbfgs_pair<T>(c, m, d, Gprev, Gcur, ring, ld, stage, c->st, N, gate, md, st);
-  P_gram<T>(c, ring, ld, nb, stage, ld, 2, n3, D + kLbNew, c->part, c->counter, gate, md, st);
-  P_gram<T>(c, ring, ld, nb, Gcur, ld, 1, n3, D + kLbNew + 2 * nb, c->part, c->counter, gate, md, st);
+  P_gram<T>(c, ring, ld, nb, Gcur, ld, 3, n3, D + kLbNew, c->part, c->counter, gate, md, st);
   P_lbfgs_solve(c, D + kLbM, p->lbfgs_mem, D + kLbNew, p->gamma0, D + kLbCoef, c->st, st);
   P_lbfgs_direction<T>(c, ring, ld, nb, D + kLbCoef, m, d, N, p->theta_max, c->part, c->counter, c->st, gate, md,
                             st);

@@ -150,9 +150,9 @@ void launch_diag(const double* src, int k, int mode, double* out, const DevState
 template <typename T>
 void launch_mmf_force(const T* g, const T* V, size_t ldv, int nv, const double* dots, T* G, int N, double* part,
                       unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st);
-// Nonlinear CG (Polak-Ribiere+).  cg (doubles): [0..3] the Gram of the pair
-// (s.s, s.y, y.s, y.y), [4] G.G, [5] y.G, [6] |G_prev|^2 (kept), [7] beta,
-// [8] step length.  cg_coeffs forms beta and the length and sets
+// Nonlinear CG (Polak-Ribiere+).  cg (doubles): [0..8] the 3 x 3 Gram of
+// [G, s, y] (row-major: G.G at 0, s.s at 4, s.y at 5, y.G at 6, y.y at 8),
+// [9] |G_prev|^2 (kept), [10] beta, [11] step length.  cg_coeffs forms beta and the length and sets
 // lb_have_prev; cg_direction writes p = -G + beta P p (p: the previous
 // direction on entry) and decides restart (pad[2]) and the capped scale;
 // cg_retract takes d = scale * (restart ? -G : p) and retracts.

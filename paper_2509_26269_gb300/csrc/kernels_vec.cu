@@ -1225,13 +1225,13 @@ __global__ void cg_coeffs_kernel(double* cg, double gamma0, DevState* dst) {
   if (threadIdx.x != 0 || (dst->gate & kGateDone)) return;
   double beta = 0.0, alpha = gamma0;
   if (dst->lb_have_prev) {
-    beta = cg[6] > 0.0 ? fmax(0.0, cg[5] / cg[6]) : 0.0;  // G.(G - P G_prev) = G.y
-    const double ss = cg[0], sy = cg[1], yy = cg[3];
+    beta = cg[9] > 0.0 ? fmax(0.0, cg[6] / cg[9]) : 0.0;  // G.(G - P G_prev) = G.y
+    const double ss = cg[4], sy = cg[5], yy = cg[8];
     if (sy > 1e-12 * sqrt(ss * yy)) alpha = sy / yy;
   }
-  cg[7] = beta;
-  cg[8] = alpha;
-  cg[6] = cg[4];  // |G|^2 becomes |G_prev|^2 of the next step
+  cg[10] = beta;
+  cg[11] = alpha;
+  cg[9] = cg[0];  // |G|^2 becomes |G_prev|^2 of the next step
   dst->lb_have_prev = 1;
 }
 
@@ -1245,7 +1245,7 @@ __global__ void __launch_bounds__(kThreads) cg_direction_kernel(const T* __restr
                                                                 double* part, unsigned* counter, DevState* dst,
                                                                 const int* gate, int mask) {
   if (gate && (*gate & mask)) return;
-  const double beta_d = cg[7];
+  const double beta_d = cg[10];
   const T beta = (T)beta_d;
   double v[3] = {0.0, 0.0, 0.0};  // p.G, max |p_i|^2, max |G_i|^2
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -1296,7 +1296,7 @@ __global__ void __launch_bounds__(kThreads) cg_direction_kernel(const T* __restr
   a2 = block_max(a2, red);
   if (threadIdx.x == 0) {
     const bool restart = !(tot[0] < 0.0);  // p is not a descent direction for G
-    const double alpha = cg[8];
+    const double alpha = cg[11];
     const double t = sqrt(restart ? a2 : a1);
     dst->pad[2] = restart ? 1 : 0;
     dst->scale = (alpha * t > theta_max) ? theta_max / t : alpha;
@@ -1358,23 +1358,22 @@ void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G,
 // The ring keeps `lb_count` <= mem accepted pairs in the slots preceding
 // `lb_head`; slot lb_head is free and receives the next candidate pair, so a
 // rejected candidate never evicts a kept pair.  M is the persistent
-// (2R+1)^2 Gram matrix of the basis.  newdots holds, for every basis vector,
-// its dots with the candidate s and y ((2R+1) x 2) followed by its dots with
-// G ((2R+1) x 1).
+// (2R+1)^2 Gram matrix of the basis.  newdots holds, for every basis vector
+// t, its dots with G, the candidate s and the candidate y at 3 t, 3 t + 1 and
+// 3 t + 2.
 __global__ void lbfgs_solve_kernel(double* M, int mem, const double* newdots, double gamma0, double* coef,
                                    DevState* dst) {
   if (dst->gate & kGateDone) return;
   if (threadIdx.x != 0) return;
   const int R = mem + 1;
   const int nb = 2 * R + 1, gi = 2 * R;
-  const double* pd = newdots;
-  const double* gd = newdots + 2 * nb;
+  const double* nd = newdots;
   if (dst->lb_have_prev) {
     const int h = dst->lb_head;
     const int si = 2 * h, yi = 2 * h + 1;
     for (int t = 0; t < nb; ++t) {
-      M[si * nb + t] = M[t * nb + si] = pd[t * 2 + 0];
-      M[yi * nb + t] = M[t * nb + yi] = pd[t * 2 + 1];
+      M[si * nb + t] = M[t * nb + si] = nd[t * 3 + 1];
+      M[yi * nb + t] = M[t * nb + yi] = nd[t * 3 + 2];
     }
     const double sy = M[si * nb + yi], ss = M[si * nb + si], yy = M[yi * nb + yi];
     if (sy > 1e-12 * sqrt(ss * yy)) {
@@ -1382,7 +1381,7 @@ __global__ void lbfgs_solve_kernel(double* M, int mem, const double* newdots, do
       dst->lb_count = min(dst->lb_count + 1, mem);
     }
   }
-  for (int t = 0; t < nb; ++t) M[gi * nb + t] = M[t * nb + gi] = gd[t];
+  for (int t = 0; t < nb; ++t) M[gi * nb + t] = M[t * nb + gi] = nd[t * 3];
   // coefficient-space dot products: u^T M w
   auto dotc = [&](const double* u, const double* w) {
     double a = 0.0;
