@@ -260,7 +260,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   constexpr int HB = TB / 2;  // bytes of a row a warp of the pair owns
   constexpr int EL = TE / 64;  // elements of a lane in the update layout
   constexpr int NCH = HB / 16;  // 16-byte chunks of a half row
-  static_assert(EL == 1 || EL == 2 || (EL == 4 && MODE <= 1), "a lane owns 4 to 16 bytes of a row");
+  static_assert(EL == 1 || EL == 2 || (EL == 4 && MODE <= 2), "a lane owns 4 to 16 bytes of a row");
   static_assert(EL * (int)sizeof(T) >= 4 && EL * (int)sizeof(T) <= 16, "lane share");
   constexpr bool kGramMode = (MODE <= 1);
   constexpr bool kF32 = sizeof(T) == 4;
@@ -610,18 +610,18 @@ bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld, in
          CUDA_SUCCESS;
 }
 
-// Row bytes of a tile.  FP64: 512 (a lane's share is one element).  FP32: a
-// Gram of at most 24 x 8 fields takes 1024-byte rows (one stage is then one
-// tile of two copies of 8 KB or more; stages of several small copies stream
-// more slowly); otherwise 512 while every consumer pair can still hold a stage
-// of its own (fewer, larger stages stream faster than more 256-byte ones),
-// else 256.
+// Row bytes of a tile.  FP64: 512 (a lane's share is one element).  FP32: the
+// largest of 1024, 512 and 256 at which every consumer pair can still hold a
+// stage of its own (fewer, larger stages stream faster), 1024 only for Grams
+// (modes 0, 1) and for the update of 9 to 16 fields (mode 2), where it was
+// measured faster (larger updates stream as fast at 512).
 template <typename T>
 int tile_bytes(int mode, int nx, int ny) {
   if (sizeof(T) == 8) return 512;
-  if (mode <= 1 && nx <= 24 && ny <= 8) return 1024;
   const int rows = (nx + 7) / 8 * 8 + (mode == 3 ? 0 : 8);
-  return (size_t)rows * 512 * kPairs <= kDynBudget - 1024 ? 512 : 256;
+  auto fits = [&](int tb) { return (size_t)rows * tb * kPairs <= kDynBudget - 1024; };
+  if ((mode <= 1 || (mode == 2 && nx > 8 && nx <= 16)) && ny <= 8 && fits(1024)) return 1024;
+  return fits(512) ? 512 : 256;
 }
 
 template <typename T, int MODE, int R, int CW, int NRL, int TB>
@@ -682,13 +682,15 @@ void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny,
     } else {
       TL(6, 4, 16);
     }
-  } else if constexpr (TB == 1024) {  // at most 24 fields
+  } else if constexpr (TB == 1024) {  // at most 32 fields
     if (nxp <= 8) {
       TL(2, 4, 4);
     } else if (nxp <= 16) {
       TL(4, 4, 4);
-    } else {
+    } else if (nxp <= 24) {
       TL(3, 4, 8);
+    } else {
+      TL(4, 4, 8);
     }
   } else if constexpr (TB == 512) {  // up to 72 fields
     switch (nxp) {
@@ -747,8 +749,10 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
     if (tb == 1024) {
       if (mode == 0)
         TD(0, 1024);
-      else
+      else if (mode == 1)
         TD(1, 1024);
+      else
+        TD(2, 1024);
       return true;
     }
     switch (mode * 2 + (tb == 512 ? 1 : 0)) {
