@@ -36,9 +36,10 @@
 // the rows of X with one load of X and broadcast loads of the C row.  FP32
 // partial sums are flushed every 512 elements of a lane's share into a second
 // FP32 total (a lane sees a few thousand elements, so a few tens of flushes);
-// lane, warp and block totals are summed in FP64 in a fixed order, the block
-// partials by the last block.  All waits are
-// bounded (timeouts are reported, never hung).
+// lane, warp, block and grid totals are summed in a fixed order in two-float
+// arithmetic (FP64 for FP64 fields), the block partials by the last block.
+// All waits are bounded (timeouts are reported, never hung).
+#include <algorithm>
 #include <cuda.h>
 #include <type_traits>
 #include <cudaTypedefs.h>
@@ -202,6 +203,63 @@ struct TileT<double> {
   static __device__ __forceinline__ double to_d(const Acc& a) { return a; }
   static __device__ __forceinline__ double2 lds128(uint32_t a) { return lds128d(a); }
 };
+
+// Two-float numbers hi + lo (|lo| <= ulp(hi) / 2) and their sum after
+// Knuth's TwoSum (the rounding error of hi + hi carried into lo): about 44
+// significant bits in FP32 instructions.  The epilogue sums (thousands of
+// additions a block, tens of thousands in the last block) use them for FP32
+// fields instead of FP64, whose pipe on GB300 is a small fraction of FP32's.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_of(float a) { return F2{a, 0.f}; }
+__device__ __forceinline__ F2 radd(F2 a, F2 b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return F2{hi, e - (hi - s)};
+}
+__device__ __forceinline__ double radd(double a, double b) { return a + b; }
+__device__ __forceinline__ F2 rshfl(F2 a, int o) {
+  return F2{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ double rshfl(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+
+// Last block: out[j] = sum over the blocks b of part[b * nv + j] (two-float),
+// in an order fixed by (nb, nv, blockDim): C chunks of consecutive blocks per
+// entry (C = blockDim / nv, 1 to 8) are summed by separate threads with eight
+// loads in flight, then the chunks in order.  scratch: C * nv entries.
+__device__ __forceinline__ void grid_sum_f2(const F2* part, int nb, int nv, double* out, F2* scratch) {
+  int C = (int)blockDim.x / nv;
+  C = C < 1 ? 1 : (C > 8 ? 8 : C);
+  const int S = (nb + C - 1) / C;
+  for (int t = threadIdx.x; t < nv * C; t += blockDim.x) {
+    const int j = t % nv, c = t / nv;
+    const int b1 = min(nb, (c + 1) * S);
+    F2 a = F2{0.f, 0.f};
+    int b = c * S;
+    for (; b + 8 <= b1; b += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(reinterpret_cast<const float2*>(part + (size_t)(b + u) * nv + j));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a = radd(a, F2{v[u].x, v[u].y});
+    }
+    for (; b < b1; ++b) {
+      const float2 v = __ldcg(reinterpret_cast<const float2*>(part + (size_t)b * nv + j));
+      a = radd(a, F2{v.x, v.y});
+    }
+    scratch[t] = a;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    F2 a = scratch[j];
+    for (int c = 1; c < C; ++c) a = radd(a, scratch[c * nv + j]);
+    out[j] = (double)a.hi + (double)a.lo;
+  }
+}
 
 // Update of the lane's EL elements of the 8 columns: y += X[u0 .. u0 + nu) Cs
 // (Cs rows of 8, padded with zeros past ny).  FP32 keeps column pairs,
@@ -530,50 +588,93 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
       }
     __syncthreads();
   }
-  // per-warp partials in the (now idle) ring, then the block partial
+  // Sums in a fixed order: lane totals -> warp -> block partial -> grid
+  // total.  FP32 fields sum in two-float arithmetic (RT = F2), FP64 fields in
+  // FP64; block partials go to `part` as 8-byte RT values.
+  typedef typename std::conditional<kF32, F2, double>::type RT;
   const int nout = na * ny;
-  double* red = reinterpret_cast<double*>(ring_ptr);
-  if (w < kConsumers) {
-    double* rw = red + (size_t)w * nout;
-    if constexpr (kGramMode) {
+  RT* red = reinterpret_cast<RT*>(ring_ptr);  // the ring is idle now
+  RT* rpart = reinterpret_cast<RT*>(part) + (size_t)blockIdx.x * nout;
+  if constexpr (kGramMode) {
+    // per-warp partials, then the block partial over the warps in order
+    if (w < kConsumers) {
+      RT* rw = red + (size_t)w * nout;
       const int rl = lane % NRL, cl = (lane / NRL) % NCG, ks = lane / (NRL * NCG);
 #pragma unroll
       for (int i = 0; i < NR; ++i)
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
           const int r = rl + NRL * i, c = cl * CW + j;
-          double v = TT::to_d(acc[0][i][j]);
-          if (NS == 2) v += TT::to_d(acc[NS - 1][i][j]);
-          if constexpr (kF32) v += (double)dacc[i * NC + j];
+          RT v;
+          if constexpr (kF32) {
+            v = f2_of(dacc[i * NC + j]);
+#pragma unroll
+            for (int s2 = 0; s2 < NS; ++s2) {
+              v = radd(v, f2_of(acc[s2][i][j].x));
+              v = radd(v, f2_of(acc[s2][i][j].y));
+            }
+          } else {
+            v = acc[0][i][j];
+            if (NS == 2) v += acc[NS - 1][i][j];
+          }
           // the KS lanes of an output, in a fixed order
 #pragma unroll
-          for (int o = NRL * NCG; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          for (int o = NRL * NCG; o < 32; o <<= 1) v = radd(v, rshfl(v, o));
           if (ks == 0 && r < na && c < ny) rw[r * ny + c] = v;
         }
-    } else {
-      int q = 0;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+      RT a = red[o];
+      for (int ww = 1; ww < kConsumers; ++ww) a = radd(a, red[(size_t)ww * nout + o]);
+      rpart[o] = a;
+    }
+  } else {
+    // update layout: every lane holds all kSelf entries.  Lane values go to
+    // shared memory; thread (entry, chunk) adds a chunk of kChunkLanes lanes,
+    // then one thread per entry adds the chunks (no cross-lane shuffles)
+    constexpr int kLanes = kConsumers * 32, kChunkLanes = 40, kChunks = kLanes / kChunkLanes;
+    static_assert(kChunks * kChunkLanes == kLanes && kChunks * kSelf <= kThrT, "self-Gram block sum layout");
+    RT* lv = red;                       // [kLanes][kSelf]
+    RT* cs = red + (size_t)kLanes * kSelf;  // [kChunks][kSelf]
+    if (w < kConsumers)
 #pragma unroll
-      for (int c1 = 0; c1 < 8; ++c1)
-#pragma unroll
-        for (int c2 = c1; c2 < 8; ++c2, ++q) {
-          double v = (double)dacc[q];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-          if (lane == 0 && c2 < ny) {
-            rw[c1 * ny + c2] = v;
-            rw[c2 * ny + c1] = v;
-          }
-        }
+      for (int q = 0; q < kSelf; ++q) {
+        if constexpr (kF32)
+          lv[(size_t)(w * 32 + lane) * kSelf + q] = f2_of(dacc[q]);
+        else
+          lv[(size_t)(w * 32 + lane) * kSelf + q] = dacc[q];
+      }
+    __syncthreads();
+    if (threadIdx.x < kChunks * kSelf) {
+      const int q = threadIdx.x % kSelf, ch = threadIdx.x / kSelf;
+      const RT* src = lv + (size_t)ch * kChunkLanes * kSelf + q;
+      RT a = src[0];
+      for (int l = 1; l < kChunkLanes; ++l) a = radd(a, src[(size_t)l * kSelf]);
+      cs[ch * kSelf + q] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < kSelf) {
+      const int q = threadIdx.x;
+      RT a = cs[q];
+      for (int ch = 1; ch < kChunks; ++ch) a = radd(a, cs[ch * kSelf + q]);
+      int c1 = 0, rem = q;
+      while (rem >= 8 - c1) {
+        rem -= 8 - c1;
+        ++c1;
+      }
+      const int c2 = c1 + rem;
+      if (c2 < ny) {
+        rpart[c1 * ny + c2] = a;
+        rpart[c2 * ny + c1] = a;
+      }
     }
   }
-  __syncthreads();
-  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
-    double a = 0.0;
-    for (int ww = 0; ww < kConsumers; ++ww) a += red[(size_t)ww * nout + o];
-    part[(size_t)blockIdx.x * nout + o] = a;
-  }
   if (!grid_last_block(counter)) return;
-  grid_sum_entries(part, gridDim.x, nout, out);
+  if constexpr (kF32)
+    grid_sum_f2(reinterpret_cast<const F2*>(part), gridDim.x, nout, out, red);
+  else
+    grid_sum_entries(part, gridDim.x, nout, out);
   if (threadIdx.x == 0) *counter = 0u;
 }
 
@@ -639,7 +740,10 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   const size_t stage_bytes = tps * tile_b;
   int nst = (int)((kDynBudget - 1024) / stage_bytes);
   if (nst > kMaxStages) nst = kMaxStages;
-  const size_t smem = (size_t)nst * stage_bytes + 1024;
+  // the epilogue reuses the ring for its partial sums (8 bytes an entry)
+  const size_t epi = MODE >= 2 ? (size_t)(kConsumers * 32 + 8) * kSelf * 8
+                               : (size_t)kConsumers * (MODE <= 1 ? nx : ny) * ny * 8;
+  const size_t smem = std::max((size_t)nst * stage_bytes, epi) + 1024;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(tile2d_kernel<T, MODE, R, CW, NRL, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
