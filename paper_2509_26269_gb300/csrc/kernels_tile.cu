@@ -204,63 +204,6 @@ struct TileT<double> {
   static __device__ __forceinline__ double2 lds128(uint32_t a) { return lds128d(a); }
 };
 
-// Two-float numbers hi + lo (|lo| <= ulp(hi) / 2) and their sum after
-// Knuth's TwoSum (the rounding error of hi + hi carried into lo): about 44
-// significant bits in FP32 instructions.  The epilogue sums (thousands of
-// additions a block, tens of thousands in the last block) use them for FP32
-// fields instead of FP64, whose pipe on GB300 is a small fraction of FP32's.
-struct F2 {
-  float hi, lo;
-};
-__device__ __forceinline__ F2 f2_of(float a) { return F2{a, 0.f}; }
-__device__ __forceinline__ F2 radd(F2 a, F2 b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  float e = (a.hi - (s - bb)) + (b.hi - bb);
-  e += a.lo + b.lo;
-  const float hi = s + e;
-  return F2{hi, e - (hi - s)};
-}
-__device__ __forceinline__ double radd(double a, double b) { return a + b; }
-__device__ __forceinline__ F2 rshfl(F2 a, int o) {
-  return F2{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
-__device__ __forceinline__ double rshfl(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
-
-// Last block: out[j] = sum over the blocks b of part[b * nv + j] (two-float),
-// in an order fixed by (nb, nv, blockDim): C chunks of consecutive blocks per
-// entry (C = blockDim / nv, 1 to 8) are summed by separate threads with eight
-// loads in flight, then the chunks in order.  scratch: C * nv entries.
-__device__ __forceinline__ void grid_sum_f2(const F2* part, int nb, int nv, double* out, F2* scratch) {
-  int C = (int)blockDim.x / nv;
-  C = C < 1 ? 1 : (C > 8 ? 8 : C);
-  const int S = (nb + C - 1) / C;
-  for (int t = threadIdx.x; t < nv * C; t += blockDim.x) {
-    const int j = t % nv, c = t / nv;
-    const int b1 = min(nb, (c + 1) * S);
-    F2 a = F2{0.f, 0.f};
-    int b = c * S;
-    for (; b + 8 <= b1; b += 8) {
-      float2 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldcg(reinterpret_cast<const float2*>(part + (size_t)(b + u) * nv + j));
-#pragma unroll
-      for (int u = 0; u < 8; ++u) a = radd(a, F2{v[u].x, v[u].y});
-    }
-    for (; b < b1; ++b) {
-      const float2 v = __ldcg(reinterpret_cast<const float2*>(part + (size_t)b * nv + j));
-      a = radd(a, F2{v.x, v.y});
-    }
-    scratch[t] = a;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
-    F2 a = scratch[j];
-    for (int c = 1; c < C; ++c) a = radd(a, scratch[c * nv + j]);
-    out[j] = (double)a.hi + (double)a.lo;
-  }
-}
-
 // Update of the lane's EL elements of the 8 columns: y += X[u0 .. u0 + nu) Cs
 // (Cs rows of 8, padded with zeros past ny).  FP32 keeps column pairs,
 // p[q][e] = (column 2q, column 2q + 1) of element e, for packed FMAs.

@@ -5,6 +5,8 @@
 // space) that run in a single block.
 #include <float.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace moto {
@@ -391,21 +393,34 @@ __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __rest
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     sacc[q] = v;
   }
+  // FP32: block and grid sums in two-float arithmetic (F2, 8 bytes like the
+  // FP64 partials of FP64 fields)
+  typedef typename std::conditional<sizeof(T) == 4, F2, double>::type RT;
+  RT(*rred)[kUpdSelf] = reinterpret_cast<RT(*)[kUpdSelf]>(red);
 #pragma unroll
   for (int q = 0; q < kUpdSelf; ++q)
-    if (lane == (q & 31)) red[wid][q] = (double)sacc[q];
+    if (lane == (q & 31)) {
+      if constexpr (sizeof(T) == 4)
+        rred[wid][q] = f2_of(sacc[q]);
+      else
+        rred[wid][q] = sacc[q];
+    }
   __syncthreads();
   if (threadIdx.x < kUpdSelf) {
-    double acc = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][threadIdx.x];
-    part[(size_t)blockIdx.x * kUpdSelf + threadIdx.x] = acc;
+    RT acc = rred[0][threadIdx.x];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) acc = radd(acc, rred[w][threadIdx.x]);
+    reinterpret_cast<RT*>(part)[(size_t)blockIdx.x * kUpdSelf + threadIdx.x] = acc;
   }
   if (!grid_last_block(counter)) return;
   __syncthreads();
-  grid_sum_entries(part, gridDim.x, kUpdSelf, red[0]);
+  __shared__ double tot[kUpdSelf];
+  if constexpr (sizeof(T) == 4)
+    grid_sum_f2(reinterpret_cast<const F2*>(part), gridDim.x, kUpdSelf, tot, reinterpret_cast<F2*>(red));
+  else
+    grid_sum_entries(part, gridDim.x, kUpdSelf, tot);
   __syncthreads();
   if (threadIdx.x < kUpdSelf) {
-    const double acc = red[0][threadIdx.x];
+    const double acc = tot[threadIdx.x];
     int c1 = 0, rem = threadIdx.x;
     while (rem >= 8 - c1) {
       rem -= 8 - c1;
@@ -579,7 +594,7 @@ __device__ __forceinline__ void amax_merge(double& a, double& ai, double& av, do
 
 // pass 1: partials per block and vector of P(V_c) (computed, not stored):
 // |P V_c|^2, max |entry|, its flat index, its signed value.  Per-thread shares are kept in the field
-// precision (a thread sees ~40 entries; comparisons of |entries| are exact in
+// precision (a thread sees ~160 entries; comparisons of |entries| are exact in
 // either precision) and promoted to FP64 for the cross-thread reductions.
 template <typename A>
 __device__ __forceinline__ void amax_merge_t(A& a, int& ai, A& av, A b, int bi, A bv) {
@@ -630,7 +645,7 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
       amax_merge_t<T>(amx_t[c], aidx_t[c], aval_t[c], fabs(a2), 2 * N + i, a2);
     }
   }
-  __shared__ double sh[kThreads / 32][4];
+  __shared__ double sh[MOTO_MAX_K][kThreads / 32][4];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < MOTO_MAX_K; ++c) {
@@ -647,34 +662,49 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
       amax_merge_t<T>(aT, aiT, avT, b, bi, bv);
     }
     if (lane == 0) {
-      sh[wid][0] = (double)sT;
-      sh[wid][1] = (double)aT;
-      sh[wid][2] = aiT == 0x7fffffff ? 1e300 : (double)aiT;
-      sh[wid][3] = (double)avT;
+      sh[c][wid][0] = (double)sT;
+      sh[c][wid][1] = (double)aT;
+      sh[c][wid][2] = aiT == 0x7fffffff ? 1e300 : (double)aiT;
+      sh[c][wid][3] = (double)avT;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double S = 0.0, A = -1.0, AI = 1e300, AV = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        S += sh[w][0];
-        amax_merge(A, AI, AV, sh[w][1], sh[w][2], sh[w][3]);
-      }
-      double* p = part + ((size_t)blockIdx.x * MOTO_MAX_K + c) * 4;
-      p[0] = S;
-      p[1] = A;
-      p[2] = AI;
-      p[3] = AV;
+  }
+  __syncthreads();
+  // thread c merges vector c over the warps in order
+  if (threadIdx.x < k) {
+    const int c = threadIdx.x;
+    double S = 0.0, A = -1.0, AI = 1e300, AV = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      S += sh[c][w][0];
+      amax_merge(A, AI, AV, sh[c][w][1], sh[c][w][2], sh[c][w][3]);
     }
-    __syncthreads();
+    double* p = part + ((size_t)blockIdx.x * MOTO_MAX_K + c) * 4;
+    p[0] = S;
+    p[1] = A;
+    p[2] = AI;
+    p[3] = AV;
   }
   if (!grid_last_block(counter)) return;
-  // warp c reduces vector c: lane l takes blocks l, l + 32, ... in order; the
-  // sums meet in a fixed shuffle tree, the largest entry in any order (ties go
-  // to the lowest index, a total order)
+  // warp c reduces vector c: lane l takes blocks l, l + 32, ... in order (four
+  // blocks' loads in flight at a time); the sums meet in a fixed shuffle tree,
+  // the largest entry in any order (ties go to the lowest index, a total order)
   if (wid < k) {
     const int c = wid;
     double S = 0.0, A = -1.0, AI = 1e300, AV = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
+    int b = lane;
+    for (; b + 96 < (int)gridDim.x; b += 128) {
+      double4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double* p = part + ((size_t)(b + 32 * u) * MOTO_MAX_K + c) * 4;
+        q[u] = make_double4(__ldcg(p), __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        S += q[u].x;
+        amax_merge(A, AI, AV, q[u].y, q[u].z, q[u].w);
+      }
+    }
+    for (; b < (int)gridDim.x; b += 32) {
       const double* p = part + ((size_t)b * MOTO_MAX_K + c) * 4;
       S += __ldcg(p);
       amax_merge(A, AI, AV, __ldcg(p + 1), __ldcg(p + 2), __ldcg(p + 3));
@@ -725,7 +755,9 @@ template <typename T>
 void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, unsigned* counter, double* scal,
                    const int* gate, int mask, cudaStream_t st) {
   const int g = stream_grid(N);
-  finish1_kernel<T><<<g, kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask);
+  // two blocks an SM for the reducing pass: fewer partials for its last block
+  const int g1 = g < 2 * kSMs ? g : 2 * kSMs;
+  finish1_kernel<T><<<g1, kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask);
   finish2_kernel<T><<<g, kThreads, 0, st>>>(m, V, ldv, k, N, scal, gate, mask);
 }
 
@@ -775,14 +807,27 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
   if (st->gate & (kGateKrylov | kGateDone)) return;
   // j >= 0: block Lanczos step j; j == -1: start block; j == -2: LOBPCG block
   __shared__ double Ls[MOTO_MAX_K][MOTO_MAX_K], Gs[MOTO_MAX_K][MOTO_MAX_K], Us[MOTO_MAX_K][MOTO_MAX_K];
-  __shared__ double dinv[MOTO_MAX_K], rsum[MOTO_MAX_K];
+  __shared__ double Ta[MOTO_MAX_K][MOTO_MAX_K], Ra[MOTO_MAX_K][MOTO_MAX_K];
+  __shared__ double dinv[MOTO_MAX_K], rsum[MOTO_MAX_K], gdiag[MOTO_MAX_K];
+  __shared__ int depk[MOTO_MAX_K];
+  __shared__ double tnorm0;
   __shared__ int bad, verdict;  // verdict: 0 go on, 1 stop (gate set), 2 LOBPCG column scaling
   const int t = threadIdx.x, r = t >> 3, c = t & 7;
   const bool in = r < b && c < b;
-  if (t == 0) bad = 0;
+  if (t == 0) {
+    bad = 0;
+    tnorm0 = st->tnorm;
+  }
+  // every global operand is read here, all loads in flight at once: the rest
+  // of the kernel is a chain of dependent steps that must not wait on memory
   if (in) {
     Gs[r][c] = 0.5 * (G[r * b + c] + G[c * b + r]);
     Ls[r][c] = 0.0;
+    if (r == c) gdiag[r] = G[r * b + r];
+    if (!second && j >= 0)  // |T| row sums of block row j: T(j, j) and R_j = T(j, j - 1)
+      Ta[r][c] = fabs(T[(size_t)(j * b + r) * ldT + j * b + c]) +
+                 (j > 0 ? fabs(T[(size_t)(j * b + r) * ldT + (j - 1) * b + c]) : 0.0);
+    if (second) Ra[r][c] = Racc[r * b + c];
   }
   __syncthreads();
   for (int k = 0; k < b; ++k) {
@@ -792,8 +837,11 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
         bad = 1;
         d = 1.0;
       }
-      Ls[k][k] = sqrt(d);
-      dinv[k] = 1.0 / Ls[k][k];
+      // one reciprocal square root on the dependent chain instead of a
+      // square root and a division
+      const double di = rsqrt(d);
+      Ls[k][k] = d * di;
+      dinv[k] = di;
     }
     __syncthreads();
     if (c == k && r > k && r < b) Ls[r][k] = Gs[r][k] * dinv[k];
@@ -803,12 +851,11 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
   }
   if (!second && j >= 0 && t < b) {
     double a = 0.0;
-    for (int cc = 0; cc < b; ++cc) {
-      a += fabs(T[(size_t)(j * b + t) * ldT + j * b + cc]);
-      if (j > 0) a += fabs(T[(size_t)(j * b + t) * ldT + (j - 1) * b + cc]);
-    }
+    for (int cc = 0; cc < b; ++cc) a += Ta[t][cc];
     rsum[t] = a;
   }
+  // near-dependent columns (pass 2, start block, LOBPCG), one thread a column
+  if (t < b) depk[t] = Ls[t][t] <= 1e-6 * sqrt(fmax(gdiag[t], 0.0)) ? 1 : 0;
   __syncthreads();
   if (t == 0) {
     double dmin = 1e300, dmax = 0.0;
@@ -820,15 +867,15 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
     if (!second && j >= 0) {
       double rs = 0.0;
       for (int k = 0; k < b; ++k) rs = fmax(rs, rsum[k]);
-      st->tnorm = fmax(st->tnorm, rs + dmax);
-      if (bad || dmin <= rel_tol * st->tnorm) {
+      const double tn = fmax(tnorm0, rs + dmax);
+      st->tnorm = tn;
+      if (bad || dmin <= rel_tol * tn) {
         st->gate |= kGateKrylov;
         v = 1;
       }
     } else {
       bool dep = bad != 0;
-      for (int k = 0; k < b && !dep; ++k)
-        if (Ls[k][k] <= 1e-6 * sqrt(fmax(G[k * b + k], 0.0))) dep = true;
+      for (int k = 0; k < b; ++k) dep = dep || depk[k] != 0;
       if (dep) {
         if (j == -2) {
           v = 2;
@@ -867,7 +914,7 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
   // R = L2^T R1 (R1 read completely before it is overwritten)
   double Rv = 0.0;
   if (in)
-    for (int q = 0; q < b; ++q) Rv += Ls[q][r] * Racc[q * b + c];
+    for (int q = 0; q < b; ++q) Rv += Ls[q][r] * Ra[q][c];
   __syncthreads();
   if (in) {
     Racc[r * b + c] = Rv;
@@ -1361,13 +1408,19 @@ void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G,
 // (2R+1)^2 Gram matrix of the basis.  newdots holds, for every basis vector
 // t, its dots with G, the candidate s and the candidate y at 3 t, 3 t + 1 and
 // 3 t + 2.
-__global__ void lbfgs_solve_kernel(double* M, int mem, const double* newdots, double gamma0, double* coef,
+__global__ void lbfgs_solve_kernel(double* Mg, int mem, const double* newdots, double gamma0, double* coef,
                                    DevState* dst) {
   if (dst->gate & kGateDone) return;
-  if (threadIdx.x != 0) return;
   const int R = mem + 1;
   const int nb = 2 * R + 1, gi = 2 * R;
-  const double* nd = newdots;
+  // the recursion is one thread's chain of dependent steps: M and the new
+  // dots are staged in shared memory by the warp first (one round trip)
+  constexpr int kNbMax = 2 * MOTO_MAX_MEM + 3;
+  __shared__ double M[kNbMax * kNbMax], nd[3 * kNbMax];
+  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) M[i] = Mg[i];
+  for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) nd[i] = newdots[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
   if (dst->lb_have_prev) {
     const int h = dst->lb_head;
     const int si = 2 * h, yi = 2 * h + 1;
@@ -1433,6 +1486,9 @@ __global__ void lbfgs_solve_kernel(double* M, int mem, const double* newdots, do
   }
   for (int t = 0; t < nb; ++t) coef[t] = q[t];
   dst->lb_have_prev = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) Mg[i] = M[i];
 }
 
 void launch_lbfgs_solve(double* M, int mem, const double* newdots, double gamma0, double* coef, DevState* dst,
