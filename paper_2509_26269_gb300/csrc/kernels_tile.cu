@@ -677,9 +677,11 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   const size_t tile_b = (size_t)(nxp + (MODE == 3 ? 0 : 8)) * TB;
   const size_t loaded = (size_t)(nx + (MODE == 3 ? 0 : ny)) * TB;
   // tiles per stage: a stage costs one CTA a roughly fixed handshake, so it
-  // should move 16 KB or more, while two stages per warp pair still fit
+  // should move 16 KB or more (32 KB for at most 8 + 8 fields, where that was
+  // measured faster), while every consumer pair can still hold a stage
+  const size_t stage_min = nx <= 8 ? 32768 : 16384;
   int tps = 1;
-  while (tps < 4 && loaded * tps < 16384 && (size_t)2 * tps * tile_b * (2 * kPairs) <= kDynBudget - 1024) tps *= 2;
+  while (tps < 4 && loaded * tps < stage_min && (size_t)2 * tps * tile_b * kPairs <= kDynBudget - 1024) tps *= 2;
   const size_t stage_bytes = tps * tile_b;
   int nst = (int)((kDynBudget - 1024) / stage_bytes);
   if (nst > kMaxStages) nst = kMaxStages;
