@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
 
   for (int i = tid; i < MOTO_MAX_BASIS; i += nth) theta[i] = 1.0 / 0.0;
   if (n <= 0) return;
+#pragma unroll 4
   for (int idx = tid; idx < n * n; idx += nth) {
     const int r = idx / n, c = idx - r * n;
     A[r * kLdA + c] = (R)(0.5 * (Tm[(size_t)r * ldT + c] + Tm[(size_t)c * ldT + r]));
@@ -116,15 +117,22 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
         __syncthreads();
         continue;
       }
-      for (int r = m0 + tid; r < n; r += nth) {  // p = b A22 v, a thread per row
-        R a0 = 0, a1 = 0;
-        int c2 = m0;
-        for (; c2 + 1 < n; c2 += 2) {
+      // p = b A22 v: two threads a row (adjacent lanes, alternate columns),
+      // four partial sums each
+      for (int idx = tid; idx < 2 * (n - m0); idx += nth) {
+        const int r = m0 + (idx >> 1), h = idx & 1;
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int c2 = m0 + h;
+        for (; c2 + 6 < n; c2 += 8) {
           a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
-          a1 += A[r * kLdA + c2 + 1] * A[(c2 + 1) * kLdA + j];
+          a1 += A[r * kLdA + c2 + 2] * A[(c2 + 2) * kLdA + j];
+          a2 += A[r * kLdA + c2 + 4] * A[(c2 + 4) * kLdA + j];
+          a3 += A[r * kLdA + c2 + 6] * A[(c2 + 6) * kLdA + j];
         }
-        if (c2 < n) a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
-        pv[r] = b * (a0 + a1);
+        for (; c2 < n; c2 += 2) a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
+        R a = (a0 + a1) + (a2 + a3);
+        a += __shfl_xor_sync(3u << (ln & 30), a, 1);
+        if (h == 0) pv[r] = b * a;
       }
       __syncthreads();
       // K = b v^T p / 2, summed by every warp in the same order; the update
@@ -132,12 +140,22 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
       R q = 0;
       for (int r = m0 + ln; r < n; r += 32) q += A[r * kLdA + j] * pv[r];
       const R K = (R)0.5 * b * warp_sum_r(q);
+      // the lane's column terms (at most three columns) do not depend on the row
+      R vcol[3], wcol[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int c2 = m0 + ln + 32 * u;
+        vcol[u] = c2 < n ? A[c2 * kLdA + j] : (R)0;
+        wcol[u] = c2 < n ? pv[c2] - K * vcol[u] : (R)0;
+      }
+#pragma unroll 2
       for (int r = m0 + wp; r < n; r += nw) {
         const R vr_ = A[r * kLdA + j];
         const R wr = pv[r] - K * vr_;
-        for (int c2 = m0 + ln; c2 < n; c2 += 32) {
-          const R vc = A[c2 * kLdA + j];
-          A[r * kLdA + c2] -= vr_ * (pv[c2] - K * vc) + wr * vc;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int c2 = m0 + ln + 32 * u;
+          if (c2 < n) A[r * kLdA + c2] -= vr_ * wcol[u] + wr * vcol[u];
         }
       }
       __syncthreads();
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
     }
     float a = lo - 1e-6f * (float)tn, bb = hi + 1e-6f * (float)tn;
     for (int round = 0; round < 24; ++round) {
-      const bool open = act && (bb - a) > 4e-7f * fmaxf(fabsf(a), fabsf(bb)) + 1e-30f;
+      const bool open = act && (bb - a) > 4e-7f * fmaxf(fabsf(a), fabsf(bb)) + 2e-7f * (float)tn;
       if (!__any_sync(0xffffffffu, open)) break;
       const float x = a + (bb - a) * (float)(sl + 1) * (1.0f / 17.0f);
       float pm = 1.f, p = df[0] - x;
@@ -263,8 +281,10 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
         su[r + 1] = -l * u1;
       }
     }
-    for (int r = 0; r < n; ++r)
+    for (int r = 0; r < n; ++r) {
       if (fabs(dg[r]) < tiny) dg[r] = (dg[r] < (R)0 ? -tiny : tiny);
+      dg[r] = (R)1 / dg[r];  // the sweeps multiply by the reciprocal pivots
+    }
     for (int r = 0; r < n; ++r) x[r] = (R)start_entry(r, i);
     for (int sweep = 0; sweep < 3; ++sweep) {
       for (int r = 0; r + 1 < n; ++r) {
@@ -280,7 +300,7 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
         R a = x[r];
         if (r + 1 < n) a -= su[r] * x[r + 1];
         if (r + 2 < n) a -= s2[r] * x[r + 2];
-        x[r] = a / dg[r];
+        x[r] = a * dg[r];
       }
       R nn = 0;
       for (int r = 0; r < n; ++r) nn += x[r] * x[r];
@@ -291,21 +311,24 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   }
   __syncthreads();
   // clusters: orthogonalise (modified Gram-Schmidt), then Rayleigh quotients
-  if (tid == 0) {
+  if (wp == 0) {  // warp 0: lanes split the rows, fixed shuffle trees
     for (int i = 1; i < ne; ++i) {
       bool touched = false;
       for (int j = 0; j < i; ++j) {
         if (fabs((double)shift[i] - (double)shift[j]) > 1e-5 * tn) continue;
         double dot = 0.0;
-        for (int r = 0; r < n; ++r) dot += vec[i * kN + r] * vec[j * kN + r];
-        for (int r = 0; r < n; ++r) vec[i * kN + r] -= dot * vec[j * kN + r];
+        for (int r = ln; r < n; r += 32) dot += vec[i * kN + r] * vec[j * kN + r];
+        dot = warp_sum(dot);
+        for (int r = ln; r < n; r += 32) vec[i * kN + r] -= dot * vec[j * kN + r];
+        __syncwarp();
         touched = true;
       }
       if (touched) {
         double nn = 0.0;
-        for (int r = 0; r < n; ++r) nn += vec[i * kN + r] * vec[i * kN + r];
-        nn = 1.0 / sqrt(nn);
-        for (int r = 0; r < n; ++r) vec[i * kN + r] *= nn;
+        for (int r = ln; r < n; r += 32) nn += vec[i * kN + r] * vec[i * kN + r];
+        nn = 1.0 / sqrt(warp_sum(nn));
+        for (int r = ln; r < n; r += 32) vec[i * kN + r] *= nn;
+        __syncwarp();
       }
     }
   }
@@ -344,6 +367,16 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   //         original T ---------------------------------------------------------------
   const int kk = k < ne ? k : ne;
   if (band > 1) {
+    // the band of the symmetrised T for the Rayleigh quotients, read in one
+    // round trip by all threads (the inverse-iteration workspace is free now)
+    const int bw = 2 * band + 1;
+    double* Tb = reinterpret_cast<double*>(iw);
+#pragma unroll 4
+    for (int idx = tid; idx < n * bw; idx += nth) {
+      const int r = idx / bw, c2 = r - band + (idx - r * bw);
+      Tb[idx] = (c2 >= 0 && c2 < n) ? 0.5 * (Tm[(size_t)r * ldT + c2] + Tm[(size_t)c2 * ldT + r]) : 0.0;
+    }
+    __syncthreads();
     for (int vi = wp; vi < kk; vi += nw) {
       R* x = vr + (size_t)vi * kN;
       for (int r = ln; r < n; r += 32) x[r] = (R)vec[vi * kN + r];
@@ -362,8 +395,7 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
       for (int r = ln; r < n; r += 32) {
         double t = 0.0;
         const int c0 = r - band < 0 ? 0 : r - band, c1 = r + band + 1 > n ? n : r + band + 1;
-        for (int c2 = c0; c2 < c1; ++c2)
-          t += 0.5 * (Tm[(size_t)r * ldT + c2] + Tm[(size_t)c2 * ldT + r]) * (double)x[c2];
+        for (int c2 = c0; c2 < c1; ++c2) t += Tb[r * bw + (c2 - r + band)] * (double)x[c2];
         a += (double)x[r] * t;
         nn += (double)x[r] * (double)x[r];
       }
