@@ -39,7 +39,7 @@ TILE_CLASSES = ("gram", "reorth_gram", "reorth_update")
 # DRAM bytes (read + write) per tile2d launch of one MMF step, measured with
 # ncu (dram__bytes_read.sum + dram__bytes_write.sum) at 1024 x 1024; every
 # launch scales with the number of sites
-TILE_TRAFFIC_1024 = 516.97e6
+TILE_TRAFFIC_1024 = 516.74e6
 WORKLOAD = "roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12)"
 
 
