@@ -799,35 +799,49 @@ void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int 
 // the |T| estimate with block row j (sum of |A| and |R_j| row entries plus the
 // largest new diagonal) and tests for breakdown (smallest diagonal of the
 // factor <= rel_tol * |T|).  Pass 2 composes R and stores it in T.
-// 64 threads, thread t = (r, c) = (t / 8, t % 8): the right-looking
-// factorisation, the triangular inverse (one column per thread) and the
-// product keep the dependent FP64 chain to a few dozen operations.
+// 64 threads, thread t = (r, c) = (t / 8, t % 8).  A dependent FP64 operation
+// costs GB300 on the order of a hundred cycles, so the kernel is built around
+// short chains: every global operand is read in one round trip (before the
+// gate test), the right-looking factorisation has one reciprocal square root
+// per pivot, the triangular inverse (one column per thread, fully unrolled)
+// adds the newest term of each sum last, and the minima, maxima and the final
+// product are trees or split sums.
 __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int second, int j, double* Rinv,
                                                     double* Racc, double* T, int ldT, DevState* st, double rel_tol) {
-  if (st->gate & (kGateKrylov | kGateDone)) return;
   // j >= 0: block Lanczos step j; j == -1: start block; j == -2: LOBPCG block
   __shared__ double Ls[MOTO_MAX_K][MOTO_MAX_K], Gs[MOTO_MAX_K][MOTO_MAX_K], Us[MOTO_MAX_K][MOTO_MAX_K];
-  __shared__ double Ta[MOTO_MAX_K][MOTO_MAX_K], Ra[MOTO_MAX_K][MOTO_MAX_K];
+  __shared__ double Ra[MOTO_MAX_K][MOTO_MAX_K];
   __shared__ double dinv[MOTO_MAX_K], rsum[MOTO_MAX_K], gdiag[MOTO_MAX_K];
-  __shared__ int depk[MOTO_MAX_K];
-  __shared__ double tnorm0;
   __shared__ int bad, verdict;  // verdict: 0 go on, 1 stop (gate set), 2 LOBPCG column scaling
   const int t = threadIdx.x, r = t >> 3, c = t & 7;
   const bool in = r < b && c < b;
-  if (t == 0) {
-    bad = 0;
-    tnorm0 = st->tnorm;
-  }
-  // every global operand is read here, all loads in flight at once: the rest
-  // of the kernel is a chain of dependent steps that must not wait on memory
+  const bool rows_t = !second && j >= 0;
+  // all loads in flight together (the buffers are valid whatever the gate says)
+  double g_rc = 0.0, g_cr = 0.0, ta = 0.0, ra = 0.0;
   if (in) {
-    Gs[r][c] = 0.5 * (G[r * b + c] + G[c * b + r]);
+    g_rc = G[r * b + c];
+    g_cr = G[c * b + r];
+    if (rows_t)  // |T| row sums of block row j: T(j, j) and R_j = T(j, j - 1)
+      ta = fabs(T[(size_t)(j * b + r) * ldT + j * b + c]) +
+           (j > 0 ? fabs(T[(size_t)(j * b + r) * ldT + (j - 1) * b + c]) : 0.0);
+    if (second) ra = Racc[r * b + c];
+  }
+  const double tnorm0 = st->tnorm;
+  if (st->gate & (kGateKrylov | kGateDone)) return;
+  if (t == 0) bad = 0;
+  if (in) {
+    Gs[r][c] = 0.5 * (g_rc + g_cr);
     Ls[r][c] = 0.0;
-    if (r == c) gdiag[r] = G[r * b + r];
-    if (!second && j >= 0)  // |T| row sums of block row j: T(j, j) and R_j = T(j, j - 1)
-      Ta[r][c] = fabs(T[(size_t)(j * b + r) * ldT + j * b + c]) +
-                 (j > 0 ? fabs(T[(size_t)(j * b + r) * ldT + (j - 1) * b + c]) : 0.0);
-    if (second) Ra[r][c] = Racc[r * b + c];
+    if (r == c) gdiag[r] = g_rc;
+    Ra[r][c] = ra;
+  }
+  // row sums of |T| by shuffles within the row's eight lanes (c order fixed)
+  {
+    double a = ta;
+    a += __shfl_down_sync(0xffffffffu, a, 4, 8);
+    a += __shfl_down_sync(0xffffffffu, a, 2, 8);
+    a += __shfl_down_sync(0xffffffffu, a, 1, 8);
+    if (c == 0 && r < b) rsum[r] = a;
   }
   __syncthreads();
   for (int k = 0; k < b; ++k) {
@@ -849,34 +863,30 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
     if (r < b && c > k && c <= r) Gs[r][c] -= Ls[r][k] * Ls[c][k];
     __syncthreads();
   }
-  if (!second && j >= 0 && t < b) {
-    double a = 0.0;
-    for (int cc = 0; cc < b; ++cc) a += Ta[t][cc];
-    rsum[t] = a;
-  }
-  // near-dependent columns (pass 2, start block, LOBPCG), one thread a column
-  if (t < b) depk[t] = Ls[t][t] <= 1e-6 * sqrt(fmax(gdiag[t], 0.0)) ? 1 : 0;
-  __syncthreads();
-  if (t == 0) {
-    double dmin = 1e300, dmax = 0.0;
-    for (int k = 0; k < b; ++k) {
-      dmin = fmin(dmin, Ls[k][k]);
-      dmax = fmax(dmax, Ls[k][k]);
+  if (t < 32) {
+    // warp 0: smallest and largest diagonal, largest |T| row sum and the
+    // near-dependent columns (L_kk^2 <= 1e-12 G_kk), trees over lanes 0..7
+    const bool on = t < b;
+    const double lkk = on ? Ls[t][t] : 0.0;
+    double dmin = on ? lkk : 1e300, dmax = on ? lkk : 0.0, rs = (on && rows_t) ? rsum[t] : 0.0;
+    int dep = (on && lkk * lkk <= 1e-12 * fmax(gdiag[t], 0.0)) ? 1 : 0;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      dmin = fmin(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+      rs = fmax(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+      dep |= __shfl_xor_sync(0xffffffffu, dep, o);
     }
-    int v = 0;
-    if (!second && j >= 0) {
-      double rs = 0.0;
-      for (int k = 0; k < b; ++k) rs = fmax(rs, rsum[k]);
-      const double tn = fmax(tnorm0, rs + dmax);
-      st->tnorm = tn;
-      if (bad || dmin <= rel_tol * tn) {
-        st->gate |= kGateKrylov;
-        v = 1;
-      }
-    } else {
-      bool dep = bad != 0;
-      for (int k = 0; k < b; ++k) dep = dep || depk[k] != 0;
-      if (dep) {
+    if (t == 0) {
+      int v = 0;
+      if (rows_t) {
+        const double tn = fmax(tnorm0, rs + dmax);
+        st->tnorm = tn;
+        if (bad || dmin <= rel_tol * tn) {
+          st->gate |= kGateKrylov;
+          v = 1;
+        }
+      } else if (bad || dep) {
         if (j == -2) {
           v = 2;
         } else {
@@ -885,25 +895,34 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
           v = 1;
         }
       }
+      verdict = v;
     }
-    verdict = v;
   }
   __syncthreads();
   if (verdict == 1) return;
   if (verdict == 2) {
     // LOBPCG residual block: fall back to column scaling; the SVQB step of
     // the Rayleigh-Ritz drops what stays dependent
-    if (in) Rinv[r * b + c] = (r == c) ? (G[r * b + r] > 0.0 ? 1.0 / sqrt(G[r * b + r]) : 1.0) : 0.0;
+    if (in) Rinv[r * b + c] = (r == c) ? (gdiag[r] > 0.0 ? 1.0 / sqrt(gdiag[r]) : 1.0) : 0.0;
     return;
   }
-  // Rinv = (L^T)^{-1}, upper triangular: column cc solves L^T x = e_cc
+  // Rinv = (L^T)^{-1}, upper triangular: column cc solves L^T x = e_cc by
+  // back substitution, each sum taken oldest term first so that only its last
+  // term waits on the entry just computed
   if (t < b) {
     const int cc = t;
-    for (int rr = b - 1; rr >= 0; --rr) {
+    double u[MOTO_MAX_K];
+#pragma unroll
+    for (int rr = MOTO_MAX_K - 1; rr >= 0; --rr) {
       double a = (rr == cc) ? 1.0 : 0.0;
-      for (int q = rr + 1; q <= cc; ++q) a -= Ls[q][rr] * Us[q][cc];
-      Us[rr][cc] = (rr <= cc) ? a * dinv[rr] : 0.0;
+#pragma unroll
+      for (int q = MOTO_MAX_K - 1; q > rr; --q)
+        if (q <= cc) a -= Ls[q][rr] * u[q];
+      u[rr] = (rr <= cc && rr < b) ? a * dinv[rr] : 0.0;
     }
+#pragma unroll
+    for (int rr = 0; rr < MOTO_MAX_K; ++rr)
+      if (rr < b) Us[rr][cc] = u[rr];
   }
   __syncthreads();
   if (in) Rinv[r * b + c] = Us[r][c];
@@ -911,11 +930,17 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
     if (in) Racc[r * b + c] = Ls[c][r];  // R1 = L^T
     return;
   }
-  // R = L2^T R1 (R1 read completely before it is overwritten)
-  double Rv = 0.0;
-  if (in)
-    for (int q = 0; q < b; ++q) Rv += Ls[q][r] * Ra[q][c];
-  __syncthreads();
+  // R = L2^T R1 (two interleaved partial sums; R1 was read before it is
+  // overwritten)
+  double R0 = 0.0, R1 = 0.0;
+  if (in) {
+#pragma unroll
+    for (int q = 0; q < MOTO_MAX_K; q += 2) {
+      if (q < b) R0 += Ls[q][r] * Ra[q][c];
+      if (q + 1 < b) R1 += Ls[q + 1][r] * Ra[q + 1][c];
+    }
+  }
+  const double Rv = R0 + R1;
   if (in) {
     Racc[r * b + c] = Rv;
     if (j >= 0) {

@@ -1,7 +1,7 @@
 """The skinny Gram product (reorthogonalisation / Rayleigh-Ritz building block)
 against numpy in FP64 on the same (rounded) fields: tiny, ragged and
 tile-multiple lengths, aligned strides (TMA path) and packed odd strides
-(plain path), every row/column count class."""
+(plain path), every row/column count class and lane layout."""
 import numpy as np
 import pytest
 import torch
@@ -27,7 +27,10 @@ def test_gram_matches_numpy(dtype, tol, L1, L2, aligned):
     rng = inputs.normal(L1 * 100 + L2, 104 * ld).reshape(104, ld)
     buf = torch.from_numpy(rng).to(device="cuda", dtype=dtype)
     A = to_np(buf)[:, :n]
-    for nx, ny in [(1, 1), (3, 3), (8, 8), (9, 3), (24, 8), (61, 1), (96, 8)]:
+    # every lane-layout class of the streaming kernel (field counts rounded
+    # up to 8: 8 ... 96) and the row sizes 1 KB (<= 32), 512 B (<= 72), 256 B
+    for nx, ny in [(1, 1), (3, 3), (8, 8), (9, 3), (24, 8), (32, 8), (40, 5), (48, 8), (53, 8), (61, 1), (72, 8),
+                   (80, 2), (88, 8), (96, 8)]:
         out = torch.empty(nx * ny, dtype=torch.float64, device="cuda")
         X = buf[0:nx].contiguous() if not aligned else buf
         Y = buf[nx:nx + ny]
