@@ -361,6 +361,40 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
       }
   }
   __syncthreads();
+  // The returned vectors, mutually orthogonalised in FP64: inverse iteration
+  // in FP32 leaves vectors of close (but not clustered) eigenvalues with
+  // overlaps of order eps |T| / gap, up to ~1e-4 on the dense low end of the
+  // spectrum.  One classical Gram-Schmidt pass removes them to O(overlap^2):
+  // the dots in parallel (a warp per pair), the updates from the unchanged
+  // vectors (thread per entry), then the norms.
+  {
+    const int kr = k < ne ? k : ne;
+    __shared__ double ov[MOTO_MAX_K][MOTO_MAX_K];
+    double* nv = reinterpret_cast<double*>(iw);  // kr x kN scratch (inverse-iteration workspace)
+    for (int pr = wp; pr < kr * kr; pr += nw) {
+      const int i = pr / kr, j = pr - i * kr;
+      if (j >= i) continue;
+      double a = 0.0;
+      for (int r = ln; r < n; r += 32) a += vec[i * kN + r] * vec[j * kN + r];
+      a = warp_sum(a);
+      if (ln == 0) ov[i][j] = a;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < kr * n; idx += nth) {
+      const int i = idx / n, r = idx - i * n;
+      double x = vec[i * kN + r];
+      for (int j = 0; j < i; ++j) x -= ov[i][j] * vec[j * kN + r];
+      nv[i * kN + r] = x;
+    }
+    __syncthreads();
+    for (int i = wp; i < kr; i += nw) {
+      double a = 0.0;
+      for (int r = ln; r < n; r += 32) a += nv[i * kN + r] * nv[i * kN + r];
+      const double f = 1.0 / sqrt(warp_sum(a));
+      for (int r = ln; r < n; r += 32) vec[i * kN + r] = nv[i * kN + r] * f;
+    }
+    __syncthreads();
+  }
 
   // ---- 4. back-transformation x <- H_0 ... H_{n-3} x in R (a warp per vector,
   //         the reflectors read-only), then FP64 Rayleigh quotients with the
