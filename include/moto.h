@@ -251,8 +251,8 @@ int moto_pairwise_l1(moto_ctx* ctx, const void* X_dev, size_t ldx, int count, do
 /* Skinny Gram product out[r * ny + c] = X_r . Y_c over the 3N elements of
  * nx <= MOTO_MAX_BASIS fields X_r (at X_dev + r * ldx) and ny <= MOTO_MAX_K
  * fields Y_c (at Y_dev + c * ldy), accumulated as the Krylov solvers do it
- * (FP32 products and short FP32 runs, FP64 above; all FP64 in an FP64
- * context).  out_dev: nx * ny doubles, row-major.  The building block of the
+ * (FP32 products and short FP32 runs, then fixed-order sums in two-float
+ * FP32 arithmetic, about 44 significant bits; all FP64 in an FP64 context).  out_dev: nx * ny doubles, row-major.  The building block of the
  * reorthogonalisation and Rayleigh-Ritz steps, exposed for checks of
  * orthogonality and for tests. */
 int moto_gram(moto_ctx* ctx, const void* X_dev, size_t ldx, int nx, const void* Y_dev, size_t ldy,

@@ -61,9 +61,10 @@ template <typename T>
 void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st);
 
 // out[r*ny + c] = sum_e X_r[e] Y_c[e] over n elements, r < nx <= 96, c < ny <= 8.
-// FP32 products summed in FP32 over at most 16 x (tile share) elements, then
-// promoted to FP64 for every cross-thread and cross-block sum (T = float);
-// all-FP64 for T = double.
+// Aligned fields go to the streaming kernel (mode 0: FP32 runs, then
+// two-float sums); otherwise FP32 products are summed in FP32 over at most
+// 16 x (tile share) elements, then promoted to FP64 for every cross-thread
+// and cross-block sum (T = float); all-FP64 for T = double.
 template <typename T>
 void launch_gram(const T* X, size_t ldx, int nx, const T* Y, size_t ldy, int ny, size_t n, double* out,
                  double* part, unsigned* counter, const int* gate, int mask, cudaStream_t st);

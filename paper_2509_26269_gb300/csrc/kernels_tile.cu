@@ -28,10 +28,11 @@
 // of every row (update and Gram need only the elements they own, so the two
 // warps never wait for each other; a stage is freed by their two mbarrier
 // arrivals).  Two consumer warps share each scheduler and hide each other's
-// latencies.  Gram layout (modes 0, 1): lane (rl, cl) owns the outputs of rows
-// rl + NRL i (i < R) and columns cl CW + j (j < CW), so it needs no cross-lane
-// sum; per 16-byte chunk it loads its R rows of X and CW rows of Y and
-// multiplies them with packed FP32 FMAs (fma.rn.f32x2).  Update layout (modes
+// latencies.  Gram layout (modes 0, 1): lane (rl, cl, ks) owns the outputs of
+// rows rl + NRL i (i < R) and columns cl CW + j (j < CW) over every KS-th
+// chunk of a tile (the KS lanes of an output are summed once, at the end);
+// per 16-byte chunk it loads its R rows of X and CW rows of Y and multiplies
+// them with packed FP32 FMAs (fma.rn.f32x2).  Update layout (modes
 // 1-3): a lane owns TB / 64 bytes of the tile of all 8 columns and loops over
 // the rows of X with one load of X and broadcast loads of the C row.  FP32
 // partial sums are flushed every 512 elements of a lane's share into a second

@@ -383,8 +383,8 @@ __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __rest
     }
   }
   // warp sums in the field precision (a fixed butterfly over 32 partials of
-  // a few tens of products each), one FP64 conversion per entry and warp;
-  // block and grid sums in FP64
+  // a few tens of products each); block and grid sums in two-float
+  // arithmetic for FP32 fields, FP64 for FP64 fields
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < kUpdSelf; ++q) {
