@@ -302,8 +302,6 @@ int moto_descend(moto_ctx* ctx, const void* m_saddle_dev, const void* v1_dev,
                  const moto_params* params, void* m_plus_dev, void* m_minus_dev,
                  double* out_dev, void* stream);
 
-/* Device status word of the context (synchronises the stream): MOTO_OK or
- * the first device-detected error since the last moto_clear_status. */
 /* ------------------------------------------------------------------------
  * Batched walkers.  The paper runs the bilayer MMF kernel on many perturbed
  * starting points (Alg. 1, one walker per explorer proposal); the batch
@@ -345,8 +343,25 @@ int moto_batch_ascend(moto_batch* batch, int check_every, double* rec_dev, int* 
 int moto_batch_descend(moto_batch* batch, void* const* m_plus, void* const* m_minus, double* out_dev,
                        int* status_host, void* stream);
 
+/* Device status word of the context (synchronises the stream): MOTO_OK or
+ * the first device-detected error since the last moto_clear_status. */
 int moto_status(moto_ctx* ctx, void* stream);
+/* Clears the context's device status word (enqueued on the stream). */
 int moto_clear_status(moto_ctx* ctx, void* stream);
+
+/* Failure-detection control (host side only).  Every wait inside the
+ * library's kernels is bounded: a consumer warp of the streaming
+ * reorthogonalisation kernel that waits for a stage of tensor copies gives up
+ * after about 2^22 blocking polls, drains the copies it has in flight, sets
+ * MOTO_ERR_TIMEOUT in the context's status word and lets the launch finish.
+ * polls > 0 replaces that bound by `polls` non-blocking tests for every later
+ * solver call of the context, so that a test can make the waits give up and
+ * check the reported status without a real stall; 0 restores the default.
+ * The copies in flight are always drained with the full bound.  Results of a
+ * solve whose waits gave up are meaningless; clear the status (and restore
+ * the default) before relying on later calls.  Returns MOTO_ERR_ARG for
+ * polls < 0. */
+int moto_set_wait_limit(moto_ctx* ctx, int polls);
 
 /* Human-readable text of a return code (static storage). */
 const char* moto_status_string(int code);
@@ -378,12 +393,18 @@ int moto_profile_end(moto_ctx* ctx, int nkinds, int* launches, double* ms, doubl
  * Its only scratch is a fixed device array inside the library (512 KB + 256 B,
  * held by every GPU that loads the library until the process exits); it
  * holds the partial sums of at most 32768 tiles of 32 x 32 sites, so
- * ceil(L1/32) * ceil(L2/32) > 32768 is rejected with MOTO_ERR_ARG.  The first
- * call on a device looks the array up with that device current; make that
- * first call outside any stream capture.  Every call shares the array and
- * keeps the last call's contents, so calls that overlap on the GPU (several
- * streams or devices' threads at once) race; serialise them.  Non-finite
- * inputs are not reported by this variant.  Calls no cudaMalloc or cudaFree. */
+ * ceil(L1/32) * ceil(L2/32) > 32768 (and, as for moto_create, L1 * L2 > 2^30)
+ * is rejected with MOTO_ERR_ARG before any CUDA call.  The first call on a
+ * device looks the array up with that device current and keeps its address
+ * for the life of the process; make that first call outside any stream
+ * capture, and do not use this call after a cudaDeviceReset of that device
+ * (the library's module, and with it the array, may then move).  Every call
+ * shares the array and keeps the last call's contents, so calls that overlap
+ * on the GPU (several streams or devices' threads at once) race; serialise
+ * them.  If a CUDA error from earlier work is pending on the calling thread,
+ * the call launches nothing and returns MOTO_ERR_CUDA (the error stays
+ * pending).  Non-finite inputs are not reported by this variant.  Calls no
+ * cudaMalloc or cudaFree. */
 int moto_energy_grad_noalloc(const moto_model* model, int dtype, const void* m_dev, void* g_dev,
                              void* s_dev, double* out_dev, void* stream);
 

@@ -88,6 +88,7 @@ def _load():
         "moto_gram": (I, [P, P, Z, I, P, Z, I, P, P]),
         "moto_perturb": (I, [P, P, P, P, Z, I, P, Z, P]),
         "moto_set_pairs": (I, [P, ctypes.POINTER(moto_pair), I]),
+        "moto_set_wait_limit": (I, [P, I]),
         "moto_pairwise_l1": (I, [P, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
         "moto_batch_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params),
@@ -109,7 +110,7 @@ EXPORTED = (
     "moto_lowest_modes", "moto_topo_charge", "moto_lbfgs_reset", "moto_mmf_step", "moto_ascend", "moto_descend",
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
-    "moto_perturb", "moto_pairwise_l1", "moto_set_pairs",
+    "moto_perturb", "moto_pairwise_l1", "moto_set_pairs", "moto_set_wait_limit",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
@@ -264,6 +265,12 @@ def moto_descend(ctx, m_saddle, v1, params, m_plus, m_minus, out, stream=None):
                            _ptr(out), _stream(stream))
     _check(rc, "moto_descend", ok=(MOTO_OK, MOTO_NOT_CONVERGED))
     return rc
+
+
+def moto_set_wait_limit(ctx, polls: int):
+    """Bound of the streaming kernel's consumer waits (0 = default); a test
+    hook for the timeout path."""
+    _check(_lib.moto_set_wait_limit(ctx, int(polls)), "moto_set_wait_limit")
 
 
 def moto_status(ctx, stream=None) -> int:

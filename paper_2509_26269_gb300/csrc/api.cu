@@ -48,6 +48,8 @@ struct moto_ctx {
   int* prof_kind;
   double* prof_bytes;
   cudaStream_t prof_stream;
+  // bound of the streaming kernel's consumer waits (moto_set_wait_limit; 0 = default)
+  int wait_polls;
 };
 
 namespace {
@@ -197,7 +199,7 @@ void P_tile(moto_ctx* c, int mode, const T* X, int nx, int u0, int nu, T* Y, int
     PROF(mode == 1 ? kPkReorthGram : (mode == 2 ? kPkReorthUpd : kPkGram), f * fields);
     set_gram_status(&c->st->status);
     done = launch_tile<T>(mode, X, ld, nx, u0, nu, Y, ld, ny, c->n3, C, Yout, ld, out, c->part, c->counter, gate,
-                          mask, &c->st->status, st, Cadd, uadd, nadd);
+                          mask, &c->st->status, st, Cadd, uadd, nadd, c->wait_polls);
   }
   if (done) return;
   switch (mode) {
@@ -677,6 +679,12 @@ void moto_destroy(moto_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
+}
+
+int moto_set_wait_limit(moto_ctx* c, int polls) {
+  if (!c || polls < 0) return MOTO_ERR_ARG;
+  c->wait_polls = polls;
+  return MOTO_OK;
 }
 
 int moto_set_pairs(moto_ctx* c, const moto_pair* pairs, int n) {

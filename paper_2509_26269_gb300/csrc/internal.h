@@ -33,6 +33,9 @@ struct DevState {
 };
 
 int tile_blocks(const ModelDev& md);
+// blocks (and so partial-sum slots) of an energy / gradient / charge launch on
+// an L1 x L2 lattice, in 64-bit so that no lattice size overflows it
+long long stencil_blocks(int L1, int L2);
 int pair_blocks(const ModelDev& md);
 // pair-list stencils (kernels_pairs.cu); launch_energy_grad, launch_hvp and
 // launch_euclid_hvp forward to them when md.npairs > 0
@@ -78,11 +81,15 @@ int gram_blocks();
 // Gram sees the updated fields, memory keeps the old ones.  Mode 2 may add Cadd
 // (nadd x ny) to rows uadd .. uadd + nadd - 1 of C.  Returns false (nothing
 // launched) when a base address or stride breaks the TMA alignment rules; the
-// caller then uses combine + the plain Gram kernel.
+// caller then uses combine + the plain Gram kernel.  polls > 0 replaces the
+// bound of the consumer warps' waits for a filled stage (polls non-blocking
+// tests instead of ~2^22 blocking ones), so that a test can make them give
+// up; 0 keeps the default.
 template <typename T>
 bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
                  const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
-                 int mask, int* status, cudaStream_t st, const double* Cadd = nullptr, int uadd = 0, int nadd = 0);
+                 int mask, int* status, cudaStream_t st, const double* Cadd = nullptr, int uadd = 0, int nadd = 0,
+                 int polls = 0);
 // Cholesky QR applied twice without storing X R1^{-1} (kernels_vec.cu): with
 // gram, S2 = (X P1)^T (X P1); without, Q = (X P1) P2, projected on the tangent
 // planes of m when m != NULL.  X: nx <= 8 fields; P1, P2: nx x nx FP64.  Both

@@ -258,10 +258,11 @@ static dim3 tile_grid(const ModelDev& md) {
   return dim3((md.L1 + kTileX - 1) / kTileX, (md.L2 + kTileY - 1) / kTileY);
 }
 
-int tile_blocks(const ModelDev& md) {
-  const dim3 g = tile_grid(md);
-  return (int)(g.x * g.y);
+long long stencil_blocks(int L1, int L2) {
+  return (((long long)L1 + kTileX - 1) / kTileX) * (((long long)L2 + kTileY - 1) / kTileY);
 }
+
+int tile_blocks(const ModelDev& md) { return (int)stencil_blocks(md.L1, md.L2); }
 
 template <typename T>
 void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,

@@ -253,7 +253,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     tile2d_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int nx, int ny,
                   int u0, int nu, size_t n, const double* __restrict__ C, const double* __restrict__ Cadd, int uadd,
                   int nadd, T* __restrict__ Yout, size_t ldo, double* out, double* part, unsigned* counter, int nst,
-                  int tps, const int* gate, int mask, int* status) {
+                  int tps, const int* gate, int mask, int* status, int polls) {
   if (gate && (*gate & mask)) return;
   typedef TileT<T> TT;
   typedef typename TT::Acc Acc;
@@ -341,7 +341,7 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     if (lane == 0) {
       for (int it = 0; it < ntile; ++it) {
         const int s = it % nst;
-        if (it >= nst && !mbar_wait(&empty[s], (unsigned)(((it / nst) - 1) & 1))) {
+        if (it >= nst && !mbar_wait_or_abort(&empty[s], (unsigned)(((it / nst) - 1) & 1), &abort_flag)) {
           atomicExch(&abort_flag, 1);
           if (status) atomicOr(status, kStatusTimeout);
           break;
@@ -396,7 +396,8 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         }
       }
       if (*(volatile int*)&abort_flag) break;
-      if (!mbar_wait(&full[s], (unsigned)((it / nst) & 1))) {
+      if (!(polls > 0 ? mbar_test_n(&full[s], (unsigned)((it / nst) & 1), polls)
+                      : mbar_wait(&full[s], (unsigned)((it / nst) & 1)))) {
         atomicExch(&abort_flag, 1);
         if (status) atomicOr(status, kStatusTimeout);
       }
@@ -523,12 +524,14 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
   }
   __syncthreads();
   if (abort_flag) {
-    // bounded drain: let tensor copies still in flight land before the ring
-    // is reused (a phase that already completed returns at once)
+    // bounded drain (full bound): the last fill issued into a stage (tile
+    // tile_of[s], the stage's fill number tile_of[s] / nst) must land before
+    // the ring is reused; earlier fills of the stage were consumed, so they
+    // landed, and a fill that already landed returns at once
     if (threadIdx.x == 0)
       for (int s = 0; s < nst; ++s) {
-        mbar_wait(&full[s], 0);
-        mbar_wait(&full[s], 1);
+        const int t = *(volatile int*)&tile_of[s];
+        if (t >= 0) mbar_wait(&full[s], (unsigned)((t / nst) & 1));
       }
     __syncthreads();
   }
@@ -672,7 +675,7 @@ int tile_bytes(int mode, int nx, int ny) {
 template <typename T, int MODE, int R, int CW, int NRL, int TB>
 void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
                  const double* C, const double* Cadd, int uadd, int nadd, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
-                 int mask, int* status, cudaStream_t st) {
+                 int mask, int* status, int polls, cudaStream_t st) {
   constexpr int TE = TB / (int)sizeof(T);
   const int nxp = (nx + 7) & ~7;
   const size_t tile_b = (size_t)(nxp + (MODE == 3 ? 0 : 8)) * TB;
@@ -703,7 +706,7 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
   const int grid = (int)(ngroups < want ? (ngroups > 0 ? ngroups : 1) : want);
   tile2d_kernel<T, MODE, R, CW, NRL, TB><<<grid, kThrT, smem, st>>>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out,
-                                                                    part, counter, nst, tps, gate, mask, status);
+                                                                    part, counter, nst, tps, gate, mask, status, polls);
 }
 
 // Gram lane layouts (R rows x CW columns a lane, NRL row lanes): FP32 fits
@@ -713,10 +716,11 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
 template <typename T, int MODE, int TB>
 void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, int u0, int nu, size_t n,
                    const double* C, const double* Cadd, int uadd, int nadd, T* Yout, size_t ldo, double* out,
-                   double* part, unsigned* counter, const int* gate, int mask, int* status, cudaStream_t st) {
+                   double* part, unsigned* counter, const int* gate, int mask, int* status, int polls,
+                   cudaStream_t st) {
 #define TL(RR, CC, NN)                                                                                           \
   tile_launch<T, MODE, RR, CC, NN, TB>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part,    \
-                                       counter, gate, mask, status, st)
+                                       counter, gate, mask, status, polls, st)
   const int nxp = (nx + 7) & ~7;
   if constexpr (MODE >= 2) {
     TL(1, 4, 16);
@@ -767,7 +771,7 @@ void tile_dispatch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny,
 template <typename T>
 bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const T* Y, size_t ldy, int ny, size_t n,
                  const double* C, T* Yout, size_t ldo, double* out, double* part, unsigned* counter, const int* gate,
-                 int mask, int* status, cudaStream_t st, const double* Cadd, int uadd, int nadd) {
+                 int mask, int* status, cudaStream_t st, const double* Cadd, int uadd, int nadd, int polls) {
   auto al = [](const void* p) { return ((uintptr_t)p % 16) == 0; };
   if ((ldx * sizeof(T)) % 16 || (ldy * sizeof(T)) % 16 || !al(X) || (mode != 3 && !al(Y))) return false;
   if (mode == 2 && !Yout) return false;
@@ -787,7 +791,7 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
   } else {
     my = mx;
   }
-#define TD(M, B) tile_dispatch<T, M, B>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, gate, mask, status, st)
+#define TD(M, B) tile_dispatch<T, M, B>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, gate, mask, status, polls, st)
   if constexpr (sizeof(T) == 8) {
     switch (mode) {
       case 0: TD(0, 512); break;
@@ -822,9 +826,9 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
 
 template bool launch_tile<float>(int, const float*, size_t, int, int, int, const float*, size_t, int, size_t,
                                  const double*, float*, size_t, double*, double*, unsigned*, const int*, int, int*,
-                                 cudaStream_t, const double*, int, int);
+                                 cudaStream_t, const double*, int, int, int);
 template bool launch_tile<double>(int, const double*, size_t, int, int, int, const double*, size_t, int, size_t,
                                   const double*, double*, size_t, double*, double*, unsigned*, const int*, int, int*,
-                                  cudaStream_t, const double*, int, int);
+                                  cudaStream_t, const double*, int, int, int);
 
 }  // namespace moto

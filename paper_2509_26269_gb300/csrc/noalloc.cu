@@ -16,9 +16,9 @@
 
 namespace {
 
-// Partial sums for up to kMaxBlocks tile blocks (two doubles each), then the
-// arrival counter and the status word.
-constexpr int kMaxBlocks = 32768;  // 32 x 32-site tiles: up to 33,554,432 sites
+// Partial sums for up to kMaxBlocks blocks of the energy stencil (two doubles
+// each), then the arrival counter and the status word.
+constexpr long long kMaxBlocks = 32768;
 constexpr size_t kScratchDoubles = 2 * (size_t)kMaxBlocks + 32;
 static __device__ __align__(256) double moto_noalloc_scratch[kScratchDoubles];
 
@@ -49,6 +49,10 @@ extern "C" int moto_energy_grad_noalloc(const moto_model* model, int dtype, cons
   if (!model || !m_dev) return MOTO_ERR_ARG;
   if (model->L1 < 5 || model->L2 < 5 || model->n_shells < 1 || model->n_shells > 3) return MOTO_ERR_ARG;
   if (dtype != MOTO_F32 && dtype != MOTO_F64) return MOTO_ERR_ARG;
+  // sizes checked in 64-bit before anything is formed in int: the site count
+  // has moto_create's cap, and the tile count must fit the fixed array
+  if ((long long)model->L1 * model->L2 > (1LL << 30)) return MOTO_ERR_ARG;
+  if (moto::stencil_blocks(model->L1, model->L2) > kMaxBlocks) return MOTO_ERR_ARG;
   moto::ModelDev md;
   md.L1 = model->L1;
   md.L2 = model->L2;
@@ -58,8 +62,9 @@ extern "C" int moto_energy_grad_noalloc(const moto_model* model, int dtype, cons
   md.D = model->D;
   md.K = model->K;
   md.muB = model->muB;
-  // larger lattices need more partial sums than the fixed array holds
-  if ((long long)moto::tile_blocks(md) > kMaxBlocks) return MOTO_ERR_ARG;
+  // an error left pending by the caller's own work is not this call's: refuse
+  // to launch rather than report it (and clear it) as ours
+  if (cudaPeekAtLastError() != cudaSuccess) return MOTO_ERR_CUDA;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc) return rc;

@@ -63,11 +63,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after ~2^22 polls (each poll may itself suspend for a
-// while) and reports a timeout instead of hanging.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr int kWaitPolls = 1 << 22;
+
+// Bounded wait: gives up after kWaitPolls polls (each poll may itself suspend
+// for a while) and reports a timeout instead of hanging.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  for (int i = 0; i < (1 << 22); ++i)
+  for (int i = 0; i < kWaitPolls; ++i)
     if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// The same bound, also giving up as soon as *abort is set (every 64 polls).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity, const int* abort) {
+  for (int i = 0; i < kWaitPolls; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && *(const volatile int*)abort) return false;
+  }
+  return false;
+}
+
+// At most n non-blocking tests (a short, caller-chosen bound).
+__device__ __forceinline__ bool mbar_test_n(uint64_t* bar, unsigned parity, int n) {
+  for (int i = 0; i < n; ++i)
+    if (mbar_test_wait(bar, parity)) return true;
   return false;
 }
 

@@ -44,3 +44,15 @@ def test_host_side_calls_without_gpu():
     p3 = mo.make_params(block=8, krylov_steps=13)
     assert lib.moto_create(ctypes.byref(bad), 0, ctypes.byref(p3), ctypes.byref(h)) == mo.MOTO_ERR_ARG
     assert lib.moto_create(ctypes.byref(bad), 7, ctypes.byref(p), ctypes.byref(h)) == mo.MOTO_ERR_ARG
+
+
+def test_noalloc_rejects_oversized_lattices_on_the_host():
+    """The allocation-free energy call holds its partial sums in a fixed array:
+    lattices whose stencil blocks would not fit (including sizes whose block
+    count overflows 32-bit arithmetic) are refused before any CUDA call."""
+    import paper_2509_26269_gb300 as mo
+    lib = mo._lib
+    fake = ctypes.c_void_p(256)  # never dereferenced: the call must return first
+    for L1, L2 in ((8192, 4097), (2147483616, 1056), (1 << 16, 1 << 15), (46341, 46341)):
+        big = mo.make_model(L1, L2, J=(1.0,))
+        assert lib.moto_energy_grad_noalloc(ctypes.byref(big), 0, fake, None, None, None, None) == mo.MOTO_ERR_ARG

@@ -116,3 +116,38 @@ def test_lanczos_and_lobpcg_agree_on_config1_state():
     assert conv
     assert th[0] == pytest.approx(lam[0], rel=1e-6)
     assert abs(vdot(V[0], VV[0])) == pytest.approx(1.0, abs=1e-6)
+
+
+def _block_with_dependent_row(rel: float):
+    """Four rows: three independent ones, and a fourth that is a combination
+    of them plus a new direction of relative size ``rel`` (the sine of its
+    angle to the span of the others)."""
+    n = 300
+    W = np.stack([inputs.normal(40 + j, n) for j in range(3)])
+    comb = 0.7 * W[0] - 1.3 * W[1] + 0.4 * W[2]
+    Qo, _ = np.linalg.qr(W.T)
+    new = inputs.normal(50, n)
+    new = new - Qo @ (Qo.T @ new)
+    new *= rel * np.linalg.norm(comb) / np.linalg.norm(new)
+    return np.vstack([W, comb + new])
+
+
+def test_cholqr2_rank_rule():
+    """The rank rule of Cholesky QR applied twice (reading R4): a row whose new
+    direction is below 1e-6 of its length makes cholqr2 report a dependent
+    block, since then the condition number of the block is at least 1e6,
+    within two orders of magnitude of the u^(-1/2) ~ 1e8 beyond which CholQR2
+    no longer delivers an orthonormal factor (Yamamoto, Nakatsukasa,
+    Yanagisawa & Fukaya 2015).  Above it, the factor is orthonormal to FP64
+    rounding and reproduces the block."""
+    assert krylov.cholqr2(_block_with_dependent_row(1e-7)) is None
+    W = _block_with_dependent_row(1e-5)
+    res = krylov.cholqr2(W)
+    assert res is not None
+    Q, R = res
+    assert np.linalg.norm(Q @ Q.T - np.eye(4)) <= 1e-12
+    assert np.linalg.norm(W - R.T @ Q) <= 1e-12 * np.linalg.norm(W)
+    # the rule reads the fourth diagonal of the factor: the relative new
+    # direction itself
+    L = np.linalg.cholesky(W @ W.T)
+    assert L[3, 3] / np.linalg.norm(W[3]) == pytest.approx(1e-5, rel=1e-3)

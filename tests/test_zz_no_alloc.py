@@ -40,6 +40,27 @@ def test_noalloc_matches_context_path_twice(dtype, code, tol):
 def test_noalloc_rejects_lattices_beyond_its_fixed_scratch():
     require_gpu()
     import paper_2509_26269_gb300 as mo
-    big = mo.make_model(8192, 4097, J=(1.0,))
-    rc = mo._lib.moto_energy_grad_noalloc(ctypes.byref(big), 0, 1, None, None, None, None)
-    assert rc == mo.MOTO_ERR_ARG
+    for L1, L2 in ((8192, 4097), (2147483616, 1056)):
+        big = mo.make_model(L1, L2, J=(1.0,))
+        rc = mo._lib.moto_energy_grad_noalloc(ctypes.byref(big), 0, 1, None, None, None, None)
+        assert rc == mo.MOTO_ERR_ARG
+
+
+def test_noalloc_allocates_no_device_memory():
+    """The defining property: after a first call (which looks up the fixed
+    array), further calls leave the device's free memory unchanged."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    M = workload_model(2, 64, 48)
+    model = mo.make_model(M.L1, M.L2, J=M.J, D=M.D, K=M.K, muB=M.muB)
+    m = to_dev(inputs.add_noise(inputs.skyrmion(M.L1, M.L2, 5.0), 0.1, 21), torch.float32)
+    g = torch.empty_like(m)
+    s = torch.empty(M.L1 * M.L2, dtype=torch.float32, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    assert mo.moto_energy_grad_noalloc(model, 0, m, g, s, out) == mo.MOTO_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        assert mo.moto_energy_grad_noalloc(model, 0, m, g, s, out) == mo.MOTO_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
