@@ -349,6 +349,22 @@ int moto_status(moto_ctx* ctx, void* stream);
 /* Clears the context's device status word (enqueued on the stream). */
 int moto_clear_status(moto_ctx* ctx, void* stream);
 
+/* HVP autotuner.  The strip HVP kernel exists in several variants (strip
+ * length, warps per block, spins held in registers) that give bit-identical
+ * results and differ only in speed.  moto_create times each variant once on
+ * its own scratch (vectors per call: params.block for block Lanczos,
+ * params.k for LOBPCG) and records the fastest for (L1, L2, precision,
+ * vectors) process-wide; later contexts of the same lattice reuse the record.
+ * With MOTO_AUTOTUNE=0 in the environment variant 0 is recorded untimed.
+ * moto_hvp_tuning returns the number of variants and writes the variant in
+ * use (*variant, optional) and, when this context ran the timing, the
+ * measured milliseconds per launch of each variant (ms[0 .. cap), optional;
+ * zeros otherwise).  moto_set_hvp_variant forces a variant for every later
+ * HVP of the context (-1 returns to the tuned one; MOTO_ERR_ARG when out of
+ * range); the pair-list model has its own kernel and ignores it. */
+int moto_hvp_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
+int moto_set_hvp_variant(moto_ctx* ctx, int variant);
+
 /* Failure-detection control (host side only).  Every wait inside the
  * library's kernels is bounded: a consumer warp of the streaming
  * reorthogonalisation kernel that waits for a stage of tensor copies gives up

@@ -89,6 +89,8 @@ def _load():
         "moto_perturb": (I, [P, P, P, P, Z, I, P, Z, P]),
         "moto_set_pairs": (I, [P, ctypes.POINTER(moto_pair), I]),
         "moto_set_wait_limit": (I, [P, I]),
+        "moto_hvp_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), I]),
+        "moto_set_hvp_variant": (I, [P, I]),
         "moto_pairwise_l1": (I, [P, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
         "moto_batch_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params),
@@ -111,6 +113,7 @@ EXPORTED = (
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
     "moto_perturb", "moto_pairwise_l1", "moto_set_pairs", "moto_set_wait_limit",
+    "moto_hvp_tuning", "moto_set_hvp_variant",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
@@ -265,6 +268,21 @@ def moto_descend(ctx, m_saddle, v1, params, m_plus, m_minus, out, stream=None):
                            _ptr(out), _stream(stream))
     _check(rc, "moto_descend", ok=(MOTO_OK, MOTO_NOT_CONVERGED))
     return rc
+
+
+def moto_hvp_tuning(ctx):
+    """(variant in use, [ms per launch of each variant, zeros unless this
+    context ran the autotuner])."""
+    v = ctypes.c_int()
+    ms = (ctypes.c_float * 16)()
+    n = _lib.moto_hvp_tuning(ctx, ctypes.byref(v), ms, 16)
+    if n < 0:
+        raise MotoError(f"moto_hvp_tuning: {moto_status_string(n)}")
+    return v.value, [float(ms[i]) for i in range(n)]
+
+
+def moto_set_hvp_variant(ctx, variant: int):
+    _check(_lib.moto_set_hvp_variant(ctx, int(variant)), "moto_set_hvp_variant")
 
 
 def moto_set_wait_limit(ctx, polls: int):

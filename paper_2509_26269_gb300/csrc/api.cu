@@ -50,6 +50,12 @@ struct moto_ctx {
   cudaStream_t prof_stream;
   // bound of the streaming kernel's consumer waits (moto_set_wait_limit; 0 = default)
   int wait_polls;
+  // HVP variant: forced by moto_set_hvp_variant (>= 0) or the autotuner's
+  // choice; per-variant times of the autotuner run that chose it
+  int hvp_force;
+  int hvp_nvec;
+  float hvp_ms[16];
+  int hvp_tuned_here;
 };
 
 namespace {
@@ -115,7 +121,10 @@ template <typename T>
 void P_hvp(moto_ctx* c, const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
            int nvec, const int* gate, int mask, cudaStream_t st) {
   PROF(kPkHvp, (4.0 + 6.0 * nvec) * md.N * sizeof(T));
-  launch_hvp<T>(md, m, s, V, ldv, HV, ldhv, nvec, gate, mask, st);
+  if (c->hvp_force >= 0 && md.npairs == 0)
+    launch_hvp_strip_variant<T>(c->hvp_force, md, m, s, V, ldv, HV, ldhv, nvec, gate, mask, st);
+  else
+    launch_hvp<T>(md, m, s, V, ldv, HV, ldhv, nvec, gate, mask, st);
 }
 template <typename T>
 void P_energy_grad(moto_ctx* c, const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
@@ -564,6 +573,61 @@ void lobpcg(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0, int k,
 
 }  // namespace
 
+// ----------------------------------------------------------------------------
+// Autotuner: the strip HVP comes in bit-identical variants whose speed depends
+// on the lattice and the number of vectors per call.  At context creation the
+// variants are timed once on the context's own scratch (CUDA events, one
+// warm-up launch and three timed launches each, vectors as many as the solver
+// passes per call) and the fastest is recorded process-wide for (L1, L2,
+// precision, vectors); later contexts of the same lattice reuse the record.
+// MOTO_AUTOTUNE=0 in the environment records variant 0 instead.
+// ----------------------------------------------------------------------------
+template <typename T>
+int autotune_hvp(moto_ctx* c) {
+  const int nvec = c->p.solver == MOTO_SOLVER_LANCZOS ? c->p.block : c->p.k;
+  c->hvp_nvec = nvec;
+  const int esz = (int)sizeof(T);
+  if (hvp_tuned_variant(c->md.L1, c->md.L2, esz, nvec) >= 0) return MOTO_OK;
+  const char* env = getenv("MOTO_AUTOTUNE");
+  const int nv = hvp_variant_count();
+  if (env && strcmp(env, "0") == 0) {
+    hvp_record_variant(c->md.L1, c->md.L2, esz, nvec, 0);
+    return MOTO_OK;
+  }
+  T* V = static_cast<T*>(c->basis);
+  T* HV = V + (size_t)nvec * c->ld;
+  const T* m = static_cast<const T*>(c->W);
+  const T* s = static_cast<const T*>(c->s);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < nv && v < 16; ++v) {
+    launch_hvp_strip_variant<T>(v, c->md, m, s, V, c->ld, HV, c->ld, nvec, nullptr, 0, 0);
+    cudaEventRecord(e0, 0);
+    for (int r = 0; r < 3; ++r)
+      launch_hvp_strip_variant<T>(v, c->md, m, s, V, c->ld, HV, c->ld, nvec, nullptr, 0, 0);
+    cudaEventRecord(e1, 0);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(cudaGetLastError(), "autotuner timing", __LINE__);
+    }
+    c->hvp_ms[v] = ms / 3.f;
+    if (v == 0 || c->hvp_ms[v] < best_ms) {
+      best = v;
+      best_ms = c->hvp_ms[v];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  hvp_record_variant(c->md.L1, c->md.L2, esz, nvec, best);
+  c->hvp_tuned_here = 1;
+  return MOTO_OK;
+}
+
 // ============================================================================
 // C ABI
 // ============================================================================
@@ -668,6 +732,17 @@ int moto_create(const moto_model* model, int dtype, const moto_params* params, m
     moto_destroy(c);
     return MOTO_ERR_CUDA;
   }
+  c->hvp_force = -1;
+  rc = dtype == MOTO_F32 ? autotune_hvp<float>(c) : autotune_hvp<double>(c);
+  if (rc == MOTO_OK) {
+    // the timing launches wrote the scratch: give the solvers zeroed fields again
+    cudaMemset(c->basis, 0, vb * MOTO_MAX_BASIS);
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = MOTO_ERR_CUDA;
+  }
+  if (rc != MOTO_OK) {
+    moto_destroy(c);
+    return rc;
+  }
   *out = c;
   return MOTO_OK;
 }
@@ -679,6 +754,24 @@ void moto_destroy(moto_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
+}
+
+int moto_set_hvp_variant(moto_ctx* c, int variant) {
+  if (!c || variant < -1 || variant >= hvp_variant_count()) return MOTO_ERR_ARG;
+  c->hvp_force = variant;
+  return MOTO_OK;
+}
+
+int moto_hvp_tuning(const moto_ctx* c, int* variant, float* ms, int cap) {
+  if (!c) return MOTO_ERR_ARG;
+  const int nv = hvp_variant_count();
+  if (variant) {
+    const int t = hvp_tuned_variant(c->md.L1, c->md.L2, (int)c->esize, c->hvp_nvec);
+    *variant = c->hvp_force >= 0 ? c->hvp_force : (t < 0 ? 0 : t);
+  }
+  if (ms)
+    for (int v = 0; v < cap && v < nv; ++v) ms[v] = c->hvp_tuned_here ? c->hvp_ms[v] : 0.f;
+  return nv;
 }
 
 int moto_set_wait_limit(moto_ctx* c, int polls) {

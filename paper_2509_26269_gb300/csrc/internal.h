@@ -56,10 +56,20 @@ void launch_euclid_hvp(const ModelDev& md, const T* V, size_t ldv, T* HV, size_t
 template <typename T>
 void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv, int nvec,
                 const int* gate, int mask, cudaStream_t st);
-// register-blocked column-strip HVP (kernels_hvp.cu); launch_hvp uses it
+// register-blocked column-strip HVP (kernels_hvp.cu); launch_hvp uses it with
+// the variant the autotuner recorded for the lattice (variant 0 without one)
 template <typename T>
 void launch_hvp_strip(const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV, size_t ldhv,
                       int nvec, const int* gate, int mask, cudaStream_t st);
+// The strip HVP variants (strip length, warps per block, m held in
+// registers): all give bit-identical results; only their speed differs.
+int hvp_variant_count();
+template <typename T>
+void launch_hvp_strip_variant(int variant, const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV,
+                              size_t ldhv, int nvec, const int* gate, int mask, cudaStream_t st);
+// process-wide autotuner record: (L1, L2, element size, nvec) -> variant (-1: none)
+int hvp_tuned_variant(int L1, int L2, int esize, int nvec);
+void hvp_record_variant(int L1, int L2, int esize, int nvec, int variant);
 template <typename T>
 void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st);
 

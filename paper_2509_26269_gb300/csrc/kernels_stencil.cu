@@ -1,11 +1,21 @@
-// Stencil kernels: energy + Riemannian gradient, tangent HVP, topological charge.
+// Stencil kernels: energy + Riemannian gradient, tangent HVP dispatch,
+// topological charge.
 //
-// Every kernel maps one 32 x 32 tile of sites to a 256-thread block (warp w
-// owns rows 4w..4w+3, lane = column), stages the field it differentiates in a
-// shared-memory tile with a 2-site periodic halo, and keeps the on-site
-// vectors (m_i, s_i) in registers.
+// The hot energy / gradient and charge kernels are persistent: a grid of a
+// few blocks per SM (a multiple of the 152 SMs) walks the lattice's 64 x 16
+// tiles, staging tile t + grid with asynchronous copies while tile t is
+// computed, and evaluates the stencil with the register strips of strip.cuh
+// (the staged spins serve both as the stencil field and as the on-site m_i).
+// Per-site work and block sums stay in the field precision (two-float sums
+// for FP32 fields): GB300's FP64 pipe is a small fraction of its FP32 rate,
+// so FP64 appears only in the last block's total.  The older 32 x 32-tile
+// kernel below evaluates the energy in FP64 arithmetic (moto_energy) and the
+// Euclidean gradient of the autograd path.
+#include <algorithm>
+
 #include "internal.h"
 #include "stencil.cuh"
+#include "strip.cuh"
 
 namespace moto {
 
@@ -190,63 +200,297 @@ __global__ void __launch_bounds__(kThreads) euclid_hvp_kernel(ModelDev md, const
   }
 }
 
-// Berg-Luescher charge: per site the up triangle (i, i+a1, i+a2) and the down
-// triangle (i+a1, i+a1+a2, i+a2); Omega = 2 atan2(a.(b x c), 1+a.b+b.c+c.a);
-// Q = -(1/4 pi) sum Omega.
-template <typename T, typename A>
-__device__ __forceinline__ A solid_angle(const A* a, const A* b, const A* c) {
-  const A num = a[0] * (b[1] * c[2] - b[2] * c[1]) + a[1] * (b[2] * c[0] - b[0] * c[2]) +
-                a[2] * (b[0] * c[1] - b[1] * c[0]);
-  const A den = (A)1 + (a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) + (b[0] * c[0] + b[1] * c[1] + b[2] * c[2]) +
-                (c[0] * a[0] + c[1] * a[1] + c[2] * a[2]);
-  return (A)2 * atan2(num, den);
+// ---------------------------------------------------------------------------
+// persistent strip kernels
+// ---------------------------------------------------------------------------
+namespace {
+
+// on-site hook of the energy walk: keeps the spins of the strip's sites
+template <typename T, int SW>
+struct SpinsOnSite {
+  typename strip::PK<T>::V mx[SW], my[SW], mz[SW];
+  template <int S>
+  __device__ __forceinline__ void center(const strip::RowP<T>& r, typename strip::PK<T>::V&,
+                                         typename strip::PK<T>::V&, typename strip::PK<T>::V&) {
+    mx[S] = r.x[2];
+    my[S] = r.y[2];
+    mz[S] = r.z[2];
+  }
+};
+
+__device__ __forceinline__ void tile_origin(int t, int ntx, int ty_sites, int& x0, int& y0) {
+  const int ty = t / ntx;
+  x0 = (t - ty * ntx) * strip::kTX;
+  y0 = ty * ty_sites;
+}
+
+// Fixed-order sum of one value per thread over the block (result in thread
+// 0): a shuffle tree per warp, then the warps in order.
+template <typename R>
+__device__ __forceinline__ R block_total(R v, R* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = radd(v, rshfl(v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i < nw; ++i) v = radd(v, sh[i]);
+  __syncthreads();
+  return v;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) topo_kernel(ModelDev md, const T* __restrict__ m, double* part,
-                                                        unsigned* counter, double* out) {
-  typedef T A;
-  __shared__ Tile<T> tile;
-  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-  load_tile(m, md.N, md.L1, md.L2, x0, y0, tile);
+__device__ __forceinline__ T block_maxv(T v, T* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sh[wid] = v;
   __syncthreads();
-  const int lx = threadIdx.x & 31, wy = threadIdx.x >> 5;
-  double acc = 0.0;
-#pragma unroll
-  for (int r = 0; r < kTileRowsPerThread; ++r) {
-    const int ly = wy * kTileRowsPerThread + r;
-    if (x0 + lx < md.L1 && y0 + ly < md.L2) {
-      const int cx = lx + kHalo, cy = ly + kHalo;
-      A m0[3], m1[3], m2[3], m3[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        m0[c] = tile.v[c][cy][cx];
-        m1[c] = tile.v[c][cy][cx + 1];
-        m2[c] = tile.v[c][cy + 1][cx];
-        m3[c] = tile.v[c][cy + 1][cx + 1];
-      }
-      acc += (double)solid_angle<T, A>(m0, m1, m2) + (double)solid_angle<T, A>(m1, m3, m2);
-    }
+  if (threadIdx.x == 0)
+    for (int i = 1; i < nw; ++i) v = max(v, sh[i]);
+  __syncthreads();
+  return v;
+}
+
+// Last block: totals of the per-block partials, in an order fixed by (nb,
+// blockDim): thread t adds blocks t, t + blockDim, ... in order, then the
+// block tree.  Sums come as R (two-float or FP64), maxima as T.
+template <typename T>
+__device__ __forceinline__ void last_block_totals(const typename strip::Red<T>::R* psum, const double* pmax, int nb,
+                                                  double* out_sum, double* out_max) {
+  typedef strip::Red<T> RD;
+  typedef typename RD::R R;
+  __shared__ R shr[32];
+  __shared__ double shm[32];
+  R a = RD::of((T)0);
+  double mx = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    a = radd(a, psum[b]);
+    if (pmax) mx = fmax(mx, __ldcg(pmax + b));
   }
-  __shared__ double red[8];
-  double v[1] = {acc};
-  block_sum<1>(v, red);
-  const int nblocks = gridDim.x * gridDim.y;
-  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  if (threadIdx.x == 0) part[bid] = v[0];
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)nblocks - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double a = 0.0;
-  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) a += __ldcg(part + k);
-  double w[1] = {a};
-  block_sum<1>(w, red);
+  a = block_total<R>(a, shr);
+  if (pmax) mx = block_maxv<double>(mx, shm);
   if (threadIdx.x == 0) {
-    out[0] = -w[0] / (4.0 * 3.14159265358979323846);
+    *out_sum = RD::value(a);
+    if (out_max) *out_max = mx;
+  }
+}
+
+}  // namespace
+
+// Energy and Riemannian gradient (the hot path: arithmetic in the field
+// precision).  grad_i E = h_i(m) - muB z - 2 K m_iz z; s_i = m_i . grad_i E;
+// g_i = grad_i E - s_i m_i; E = sum_i (s_i - muB m_iz) / 2 (E is quadratic in
+// m).  out = [E, max_i |g_i|].  Partials: part[0 .. grid) the block energies
+// (8-byte reduction values), part[grid .. 2 grid) the block maxima of |g|^2.
+template <typename T, int SW, int WY>
+__global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md, strip::Weights<T> hw, T muB,
+                                                                    const T* __restrict__ m, T* __restrict__ g,
+                                                                    T* __restrict__ s, double* part, unsigned* counter,
+                                                                    double* out, int* status, int aligned, int ntx,
+                                                                    int ntiles) {
+  using namespace strip;
+  constexpr int TY = SW * WY;
+  typedef Dims<TY> DM;
+  typedef PK<T> P;
+  typedef typename P::V VP;
+  typedef Red<T> RD;
+  typedef typename RD::R R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][SY][kSX]
+  __shared__ R shr[WY];
+  __shared__ T shm[WY];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int L1 = md.L1, L2 = md.L2;
+  const size_t N = md.N;
+  const WP<T> w(hw);
+  const VP nmuB = P::bc(-muB), n2K = P::bc(-hw.twoK), half = P::bc((T)0.5), neg = P::bc((T)-1);
+  R eacc = RD::of((T)0);
+  T gmax = (T)0;
+  bool bad = false;
+  int t = blockIdx.x, x0, y0;
+  if (t < ntiles) {
+    tile_origin(t, ntx, TY, x0, y0);
+    stage_tile<T, DM::SY>(tiles, m, N, L1, L2, x0, y0, aligned && tile_inside<TY>(x0, y0, L1, L2));
+  }
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      tile_origin(tn, ntx, TY, x0, y0);
+      stage_tile<T, DM::SY>(tiles + (size_t)((it + 1) & 1) * DM::kTile, m, N, L1, L2, x0, y0,
+                            aligned && tile_inside<TY>(x0, y0, L1, L2));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    tile_origin(t, ntx, TY, x0, y0);
+    SpinsOnSite<T, SW> os;
+    VP ax[SW], ay[SW], az[SW];
+    walk<T, SW, DM::SY>(tiles + (size_t)(it & 1) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
+    const int x = x0 + 2 * lane;
+    const bool two = x + 1 < L1;
+    const bool pair_store = aligned && two;
+    T etile = (T)0;
+    if (x < L1) {
+#pragma unroll
+      for (int k = 0; k < SW; ++k) {
+        const int y = y0 + wy * SW + k;
+        if (y >= L2) break;
+        const VP m0 = os.mx[k], m1 = os.my[k], m2 = os.mz[k];
+        const VP hx = ax[k], hy = ay[k];
+        const VP hz = P::add(P::fma(n2K, m2, az[k]), nmuB);
+        const VP si = P::fma(m2, hz, P::fma(m1, hy, P::mul(m0, hx)));
+        const VP nsi = P::mul(si, neg);
+        const VP gx = P::fma(nsi, m0, hx), gy = P::fma(nsi, m1, hy), gz = P::fma(nsi, m2, hz);
+        const size_t i = (size_t)y * L1 + x;
+        if (pair_store) {
+          if (g) {
+            *reinterpret_cast<VP*>(g + i) = gx;
+            *reinterpret_cast<VP*>(g + N + i) = gy;
+            *reinterpret_cast<VP*>(g + 2 * N + i) = gz;
+          }
+          if (s) *reinterpret_cast<VP*>(s + i) = si;
+        } else {
+          if (g) {
+            g[i] = gx.x;
+            g[N + i] = gy.x;
+            g[2 * N + i] = gz.x;
+          }
+          if (s) s[i] = si.x;
+          if (two) {
+            if (g) {
+              g[i + 1] = gx.y;
+              g[N + i + 1] = gy.y;
+              g[2 * N + i + 1] = gz.y;
+            }
+            if (s) s[i + 1] = si.y;
+          }
+        }
+        const VP e = P::mul(half, P::fma(nmuB, m2, si));
+        const VP g2 = P::fma(gz, gz, P::fma(gy, gy, P::mul(gx, gx)));
+        etile += e.x;
+        gmax = max(gmax, g2.x);
+        bad |= !isfinite(g2.x);
+        if (two) {
+          etile += e.y;
+          gmax = max(gmax, g2.y);
+          bad |= !isfinite(g2.y);
+        }
+      }
+    }
+    eacc = radd(eacc, RD::of(etile));
+    // every warp is done with this buffer before the copy of tile t + 2 grid
+    // (issued in the next iteration) overwrites it
+    __syncthreads();
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonfinite);
+  if (!out) return;
+  eacc = block_total<R>(eacc, shr);
+  gmax = block_maxv<T>(gmax, shm);
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+    reinterpret_cast<R*>(part)[blockIdx.x] = eacc;
+    part[nb + blockIdx.x] = (double)gmax;
+  }
+  if (!grid_last_block(counter)) return;
+  last_block_totals<T>(reinterpret_cast<const R*>(part), part + nb, nb, out, out + 1);
+  if (threadIdx.x == 0) {
+    out[1] = sqrt(out[1]);
+    *counter = 0u;
+  }
+}
+
+// Berg-Luescher charge: per site the up triangle (i, i+a1, i+a2) and the down
+// triangle (i+a1, i+a1+a2, i+a2), Omega = 2 atan2(a.(b x c), 1 + a.b + b.c +
+// c.a), Q = -(1/4 pi) sum Omega.  Solid angles and the thread's sums in the
+// field precision, block and grid sums as two-float (FP32) or FP64.
+template <typename T>
+__device__ __forceinline__ T solid_angle(T ax, T ay, T az, T bx, T by, T bz, T cx, T cy, T cz) {
+  const T num = ax * (by * cz - bz * cy) + ay * (bz * cx - bx * cz) + az * (bx * cy - by * cx);
+  const T den = (T)1 + (ax * bx + ay * by + az * bz) + (bx * cx + by * cy + bz * cz) + (cx * ax + cy * ay + cz * az);
+  return (T)2 * atan2(num, den);
+}
+
+template <typename T, int SW, int WY>
+__global__ void __launch_bounds__(32 * WY) topo_strip_kernel(ModelDev md, const T* __restrict__ m, double* part,
+                                                             unsigned* counter, double* out, int aligned, int ntx,
+                                                             int ntiles) {
+  using namespace strip;
+  constexpr int TY = SW * WY;
+  typedef Dims<TY> DM;
+  typedef Red<T> RD;
+  typedef typename RD::R R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tiles = reinterpret_cast<T*>(smem_raw);
+  __shared__ R shr[WY];
+  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+  const int L1 = md.L1, L2 = md.L2;
+  const size_t N = md.N;
+  R acc = RD::of((T)0);
+  int t = blockIdx.x, x0, y0;
+  if (t < ntiles) {
+    tile_origin(t, ntx, TY, x0, y0);
+    stage_tile<T, DM::SY>(tiles, m, N, L1, L2, x0, y0, aligned && tile_inside<TY>(x0, y0, L1, L2));
+  }
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    if (tn < ntiles) {
+      tile_origin(tn, ntx, TY, x0, y0);
+      stage_tile<T, DM::SY>(tiles + (size_t)((it + 1) & 1) * DM::kTile, m, N, L1, L2, x0, y0,
+                            aligned && tile_inside<TY>(x0, y0, L1, L2));
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    tile_origin(t, ntx, TY, x0, y0);
+    const T* tile = tiles + (size_t)(it & 1) * DM::kTile;
+    const int x = x0 + 2 * lane;
+    T qt = (T)0;
+    if (x < L1) {
+      const bool two = x + 1 < L1;
+      // staged column of x is 2 lane + kPadL, staged row of y is y - y0 + 2;
+      // the walk holds columns x, x + 1, x + 2 of the current and next rows
+      T c[2][3][3];
+      const int lx = 2 * lane + kPadL;
+#pragma unroll
+      for (int k = 0; k <= SW; ++k) {
+        const int ly = wy * SW + k + 2;
+        const int cur = k & 1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const T* row = tile + (size_t)q * DM::kPlane + (size_t)ly * kSX + lx;
+          const typename PK<T>::V p01 = *reinterpret_cast<const typename PK<T>::V*>(row);
+          c[cur][q][0] = p01.x;
+          c[cur][q][1] = p01.y;
+          c[cur][q][2] = row[2];
+        }
+        if (k > 0) {
+          const int y = y0 + wy * SW + k - 1;
+          if (y < L2) {
+            const int pr = cur ^ 1;  // row y; cur holds row y + 1
+#define M_(r, col) c[r][0][col], c[r][1][col], c[r][2][col]
+            qt += solid_angle<T>(M_(pr, 0), M_(pr, 1), M_(cur, 0)) + solid_angle<T>(M_(pr, 1), M_(cur, 1), M_(cur, 0));
+            if (two)
+              qt += solid_angle<T>(M_(pr, 1), M_(pr, 2), M_(cur, 1)) +
+                    solid_angle<T>(M_(pr, 2), M_(cur, 2), M_(cur, 1));
+#undef M_
+          }
+        }
+      }
+    }
+    acc = radd(acc, RD::of(qt));
+    __syncthreads();
+  }
+  acc = block_total<R>(acc, shr);
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) reinterpret_cast<R*>(part)[blockIdx.x] = acc;
+  if (!grid_last_block(counter)) return;
+  double q = 0.0;
+  last_block_totals<T>(reinterpret_cast<const R*>(part), nullptr, nb, &q, nullptr);
+  if (threadIdx.x == 0) {
+    out[0] = -q / (4.0 * 3.14159265358979323846);
     *counter = 0u;
   }
 }
@@ -258,17 +502,66 @@ static dim3 tile_grid(const ModelDev& md) {
   return dim3((md.L1 + kTileX - 1) / kTileX, (md.L2 + kTileY - 1) / kTileY);
 }
 
+// persistent strip kernels: at most this many blocks an SM
+constexpr int kStripMaxBps = 8;
+constexpr int kStripSW = 4, kStripWY = 4;  // 64 x 16-site tiles, 128 threads
+
 long long stencil_blocks(int L1, int L2) {
-  return (((long long)L1 + kTileX - 1) / kTileX) * (((long long)L2 + kTileY - 1) / kTileY);
+  const long long old_tiles = (((long long)L1 + kTileX - 1) / kTileX) * (((long long)L2 + kTileY - 1) / kTileY);
+  const long long strip_tiles = (((long long)L1 + strip::kTX - 1) / strip::kTX) *
+                                (((long long)L2 + kStripSW * kStripWY - 1) / (kStripSW * kStripWY));
+  return std::max(old_tiles, std::min(strip_tiles, (long long)kSMs * kStripMaxBps));
 }
 
 int tile_blocks(const ModelDev& md) { return (int)stencil_blocks(md.L1, md.L2); }
+
+namespace {
+
+// Blocks an SM of a persistent strip kernel (occupancy with its shared
+// memory, at most kStripMaxBps), queried once per kernel.
+template <typename K>
+int strip_bps(K kernel, int threads, size_t smem, int& cache) {
+  if (cache == 0) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess || b < 1) b = 1;
+    cache = std::min(b, kStripMaxBps);
+  }
+  return cache;
+}
+
+template <typename T>
+bool al16(const void* p) {
+  return p == nullptr || ((uintptr_t)p % 16) == 0;
+}
+
+template <typename T>
+void launch_energy_grad_strip(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
+                              double* out, int* status, cudaStream_t st) {
+  constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
+  const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  const size_t smem = 2 * strip::Dims<TY>::kTile * sizeof(T);
+  static int bps_cache = 0;
+  const int bps = strip_bps(energy_grad_strip_kernel<T, SW, WY>, 32 * WY, smem, bps_cache);
+  const int grid = std::min(ntiles, kSMs * bps);
+  constexpr int kE = 16 / (int)sizeof(T);
+  const int aligned = (md.L1 % kE == 0) && al16<T>(m) && al16<T>(g) && al16<T>(s);
+  energy_grad_strip_kernel<T, SW, WY><<<grid, 32 * WY, smem, st>>>(
+      md, strip::make_weights<T>(md), (T)md.muB, m, g, s, part, counter, out, status, aligned, ntx, ntiles);
+}
+
+}  // namespace
 
 template <typename T>
 void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
                         int* status, bool fp64_arith, cudaStream_t st, bool euclid) {
   if (md.npairs > 0) {
     launch_pair_energy_grad<T>(md, m, g, s, part, counter, out, status, fp64_arith, euclid, st);
+    return;
+  }
+  if (!fp64_arith && !euclid) {
+    launch_energy_grad_strip<T>(md, m, g, s, part, counter, out, status, st);
     return;
   }
   const int e = euclid ? 1 : 0;
@@ -299,7 +592,16 @@ void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t l
 
 template <typename T>
 void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st) {
-  topo_kernel<T><<<tile_grid(md), kThreads, 0, st>>>(md, m, part, counter, out);
+  constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
+  const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  const size_t smem = 2 * strip::Dims<TY>::kTile * sizeof(T);
+  static int bps_cache = 0;
+  const int bps = strip_bps(topo_strip_kernel<T, SW, WY>, 32 * WY, smem, bps_cache);
+  const int grid = std::min(ntiles, kSMs * bps);
+  constexpr int kE = 16 / (int)sizeof(T);
+  const int aligned = (md.L1 % kE == 0) && al16<T>(m);
+  topo_strip_kernel<T, SW, WY><<<grid, 32 * WY, smem, st>>>(md, m, part, counter, out, aligned, ntx, ntiles);
 }
 
 #define INST(T)                                                                                               \

@@ -77,12 +77,35 @@ def test_batch_equals_walkers_run_alone(dtype):
         np.testing.assert_array_equal(b["out"][i][:4], s["out"][i][:4])
 
 
+def oracle_certify(M, m_gpu, V_gpu, steps=30, dense_max_sites=1600, max_refine=50):
+    """The saddle rule for a saddle found in FP32 (MMF is path-dependent, so
+    the oracle checks the end point rather than the trajectory): at the GPU's
+    spins, in FP64, the oracle recomputes the gradient, its own two lowest
+    modes (block Lanczos from the GPU modes) and the reflected force; then
+    refines with its own MMF ascent (at most 50 steps) from the GPU's spins.
+    Returns a dict of what the checks need."""
+    from oracle import krylov, mmf
+    g, s = spin.riemann_grad(M, m_gpu)
+    lam, V = krylov.block_lanczos_modes(M, m_gpu, s, [V_gpu[0], V_gpu[1]], steps, 2)
+    Fm = mmf.reflected_force(-g, V[0])
+    P = mmf.MMFParams(k=2, solver="block_lanczos", krylov_steps=steps, max_steps=max_refine, tau_F=1e-3)
+    res = mmf.ascend(M, m_gpu, [V_gpu[0], V_gpu[1]], P)
+    out = dict(lam=lam, fmax=mmf.max_torque(Fm), refine=res,
+               dE=abs(spin.energy(M, res.m) - spin.energy(M, m_gpu)),
+               dev=float(np.sqrt(np.max(np.sum((res.m - m_gpu) ** 2, axis=0)))))
+    if M.N <= dense_max_sites:
+        out["dense"] = np.linalg.eigvalsh(spin.dense_tangent_hessian(M, res.m)[0])[:3]
+    return out
+
+
 def test_batched_walkers_certify_saddles_fp32():
     """Explorer-style walkers (random charge, masked perturbation) on mixed
-    lattices, k = 2 block Lanczos, FP32: every walker the batch reports at a
-    saddle passes the saddle test in the oracle's FP64 arithmetic on its
-    stored spins (|F_mmf| from the GPU modes, lambda_1 < 0 < lambda_2 from the
-    rec, the energy recomputed)."""
+    lattices, k = 2 block Lanczos, FP32.  Every walker the batch reports at a
+    saddle is certified by the oracle in FP64 on its stored spins: the oracle's
+    own minimum modes give lambda_1 < 0 < lambda_2 and a reflected force within
+    a few times tau_F, and its own MMF ascent started there converges within 50
+    steps to a saddle within 1e-4 meV and 1e-3 rad of the GPU's, index 1 in the
+    dense spectrum where the lattice is small enough (N <= 1600)."""
     require_gpu()
     sides = [32, 40, 48, 32, 40, 48]
     # these walkers reach their saddles in 350-900 outer steps
@@ -106,8 +129,17 @@ def test_batched_walkers_certify_saddles_fp32():
         ok += 1
         M = Model(L, L, **FULL)
         mo = to_np(dev[i][0])
+        Vo = to_np(dev[i][1])
+        # the GPU's record describes the stored spins (FP32 force below tau_F)
         assert rec[i, 1] <= params["tau_F"]
-        assert rec[i, 2] < 0.0 < rec[i, 3]
         assert spin.energy(M, mo) == pytest.approx(rec[i, 0], rel=1e-6)
+        c = oracle_certify(M, mo, Vo)
+        assert c["lam"][0] < 0.0 < c["lam"][1], (i, c["lam"][:3])
+        assert c["fmax"] <= 5 * params["tau_F"], (i, c["fmax"])
+        assert c["refine"].converged and c["refine"].steps <= 50, (i, c["refine"].steps)
+        assert c["dE"] <= 1e-4, (i, c["dE"])
+        assert c["dev"] < 1e-3, (i, c["dev"])
+        if "dense" in c:
+            assert c["dense"][0] < 0.0 < c["dense"][1], (i, c["dense"])
     assert ok >= 4
     b.close()
