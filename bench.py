@@ -299,7 +299,8 @@ def run_ours(args, rank, world, local):
     # nonlinear CG instead of L-BFGS, and the subspace reflection over all k
     # modes: a few steps each from the same start, CUDA-event timed
     variants = {}
-    for vname, over in (("cg", {"optimizer": mo.MOTO_OPT_CG}), ("subspace_k8", {"subspace": 1})):
+    for vname, over in (("cg", {"optimizer": mo.MOTO_OPT_CG}), ("subspace_k8", {"subspace": 1}),
+                        ("selective_reorth", {"reorth": mo.MOTO_REORTH_SELECTIVE})):
         pv = mo.make_params(**{f: getattr(params, f) for f, _ in params._fields_})
         for f, v in over.items():
             setattr(pv, f, v)

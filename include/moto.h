@@ -71,6 +71,19 @@ enum {
   MOTO_DESCENT_LLG = 1   /* damped spin dynamics (Landau-Lifshitz-Gilbert, Heun) */
 };
 
+/* Reorthogonalisation of block Lanczos.  FULL: every new block is
+ * orthogonalised against the whole basis (the three-term local pass, then one
+ * pass against every block).  SELECTIVE: the local pass only, while a block
+ * form of Simon's estimate of the loss of orthogonality (the omega
+ * recurrence; Simon 1984) stays below sqrt(eps) of the field precision; when
+ * it crosses, the new block and the next one get the full pass (partial
+ * reorthogonalisation: the basis stays semi-orthogonal, which keeps the Ritz
+ * values as accurate as with full reorthogonalisation). */
+enum {
+  MOTO_REORTH_FULL = 0,
+  MOTO_REORTH_SELECTIVE = 1
+};
+
 /* Outer-layer optimiser (Results, "Bilayer MMF": "LBFGS or CG"). */
 enum {
   MOTO_OPT_LBFGS = 0,  /* tangent-space L-BFGS two-loop, step cap theta_max, no line search */
@@ -125,6 +138,10 @@ typedef struct {
   double llg_alpha;   /* Gilbert damping of the LLG descent                    (1.0) */
   double llg_dt;      /* LLG time step, hbar/meV (0.6582 ps)                   (0.01) */
   double llg_time;    /* LLG duration per side, hbar/meV            (75.96 = 50 ps) */
+  int reorth;         /* MOTO_REORTH_*, block Lanczos reorthogonalisation       (FULL) */
+  double tau_lambda;  /* curvature threshold of the saddle test: lambda_1 < -tau_lambda
+                         and lambda_2 > -tau_lambda (0: the printed test
+                         lambda_1 < 0 < lambda_2), meV                        (0) */
 } moto_params;
 
 /* One ordered pair (i, i + d) of a pair-list Hamiltonian, d = d1 a1 + d2 a2
@@ -348,6 +365,16 @@ int moto_batch_descend(moto_batch* batch, void* const* m_plus, void* const* m_mi
 int moto_status(moto_ctx* ctx, void* stream);
 /* Clears the context's device status word (enqueued on the stream). */
 int moto_clear_status(moto_ctx* ctx, void* stream);
+
+/* Diagnostics of the last block Lanczos solve of the context (synchronises
+ * the stream): *basis_dev receives the device address of its Krylov basis
+ * (*nvec fields at element stride *ld, read-only, valid until the next solver
+ * call of the context), *reorth_steps the number of steps that ran the full
+ * pass against the basis (all of them with MOTO_REORTH_FULL, those the
+ * orthogonality estimate asked for with MOTO_REORTH_SELECTIVE).  Each output
+ * pointer is optional.  With moto_gram this measures Q^T Q - I. */
+int moto_krylov_basis(moto_ctx* ctx, const void** basis_dev, size_t* ld, int* nvec, int* reorth_steps,
+                      void* stream);
 
 /* HVP autotuner.  The strip HVP kernel exists in several variants (strip
  * length, warps per block, spins held in registers) that give bit-identical

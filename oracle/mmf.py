@@ -40,6 +40,12 @@ downhill).  Readings where the paper gives no rule:
   Barzilai & Borwein 1988, the same scale L-BFGS starts from), capped at
   theta_max per spin.  (A fixed alpha = gamma0 was tried first: on the
   32 x 32 workload it did not reach a saddle in 300 steps.)
+* [R22] The saddle test's curvature threshold: Algorithm 1 takes thresholds
+  (tau_F, tau_lambda) as inputs but prints the test as lambda_1 < 0 <
+  lambda_2.  Read with tau_lambda: lambda_1 < -tau_lambda (one clearly
+  negative curvature) and lambda_2 > -tau_lambda (no second one beyond the
+  resolution of the curvatures, e.g. a soft translation mode of a texture on
+  the periodic lattice); tau_lambda = 0 (the default) is the printed test.
 * [R20] Dynamic certifier (Supplementary Note 1 (iii), "or dynamic simulator";
   Supplementary Note 2: atomistic spin dynamics, Gilbert damping alpha = 1,
   T = 1e-6, 50 ps): the Landau-Lifshitz-Gilbert equation in the
@@ -83,6 +89,7 @@ class MMFParams:
     llg_alpha: float = 1.0         # Gilbert damping
     llg_dt: float = 0.01           # hbar/meV
     llg_time: float = 50.0 / 0.6582119569  # 50 ps in hbar/meV
+    tau_lambda: float = 0.0        # curvature threshold of the saddle test (R22)
 
 
 def _dot(a, b) -> float:
@@ -233,9 +240,12 @@ def reflected_force_subspace(F: np.ndarray, V) -> np.ndarray:
     return out
 
 
-def saddle_test(fmax: float, lam, tau_F: float) -> bool:
-    """|F_mmf| <= tau_F and lambda_1 < 0 < lambda_2 (Algorithm 1)."""
-    return fmax <= tau_F and lam[0] < 0.0 < lam[1]
+def saddle_test(fmax: float, lam, tau_F: float, tau_lambda: float = 0.0) -> bool:
+    """|F_mmf| <= tau_F and lambda_1 < 0 < lambda_2 (Algorithm 1), read with
+    the curvature threshold tau_lambda that Algorithm 1 takes as an input
+    (R22): lambda_1 < -tau_lambda and lambda_2 > -tau_lambda; tau_lambda = 0
+    is the printed test."""
+    return fmax <= tau_F and lam[0] < -tau_lambda and lam[1] > -tau_lambda
 
 
 def ascend(model, m0: np.ndarray, start: list, p: MMFParams) -> AscentResult:
@@ -256,7 +266,7 @@ def ascend(model, m0: np.ndarray, start: list, p: MMFParams) -> AscentResult:
         Fm = reflected_force_subspace(F, V[:p.k]) if p.subspace else reflected_force(F, v1)
         fmax = max_torque(Fm)
         trace.append(dict(E=spin.energy(model, m), fmax=fmax, lam1=float(lam[0]), lam2=float(lam[1])))
-        if saddle_test(fmax, lam, p.tau_F):
+        if saddle_test(fmax, lam, p.tau_F, p.tau_lambda):
             converged = True
             break
         if step == p.max_steps:

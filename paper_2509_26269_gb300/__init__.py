@@ -22,6 +22,7 @@ MOTO_ERR_NONFINITE, MOTO_ERR_TIMEOUT, MOTO_ERR_NOMEM = -4, -5, -6
 MOTO_SOLVER_LANCZOS, MOTO_SOLVER_LOBPCG = 0, 1
 MOTO_OPT_LBFGS, MOTO_OPT_CG = 0, 1
 MOTO_DESCENT_OPT, MOTO_DESCENT_LLG = 0, 1
+MOTO_REORTH_FULL, MOTO_REORTH_SELECTIVE = 0, 1
 MOTO_MAX_POP = 64
 MOTO_MAX_PAIRS, MOTO_MAX_REACH = 128, 8
 MOTO_MAX_K, MOTO_MAX_BASIS, MOTO_MAX_MEM = 8, 96, 8
@@ -42,6 +43,7 @@ class moto_params(ctypes.Structure):
         ("eta_theta", ctypes.c_double), ("max_steps", ctypes.c_int), ("descent_max_steps", ctypes.c_int),
         ("optimizer", ctypes.c_int), ("subspace", ctypes.c_int), ("descent", ctypes.c_int),
         ("llg_alpha", ctypes.c_double), ("llg_dt", ctypes.c_double), ("llg_time", ctypes.c_double),
+        ("reorth", ctypes.c_int), ("tau_lambda", ctypes.c_double),
     ]
 
 
@@ -91,6 +93,8 @@ def _load():
         "moto_set_wait_limit": (I, [P, I]),
         "moto_hvp_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), I]),
         "moto_set_hvp_variant": (I, [P, I]),
+        "moto_krylov_basis": (I, [P, ctypes.POINTER(P), ctypes.POINTER(Z), ctypes.POINTER(I), ctypes.POINTER(I),
+                                  P]),
         "moto_pairwise_l1": (I, [P, P, Z, I, P, P]),
         "moto_profile_end": (I, [P, I, P, P, P]),
         "moto_batch_create": (I, [ctypes.POINTER(moto_model), I, ctypes.POINTER(moto_params),
@@ -113,7 +117,7 @@ EXPORTED = (
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
     "moto_perturb", "moto_pairwise_l1", "moto_set_pairs", "moto_set_wait_limit",
-    "moto_hvp_tuning", "moto_set_hvp_variant",
+    "moto_hvp_tuning", "moto_set_hvp_variant", "moto_krylov_basis",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
@@ -279,6 +283,15 @@ def moto_hvp_tuning(ctx):
     if n < 0:
         raise MotoError(f"moto_hvp_tuning: {moto_status_string(n)}")
     return v.value, [float(ms[i]) for i in range(n)]
+
+
+def moto_krylov_basis(ctx, stream=None):
+    """(device address of the last block Lanczos basis, element stride,
+    number of basis fields, steps with a full reorthogonalisation pass)."""
+    b, ld, nv, nr = ctypes.c_void_p(), ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.moto_krylov_basis(ctx, ctypes.byref(b), ctypes.byref(ld), ctypes.byref(nv), ctypes.byref(nr),
+                                  _stream(stream)), "moto_krylov_basis")
+    return b.value, ld.value, nv.value, nr.value
 
 
 def moto_set_hvp_variant(ctx, variant: int):

@@ -56,6 +56,7 @@ struct moto_ctx {
   int hvp_nvec;
   float hvp_ms[16];
   int hvp_tuned_here;
+  int last_selective;  // the last block Lanczos solve reorthogonalised selectively
 };
 
 namespace {
@@ -275,7 +276,15 @@ SMALL_WRAP(lbfgs_solve)
 SMALL_WRAP(saddle_test)
 SMALL_WRAP(cg_coeffs)
 SMALL_WRAP(arnoldi_diag)
+SMALL_WRAP(omega_estimate)
+SMALL_WRAP(omega_reset)
 #undef SMALL_WRAP
+// Cholesky QR pass that also skips when a gate bit of `skip` is set
+void P_cholqr_skip(moto_ctx* c, const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T,
+                   int ldT, DevState* dst, double rel, int skip, cudaStream_t st) {
+  PROF(kPkSmall, 0.0);
+  launch_cholqr(G, b, second, j, Rinv, Racc, T, ldT, dst, rel, st, skip);
+}
 void P_tridiag_eig(moto_ctx* c, const double* T, int ldT, int band, double* theta, double* Y, int k, DevState* dst,
                    cudaStream_t st) {
   PROF(kPkEig, 0.0);
@@ -310,7 +319,8 @@ constexpr size_t kLobC = kLobM + 9 * MOTO_MAX_K * MOTO_MAX_K;      // 3K x 2K co
 constexpr size_t kLobAux = kLobC + 6 * MOTO_MAX_K * MOTO_MAX_K;    // 64 aux
 constexpr size_t kMmfDots = kLobAux + 64 * MOTO_MAX_K;             // MAX_K: g . V_c (subspace force)
 constexpr size_t kCg = kMmfDots + MOTO_MAX_K;                      // 12: Gram of [G, s, y], |G_prev|^2, beta, alpha
-constexpr size_t kDsmSize = kCg + 12;
+constexpr size_t kOm = kCg + 12;                                   // MAX_BASIS^2: orthogonality estimates
+constexpr size_t kDsmSize = kOm + MOTO_MAX_BASIS * MOTO_MAX_BASIS;
 
 constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
 
@@ -338,7 +348,10 @@ __global__ void state_kernel(DevState* st, int op) {
   if (threadIdx.x != 0) return;
   switch (op) {
     case 0:  // begin Krylov solve
-      st->gate &= ~kGateKrylov;
+      st->gate &= ~(kGateKrylov | kGateNoReorth);
+      st->pad[3] = 0;
+      st->pad[4] = 0;
+      st->pad[5] = 0;
       st->steps = 0;
       st->nT = 0;
       st->tnorm = 0.0;
@@ -396,6 +409,8 @@ int check_params(const moto_params* p) {
   if (p->descent != MOTO_DESCENT_OPT && p->descent != MOTO_DESCENT_LLG) return MOTO_ERR_ARG;
   if (!(p->llg_alpha >= 0.0) || !(p->llg_dt > 0.0) || !(p->llg_time >= 0.0)) return MOTO_ERR_ARG;
   if (p->descent == MOTO_DESCENT_LLG && p->llg_time / p->llg_dt > 1e8) return MOTO_ERR_ARG;
+  if (p->reorth != MOTO_REORTH_FULL && p->reorth != MOTO_REORTH_SELECTIVE) return MOTO_ERR_ARG;
+  if (!(p->tau_lambda >= 0.0) || !std::isfinite(p->tau_lambda)) return MOTO_ERR_ARG;
   return MOTO_OK;
 }
 
@@ -405,7 +420,7 @@ int check_params(const moto_params* p) {
 // ----------------------------------------------------------------------------
 template <typename T>
 void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0, int b, int steps, T* V, size_t ldv,
-                   int nout, double* lam, cudaStream_t st) {
+                   int nout, double* lam, cudaStream_t st, bool selective = false) {
   const int N = c->N;
   const size_t n3 = c->n3, ld = c->ld;
   T* Q = static_cast<T*>(c->basis);
@@ -414,6 +429,9 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   int* gate = &c->st->gate;
   const int mk = kGateKrylov | kGateDone;
   const double rel = (c->dtype == MOTO_F64) ? 1e-12 : 1e-6;
+  // unit roundoff of the stored fields (selective reorthogonalisation)
+  const double eps = (c->dtype == MOTO_F64) ? 0x1p-53 : 0x1p-24;
+  c->last_selective = selective ? 1 : 0;
   state_kernel<<<1, 32, 0, st>>>(c->st, 0);
   // start block: project, Cholesky QR twice
   P_project<T>(c, m, v0, ld0, W, ld, b, N, gate, kGateDone, st);
@@ -440,9 +458,23 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
     // T(j, j) = sym(Q_j^T H Q_j); local coefficients [R_j^T; T(j, j)]
     P_lanczos_coeffs(c, D + kC, b, j, D + kT, kLd, D + kC3, c->st, st);
     if (j == steps - 1) break;
-    P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC3, nullptr, D + kC2, gate, mk, st);
-    P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st, D + kC3, (j - jl) * b, (jl + 1) * b);
-    P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+    if (selective) {
+      // local three-term pass, stored, with the Gram of its result; the
+      // tentative factor feeds the orthogonality estimate, which decides
+      // whether the full pass against the basis (mode-0 Gram, then the
+      // update with the Cholesky Gram) runs this step
+      P_tile<T>(c, 2, Q + (size_t)(j - jl) * b * ld, (jl + 1) * b, 0, 0, W, b, D + kC3, W, D + kG, gate, mk, st);
+      P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+      P_omega_estimate(c, b, j, D + kT, kLd, D + kRacc, D + kOm, c->st, eps, st);
+      P_tile<T>(c, 0, Q, nq, 0, 0, W, b, nullptr, nullptr, D + kC2, gate, mk | kGateNoReorth, st);
+      P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk | kGateNoReorth, st);
+      P_cholqr_skip(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, kGateNoReorth, st);
+      P_omega_reset(c, b, j, D + kRacc, D + kOm, c->st, eps, st);
+    } else {
+      P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC3, nullptr, D + kC2, gate, mk, st);
+      P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st, D + kC3, (j - jl) * b, (jl + 1) * b);
+      P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
+    }
     P_chol2_gram<T>(c, W, b, D + kRinv, D + kG, gate, mk, st);
     P_cholqr(c, D + kG, b, 1, j, D + kRinv2, D + kRacc, D + kT, kLd, c->st, rel, st);
     P_combine2<T>(c, W, b, D + kRinv, D + kRinv2, Q + (size_t)(j + 1) * b * ld, m, gate, mk, st);
@@ -654,6 +686,8 @@ void moto_default_params(moto_params* p) {
   p->llg_alpha = 1.0;
   p->llg_dt = 0.01;
   p->llg_time = 50.0 / 0.6582119569;  // 50 ps in hbar/meV
+  p->reorth = MOTO_REORTH_FULL;
+  p->tau_lambda = 0.0;
 }
 
 const char* moto_status_string(int code) {
@@ -772,6 +806,19 @@ int moto_hvp_tuning(const moto_ctx* c, int* variant, float* ms, int cap) {
   if (ms)
     for (int v = 0; v < cap && v < nv; ++v) ms[v] = c->hvp_tuned_here ? c->hvp_ms[v] : 0.f;
   return nv;
+}
+
+int moto_krylov_basis(moto_ctx* c, const void** basis_dev, size_t* ld, int* nvec, int* reorth_steps,
+                      void* stream) {
+  if (!c) return MOTO_ERR_ARG;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
+  CK(cudaStreamSynchronize(S(stream)));
+  if (basis_dev) *basis_dev = c->basis;
+  if (ld) *ld = c->ld;
+  if (nvec) *nvec = h.nT;
+  if (reorth_steps) *reorth_steps = c->last_selective ? h.pad[4] : std::max(h.steps - 1, 0);
+  return MOTO_OK;
 }
 
 int moto_set_wait_limit(moto_ctx* c, int polls) {
@@ -936,7 +983,8 @@ template <typename T>
 void lowest_modes_impl(moto_ctx* c, const T* m, const T* s, const moto_params* p, const T* v0, size_t ld0, T* V,
                        size_t ldv, int nout, double* lam, cudaStream_t st) {
   if (p->solver == MOTO_SOLVER_LANCZOS) {
-    block_lanczos<T>(c, m, s, v0, ld0, p->block, p->krylov_steps, V, ldv, nout, lam, st);
+    block_lanczos<T>(c, m, s, v0, ld0, p->block, p->krylov_steps, V, ldv, nout, lam, st,
+                     p->reorth == MOTO_REORTH_SELECTIVE);
   } else {
     lobpcg<T>(c, m, s, v0, ld0, p->k, p->max_iter, p->tol, V, ldv, lam, st);
   }
@@ -974,8 +1022,8 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
   } else {
     P_mmf_force<T>(c, g, nullptr, n3, 0, D + kMmfDots, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
   }
-  P_saddle_test(c, D + kEG, D + kFmax, lam, D + kMmfDots, p->tau_F, out6, status, c->st, ascent ? 1 : 0,
-                update ? 0 : 1, st);
+  P_saddle_test(c, D + kEG, D + kFmax, lam, D + kMmfDots, p->tau_F, p->tau_lambda, out6, status, c->st,
+                ascent ? 1 : 0, update ? 0 : 1, st);
   if (!update) return;
   if (p->optimizer == MOTO_OPT_CG) {
     // nonlinear CG: the pair s = P d_prev, y = G - P G_prev (staging fields),
@@ -1057,8 +1105,8 @@ int run_llg(moto_ctx* c, T* m, const moto_params* p, int check_every, int* steps
   memset(&h, 0, sizeof(h));
   for (long t = 0; t <= nmax; ++t) {
     P_energy_grad<T>(c, c->md, m, g0, nullptr, c->part, c->counter, D + kEG, &c->st->status, false, st);
-    P_saddle_test(c, D + kEG, D + kFmax, D + kTheta, D + kMmfDots, p->tau_F, D + kTmp, nullptr, c->st, 0,
-                  t == nmax ? 1 : 0, st);
+    P_saddle_test(c, D + kEG, D + kFmax, D + kTheta, D + kMmfDots, p->tau_F, p->tau_lambda, D + kTmp, nullptr,
+                  c->st, 0, t == nmax ? 1 : 0, st);
     if (t < nmax) {
       P_llg_predict<T>(c, m, g0, mp, p->llg_alpha, p->llg_dt, N, gate, kGateDone, st);
       P_energy_grad<T>(c, c->md, mp, g1, nullptr, c->part, c->counter, D + kTmp + 2, &c->st->status, false, st);

@@ -12,6 +12,7 @@ namespace moto {
 enum : int {
   kGateKrylov = 1,  // the Krylov recurrence broke down; skip its remaining steps
   kGateDone = 2,    // the ascent / descent has converged; skip the rest
+  kGateNoReorth = 4,  // selective reorthogonalisation: this step keeps the local pass only
 };
 
 // Device-side bookkeeping of one eigensolve / optimisation, in device memory.
@@ -25,7 +26,10 @@ struct DevState {
   int lb_count;    // L-BFGS ring: pairs held
   int lb_have_prev;
   int converged;   // 1 once the stopping test passed
-  int pad[7];      // pad[0]: current LOBPCG set; pad[1]: outer steps taken
+  int pad[7];      // pad[0]: current LOBPCG set; pad[1]: outer steps taken;
+                   // pad[2]: CG restart; pad[3]: force a full pass on the next
+                   // Lanczos step; pad[4]: steps reorthogonalised in full this
+                   // solve; pad[5]: the current step's full pass was forced
   double tnorm;    // running estimate of |T| (largest row sum seen)
   double hnorm;    // LOBPCG: largest |theta| seen
   double scale;    // step scale of the current direction
@@ -145,7 +149,13 @@ void launch_lanczos_coeffs(const double* A, int b, int j, double* T, int ldT, do
 // T(j+1, j) / T(j, j+1) (when j >= 0) and st->steps advanced.  Breakdown sets
 // kGateKrylov.
 void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T, int ldT,
-                   DevState* st, double rel_tol, cudaStream_t s);
+                   DevState* st, double rel_tol, cudaStream_t s, int skip = 0);
+// Selective reorthogonalisation (kernels_omega.cu): estimates of Q_{j+1}^T Q_k
+// from the block recurrence, the decision (gate bit kGateNoReorth), and the
+// restart of the estimates after a full pass.  Om: MOTO_MAX_BASIS^2 doubles.
+void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, DevState* st,
+                           double eps, cudaStream_t s);
+void launch_omega_reset(int b, int j, const double* Rn, double* Om, DevState* st, double eps, cudaStream_t s);
 // Symmetric eigensolver (cyclic Jacobi, FP64) on the leading nT x nT block of
 // T (nT read from st->nT, <= 96): theta ascending (MOTO_MAX_BASIS entries,
 // +inf padded) and the first k eigenvectors as an (nT x k) coefficient matrix Y.
@@ -217,7 +227,7 @@ void launch_llg_correct(T* m, const T* g0, const T* mp, const T* g1, double alph
                         const int* gate, int mask, cudaStream_t st);
 
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
-                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, int last,
-                        cudaStream_t st);
+                        double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst, int ascent,
+                        int last, cudaStream_t st);
 
 }  // namespace moto

@@ -1,0 +1,145 @@
+// Estimated loss of orthogonality of block Lanczos, for selective (partial)
+// reorthogonalisation.
+//
+// Block Lanczos satisfies H Q_k = Q_{k-1} B_k^T + Q_k A_k + Q_{k+1} B_{k+1} up
+// to rounding, with A_k = T(k, k) symmetric and B_{k+1} = T(k+1, k) the upper
+// triangular factor of the new block.  Writing W_{i,k} = Q_i^T Q_k and using
+// the symmetry of H (Q_j^T H Q_k = (Q_k^T H Q_j)^T) gives the block form of
+// Simon's omega recurrence (Simon 1984):
+//   B_{j+1}^T W_{j+1,k} = W_{j,k+1} B_{k+1} + W_{j,k} A_k - A_j W_{j,k}
+//                         + W_{j,k-1} B_k^T - B_j W_{j-1,k}        (k < j)
+// with W_{k,k} = I.  The estimates add, with the sign of each entry, a
+// rounding term nu = eps |T| / min diag(B_{j+1}) (the size of the local
+// rounding error of one step magnified by B_{j+1}^{-1}), and take
+// W_{j+1,j} = nu for the local orthogonality the three-term pass and the
+// Cholesky QR keep.  When the largest |W_{j+1,k}| exceeds sqrt(eps) (or the
+// previous step was reorthogonalised because of the estimate: Simon's rule
+// of two consecutive blocks) the new block gets the full pass against the
+// basis; its estimates then restart at nu.
+//
+// The estimates live in an MOTO_MAX_BASIS x MOTO_MAX_BASIS FP64 matrix Om
+// (block (i, k) at rows i b .., columns k b ..); the decision is the gate bit
+// kGateNoReorth, which the full-pass launches of the step test.
+#include "internal.h"
+
+namespace moto {
+
+namespace {
+constexpr int kLdO = MOTO_MAX_BASIS;
+
+__device__ __forceinline__ double tblk(const double* T, int ldT, int b, int i, int k, int r, int c) {
+  return T[(size_t)(i * b + r) * ldT + k * b + c];
+}
+}  // namespace
+
+// Block row j + 1 of the estimates from rows j and j - 1 (k < j), the
+// decision, and W_{j+1,j} = nu.  Rn: the (tentative) B_{j+1}, b x b row-major.
+// One block of 1024 threads; thread (k, r, c) forms one entry of the
+// right-hand side, thread (k, c) solves one column of the triangular system.
+__global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, const double* T, int ldT,
+                                                              const double* Rn, double* Om, DevState* st,
+                                                              double eps) {
+  if (st->gate & (kGateKrylov | kGateDone)) return;
+  __shared__ double Bn[MOTO_MAX_K][MOTO_MAX_K];
+  __shared__ double M[MOTO_MAX_BASIS * MOTO_MAX_K];  // [k][r][c], k < j
+  __shared__ double nu_s, wmax[32];
+  const int bb = b * b, t = threadIdx.x;
+  if (t < bb) Bn[t / b][t % b] = Rn[t];
+  __syncthreads();
+  if (t == 0) {
+    double dmin = 1e300;
+    for (int r = 0; r < b; ++r) dmin = fmin(dmin, Bn[r][r]);
+    const double tn = fmax(st->tnorm, 1e-300);
+    nu_s = dmin > 0.0 ? eps * tn / dmin : 1e300;
+  }
+  // right-hand sides
+  for (int e = t; e < j * bb; e += blockDim.x) {
+    const int k = e / bb, r = (e % bb) / b, c = e % b;
+    double a = 0.0;
+    for (int q = 0; q < b; ++q) {
+      // W_{j,k+1} B_{k+1}   (W_{j,j} = I)
+      const double wjk1 = (k + 1 == j) ? (r == q ? 1.0 : 0.0) : Om[(size_t)(j * b + r) * kLdO + (k + 1) * b + q];
+      a += wjk1 * tblk(T, ldT, b, k + 1, k, q, c);
+      // W_{j,k} A_k - A_j W_{j,k}
+      a += Om[(size_t)(j * b + r) * kLdO + k * b + q] * tblk(T, ldT, b, k, k, q, c);
+      a -= tblk(T, ldT, b, j, j, r, q) * Om[(size_t)(j * b + q) * kLdO + k * b + c];
+      // W_{j,k-1} B_k^T
+      if (k > 0) a += Om[(size_t)(j * b + r) * kLdO + (k - 1) * b + q] * tblk(T, ldT, b, k, k - 1, c, q);
+      // - B_j W_{j-1,k}   (W_{j-1,j-1} = I)
+      const double wj1k =
+          (k == j - 1) ? (q == c ? 1.0 : 0.0) : Om[(size_t)((j - 1) * b + q) * kLdO + k * b + c];
+      a -= tblk(T, ldT, b, j, j - 1, r, q) * wj1k;
+    }
+    M[e] = a;
+  }
+  __syncthreads();
+  const double nu = nu_s;
+  double mx = 0.0;
+  // B_{j+1}^T X = M, B upper triangular: forward substitution down each column
+  for (int e = t; e < j * b; e += blockDim.x) {
+    const int k = e / b, c = e % b;
+    double x[MOTO_MAX_K];
+    for (int r = 0; r < b; ++r) {
+      double a = M[k * bb + r * b + c];
+      for (int q = 0; q < r; ++q) a -= Bn[q][r] * x[q];
+      x[r] = (Bn[r][r] > 0.0) ? a / Bn[r][r] : 1e300;
+    }
+    for (int r = 0; r < b; ++r) {
+      const double v = x[r] + copysign(nu, x[r]);
+      Om[(size_t)((j + 1) * b + r) * kLdO + k * b + c] = v;
+      mx = fmax(mx, fabs(v));
+    }
+  }
+  for (int e = t; e < bb; e += blockDim.x)
+    Om[(size_t)((j + 1) * b + e / b) * kLdO + j * b + e % b] = nu;
+  // block maximum, then the decision
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) wmax[t >> 5] = mx;
+  __syncthreads();
+  if (t == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, wmax[w]);
+    const bool forced = st->pad[3] != 0;
+    const bool need = forced || !(m2 <= sqrt(eps));
+    st->pad[5] = forced ? 1 : 0;
+    if (need)
+      st->gate &= ~kGateNoReorth;
+    else
+      st->gate |= kGateNoReorth;
+  }
+}
+
+// After a full pass of step j (runs only when the step was reorthogonalised):
+// the estimates of block row j + 1 restart at nu; a pass the estimate asked
+// for forces one on the next step too, a forced pass does not.
+__global__ void omega_reset_kernel(int b, int j, const double* Rn, double* Om, DevState* st, double eps) {
+  if (st->gate & (kGateKrylov | kGateDone | kGateNoReorth)) return;
+  __shared__ double nu_s;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    double dmin = 1e300;
+    for (int r = 0; r < b; ++r) dmin = fmin(dmin, Rn[r * b + r]);
+    nu_s = dmin > 0.0 ? eps * fmax(st->tnorm, 1e-300) / dmin : 1e300;
+  }
+  __syncthreads();
+  for (int e = t; e < (j + 1) * b * b; e += blockDim.x) {
+    const int k = e / (b * b), r = (e % (b * b)) / b, c = e % b;
+    Om[(size_t)((j + 1) * b + r) * kLdO + k * b + c] = nu_s;
+  }
+  if (t == 0) {
+    st->pad[3] = st->pad[5] ? 0 : 1;
+    st->pad[4] += 1;  // reorthogonalised steps of this solve
+  }
+}
+
+void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, DevState* st,
+                           double eps, cudaStream_t s) {
+  omega_estimate_kernel<<<1, 1024, 0, s>>>(b, j, T, ldT, Rn, Om, st, eps);
+}
+
+void launch_omega_reset(int b, int j, const double* Rn, double* Om, DevState* st, double eps, cudaStream_t s) {
+  omega_reset_kernel<<<1, 256, 0, s>>>(b, j, Rn, Om, st, eps);
+}
+
+}  // namespace moto

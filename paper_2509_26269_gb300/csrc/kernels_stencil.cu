@@ -224,6 +224,48 @@ __device__ __forceinline__ void tile_origin(int t, int ntx, int ty_sites, int& x
   y0 = ty * ty_sites;
 }
 
+// Tile ring of the persistent kernels: tile t + i grid is staged in buffer
+// (it + i) % kStages, so kStages - 1 tiles are in flight while one is used.
+constexpr int kStages = 3;
+
+template <typename T, int TY>
+__device__ __forceinline__ void stage_one(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int t, int buf,
+                                          int aligned) {
+  int x0, y0;
+  tile_origin(t, ntx, TY, x0, y0);
+  strip::stage_tile<T, strip::Dims<TY>::SY>(tiles + (size_t)buf * strip::Dims<TY>::kTile, m, N, L1, L2, x0, y0,
+                                            aligned && strip::tile_inside<TY>(x0, y0, L1, L2));
+}
+
+// the first kStages - 1 tiles of the block
+template <typename T, int TY>
+__device__ __forceinline__ void stage_prologue(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int ntiles,
+                                               int t0, int aligned) {
+#pragma unroll
+  for (int i = 0; i < kStages - 1; ++i) {
+    const int t = t0 + i * (int)gridDim.x;
+    if (t < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, t, i, aligned);
+  }
+}
+
+// Before using tile t (the block's it-th): stage the tile kStages - 1
+// iterations ahead (its buffer was released by the barrier at the end of the
+// previous iteration), then wait until tile t has landed: the copy groups
+// issued after it may stay pending.
+template <typename T, int TY>
+__device__ __forceinline__ void stage_next(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int ntiles, int t,
+                                           int it, int aligned) {
+  const int ahead = t + (kStages - 1) * (int)gridDim.x;
+  if (ahead < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, ahead, (it + kStages - 1) % kStages, aligned);
+  const int later = (ntiles - 1 - t) / (int)gridDim.x;  // tiles of this block after t
+  if (later >= 2)
+    strip::cp_async_wait<2>();
+  else if (later == 1)
+    strip::cp_async_wait<1>();
+  else
+    strip::cp_async_wait<0>();
+}
+
 // Fixed-order sum of one value per thread over the block (result in thread
 // 0): a shuffle tree per warp, then the warps in order.
 template <typename R>
@@ -297,7 +339,7 @@ __global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md,
   typedef Red<T> RD;
   typedef typename RD::R R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][SY][kSX]
+  T* tiles = reinterpret_cast<T*>(smem_raw);  // [kStages][3][SY][kSX]
   __shared__ R shr[WY];
   __shared__ T shm[WY];
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
@@ -309,25 +351,14 @@ __global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md,
   T gmax = (T)0;
   bool bad = false;
   int t = blockIdx.x, x0, y0;
-  if (t < ntiles) {
-    tile_origin(t, ntx, TY, x0, y0);
-    stage_tile<T, DM::SY>(tiles, m, N, L1, L2, x0, y0, aligned && tile_inside<TY>(x0, y0, L1, L2));
-  }
+  stage_prologue<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    const int tn = t + gridDim.x;
-    if (tn < ntiles) {
-      tile_origin(tn, ntx, TY, x0, y0);
-      stage_tile<T, DM::SY>(tiles + (size_t)((it + 1) & 1) * DM::kTile, m, N, L1, L2, x0, y0,
-                            aligned && tile_inside<TY>(x0, y0, L1, L2));
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    stage_next<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
     __syncthreads();
     tile_origin(t, ntx, TY, x0, y0);
     SpinsOnSite<T, SW> os;
     VP ax[SW], ay[SW], az[SW];
-    walk<T, SW, DM::SY>(tiles + (size_t)(it & 1) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
+    walk<T, SW, DM::SY>(tiles + (size_t)(it % kStages) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
     const int x = x0 + 2 * lane;
     const bool two = x + 1 < L1;
     const bool pair_store = aligned && two;
@@ -429,23 +460,12 @@ __global__ void __launch_bounds__(32 * WY) topo_strip_kernel(ModelDev md, const 
   const size_t N = md.N;
   R acc = RD::of((T)0);
   int t = blockIdx.x, x0, y0;
-  if (t < ntiles) {
-    tile_origin(t, ntx, TY, x0, y0);
-    stage_tile<T, DM::SY>(tiles, m, N, L1, L2, x0, y0, aligned && tile_inside<TY>(x0, y0, L1, L2));
-  }
+  stage_prologue<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    const int tn = t + gridDim.x;
-    if (tn < ntiles) {
-      tile_origin(tn, ntx, TY, x0, y0);
-      stage_tile<T, DM::SY>(tiles + (size_t)((it + 1) & 1) * DM::kTile, m, N, L1, L2, x0, y0,
-                            aligned && tile_inside<TY>(x0, y0, L1, L2));
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    stage_next<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
     __syncthreads();
     tile_origin(t, ntx, TY, x0, y0);
-    const T* tile = tiles + (size_t)(it & 1) * DM::kTile;
+    const T* tile = tiles + (size_t)(it % kStages) * DM::kTile;
     const int x = x0 + 2 * lane;
     T qt = (T)0;
     if (x < L1) {
@@ -541,7 +561,7 @@ void launch_energy_grad_strip(const ModelDev& md, const T* m, T* g, T* s, double
   constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
   const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
   const int ntiles = ntx * nty;
-  const size_t smem = 2 * strip::Dims<TY>::kTile * sizeof(T);
+  const size_t smem = kStages * strip::Dims<TY>::kTile * sizeof(T);
   static int bps_cache = 0;
   const int bps = strip_bps(energy_grad_strip_kernel<T, SW, WY>, 32 * WY, smem, bps_cache);
   const int grid = std::min(ntiles, kSMs * bps);
@@ -595,7 +615,7 @@ void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter
   constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
   const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
   const int ntiles = ntx * nty;
-  const size_t smem = 2 * strip::Dims<TY>::kTile * sizeof(T);
+  const size_t smem = kStages * strip::Dims<TY>::kTile * sizeof(T);
   static int bps_cache = 0;
   const int bps = strip_bps(topo_strip_kernel<T, SW, WY>, 32 * WY, smem, bps_cache);
   const int grid = std::min(ntiles, kSMs * bps);

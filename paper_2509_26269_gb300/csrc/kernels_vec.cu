@@ -807,7 +807,8 @@ void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int 
 // adds the newest term of each sum last, and the minima, maxima and the final
 // product are trees or split sums.
 __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int second, int j, double* Rinv,
-                                                    double* Racc, double* T, int ldT, DevState* st, double rel_tol) {
+                                                    double* Racc, double* T, int ldT, DevState* st, double rel_tol,
+                                                    int skip) {
   // j >= 0: block Lanczos step j; j == -1: start block; j == -2: LOBPCG block
   __shared__ double Ls[MOTO_MAX_K][MOTO_MAX_K], Gs[MOTO_MAX_K][MOTO_MAX_K], Us[MOTO_MAX_K][MOTO_MAX_K];
   __shared__ double Ra[MOTO_MAX_K][MOTO_MAX_K];
@@ -827,7 +828,7 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
     if (second) ra = Racc[r * b + c];
   }
   const double tnorm0 = st->tnorm;
-  if (st->gate & (kGateKrylov | kGateDone)) return;
+  if (st->gate & (kGateKrylov | kGateDone | skip)) return;
   if (t == 0) bad = 0;
   if (in) {
     Gs[r][c] = 0.5 * (g_rc + g_cr);
@@ -955,8 +956,8 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
 }
 
 void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T, int ldT,
-                   DevState* st, double rel_tol, cudaStream_t s) {
-  cholqr_kernel<<<1, 64, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol);
+                   DevState* st, double rel_tol, cudaStream_t s, int skip) {
+  cholqr_kernel<<<1, 64, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol, skip);
 }
 
 // Cyclic Jacobi with round-robin (parallel) ordering on an n x n symmetric
@@ -1776,8 +1777,8 @@ void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign,
 // Saddle / minimum test and the per-step output vector.
 // last: the final test of a run (no step follows it, so none is counted)
 __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
-                                   double tau_F, double* out6, int* status_out, DevState* dst, int ascent,
-                                   int last) {
+                                   double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst,
+                                   int ascent, int last) {
   if (threadIdx.x != 0) return;
   if (dst->gate & kGateDone) {
     if (status_out) *status_out = 1;
@@ -1786,7 +1787,9 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
   const double E = eg_out[0], gmax = eg_out[1];
   bool conv;
   if (ascent) {
-    conv = fmax[0] <= tau_F && lam[0] < 0.0 && 0.0 < lam[1];
+    // lambda_1 < 0 < lambda_2 with the curvature threshold tau_lambda:
+    // lambda_1 clearly negative, lambda_2 not below -tau_lambda
+    conv = fmax[0] <= tau_F && lam[0] < -tau_lambda && -tau_lambda < lam[1];
     if (out6) {
       out6[0] = E;
       out6[1] = fmax[0];
@@ -1813,9 +1816,10 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
 }
 
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
-                        double tau_F, double* out6, int* status_out, DevState* dst, int ascent, int last,
-                        cudaStream_t st) {
-  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, out6, status_out, dst, ascent, last);
+                        double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst, int ascent,
+                        int last, cudaStream_t st) {
+  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, tau_lambda, out6, status_out, dst, ascent,
+                                       last);
 }
 
 #define INST(T)                                                                                                   \

@@ -275,3 +275,19 @@ def test_llg_damping_lowers_the_energy_and_precession_conserves_it():
             x, _ = mmf.llg_step(M, x, 0.0, dt)
         drift.append(abs(spin.energy(M, x) - E[0]))
     assert drift[1] < 0.35 * drift[0]
+
+
+def test_saddle_test_curvature_threshold():
+    """R22: tau_lambda = 0 is the printed test lambda_1 < 0 < lambda_2 (with
+    |F_mmf| <= tau_F); a positive tau_lambda demands lambda_1 < -tau_lambda and
+    accepts a second curvature down to -tau_lambda."""
+    from oracle import mmf
+    assert mmf.saddle_test(1e-4, [-0.5, 1e-7], 1e-3)
+    assert not mmf.saddle_test(1e-4, [-0.5, -1e-7], 1e-3)
+    assert not mmf.saddle_test(1e-4, [-0.5, 0.0], 1e-3)
+    assert not mmf.saddle_test(2e-3, [-0.5, 0.2], 1e-3)
+    assert not mmf.saddle_test(1e-4, [1e-9, 0.2], 1e-3)
+    assert mmf.saddle_test(1e-4, [-0.5, -1e-7], 1e-3, tau_lambda=1e-5)
+    assert not mmf.saddle_test(1e-4, [-0.5, -2e-5], 1e-3, tau_lambda=1e-5)
+    assert not mmf.saddle_test(1e-4, [-5e-6, 0.2], 1e-3, tau_lambda=1e-5)
+    assert mmf.MMFParams().tau_lambda == 0.0
