@@ -376,6 +376,9 @@ __global__ void state_kernel(DevState* st, int op) {
       st->hnorm = 0.0;
       st->pad[0] = 0;
       break;
+    case 4:  // a standalone solve: an earlier ascent or descent may have left its done bit
+      st->gate &= ~kGateDone;
+      break;
   }
 }
 
@@ -1135,6 +1138,7 @@ int moto_lowest_modes(moto_ctx* c, const void* m, const void* s, const moto_para
   int rc = check_params(p);
   if (rc) return rc;
   cudaStream_t st = S(stream);
+  state_kernel<<<1, 32, 0, st>>>(c->st, 4);
   if (c->dtype == MOTO_F32) {
     const float* sp = (const float*)s;
     if (!sp) {

@@ -161,3 +161,26 @@ def test_lobpcg_fp32_workload2_size_checked_by_oracle_residuals():
         assert fp32_ok(lam[j], rq, 12.0)
     assert np.all(np.diff(lam[:6]) >= -1e-7)
     ctx.close()
+
+
+def test_lowest_modes_after_a_converged_ascent():
+    """A standalone solve on a context whose ascent converged (its done bit
+    set) gives what a fresh context gives."""
+    require_gpu()
+    M = workload_model(1)
+    m0 = inputs.workload1_state()
+    q0 = inputs.gaussian_field(inputs.workload_seed(1, 0), 32, 32, offset=10**6)
+    ctx = context(M, torch.float64)
+    m = to_dev(m0, torch.float64)
+    V = to_dev(q0, torch.float64)[None].contiguous()
+    rc, steps, _ = ctx.ascend(m, V, check_every=10)
+    assert rc == 0
+    v0 = to_dev(inputs.gaussian_field(77, 32, 32), torch.float64)[None].contiguous()
+    lam1, V1, info1 = ctx.lowest_modes(m, v0)
+    fresh = context(M, torch.float64)
+    lam2, V2, info2 = fresh.lowest_modes(m, v0)
+    np.testing.assert_array_equal(to_np(lam1), to_np(lam2))
+    np.testing.assert_array_equal(to_np(V1), to_np(V2))
+    assert int(to_np(info1)[0]) == 60
+    ctx.close()
+    fresh.close()
