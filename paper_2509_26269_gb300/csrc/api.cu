@@ -17,6 +17,13 @@
 
 using namespace moto;
 
+namespace moto {
+WalkerGrid& walker_grid() {
+  thread_local WalkerGrid g{1, 0};
+  return g;
+}
+}  // namespace moto
+
 struct moto_ctx {
   ModelDev md;
   double* pairs;  // pair-list storage, MOTO_MAX_PAIRS x [d1, d2, J, Dx, Dy, Dz]
@@ -57,6 +64,14 @@ struct moto_ctx {
   float hvp_ms[16];
   int hvp_tuned_here;
   int last_selective;  // the last block Lanczos solve reorthogonalised selectively
+  // walker group (batches): nw walkers whose scratch and fields lie in
+  // equally sized slices (wstride bytes) of one allocation, `arena`; the
+  // pointers above address slice 0.  Slots for the walkers' spins, modes and
+  // descent copies follow the scratch in each slice.
+  int nw;
+  size_t wstride;
+  void* arena;
+  void *mslot, *Vslot, *mpslot, *mmslot;
 };
 
 namespace {
@@ -238,7 +253,8 @@ void P_tile(moto_ctx* c, int mode, const T* X, int nx, int u0, int nu, T* Y, int
   }
 }
 
-__global__ void set_status_kernel(DevState* st, int bits) {
+__global__ void set_status_kernel(DevState* st, int bits, size_t ws) {
+  st = wofs(st, ws);
   if (threadIdx.x == 0) st->status |= bits;
 }
 
@@ -250,7 +266,7 @@ void P_chol2_gram(moto_ctx* c, const T* W, int b, const double* R1inv, double* S
   PROF(kPkChol2, (double)b * 3.0 * c->N * sizeof(T));
   if (!launch_chol2<T>(W, c->ld, b, R1inv, nullptr, nullptr, 0, nullptr, c->N, S2, c->part, c->counter, gate, mask,
                        true, st))
-    set_status_kernel<<<1, 1, 0, st>>>(c->st, kStatusNotSPD);
+    set_status_kernel<<<wgrid(1), 1, 0, st>>>(c->st, kStatusNotSPD, walker_ws());
 }
 template <typename T>
 void P_combine2(moto_ctx* c, const T* W, int b, const double* R1inv, const double* R2inv, T* Q, const T* m,
@@ -320,7 +336,8 @@ constexpr size_t kLobAux = kLobC + 6 * MOTO_MAX_K * MOTO_MAX_K;    // 64 aux
 constexpr size_t kMmfDots = kLobAux + 64 * MOTO_MAX_K;             // MAX_K: g . V_c (subspace force)
 constexpr size_t kCg = kMmfDots + MOTO_MAX_K;                      // 12: Gram of [G, s, y], |G_prev|^2, beta, alpha
 constexpr size_t kOm = kCg + 12;                                   // MAX_BASIS^2: orthogonality estimates
-constexpr size_t kDsmSize = kOm + MOTO_MAX_BASIS * MOTO_MAX_BASIS;
+constexpr size_t kBout = kOm + MOTO_MAX_BASIS * MOTO_MAX_BASIS;  // 8: a batch walker's descent record
+constexpr size_t kDsmSize = kBout + 8;
 
 constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
 
@@ -344,7 +361,8 @@ T* F(void* base, size_t ld, int j) {
   return static_cast<T*>(base) + (size_t)j * ld;
 }
 
-__global__ void state_kernel(DevState* st, int op) {
+__global__ void state_kernel(DevState* st, int op, size_t ws) {
+  st = wofs(st, ws);
   if (threadIdx.x != 0) return;
   switch (op) {
     case 0:  // begin Krylov solve
@@ -382,7 +400,9 @@ __global__ void state_kernel(DevState* st, int op) {
   }
 }
 
-__global__ void info_kernel(const DevState* st, int* info) {
+__global__ void info_kernel(const DevState* st, int* info, size_t ws) {
+  st = wofs(st, ws);
+  info = wofs(info, ws);
   if (threadIdx.x != 0) return;
   info[0] = st->steps + st->iters;  // block steps (Lanczos) or iterations (LOBPCG)
   info[1] = st->status;
@@ -435,7 +455,7 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
   // unit roundoff of the stored fields (selective reorthogonalisation)
   const double eps = (c->dtype == MOTO_F64) ? 0x1p-53 : 0x1p-24;
   c->last_selective = selective ? 1 : 0;
-  state_kernel<<<1, 32, 0, st>>>(c->st, 0);
+  state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 0, walker_ws());
   // start block: project, Cholesky QR twice
   P_project<T>(c, m, v0, ld0, W, ld, b, N, gate, kGateDone, st);
   P_gram<T>(c, W, ld, b, W, ld, b, n3, D + kG, c->part, c->counter, gate, mk, st);
@@ -532,7 +552,7 @@ void lobpcg(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0, int k,
   double* Mb = D + kLobM;
   double* Cx = D + kLobC;
   double* Cp = Cx + 3 * k * k;
-  state_kernel<<<1, 32, 0, st>>>(c->st, 3);
+  state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 3, walker_ws());
   fill_inf_kernel<<<1, 128, 0, st>>>(lam, k);
   // initial Rayleigh-Ritz on span(P v0)
   T* A = SET(0);
@@ -663,6 +683,138 @@ int autotune_hvp(moto_ctx* c) {
   return MOTO_OK;
 }
 
+// ----------------------------------------------------------------------------
+// Context creation.  nw == 0: one walker, every scratch area its own
+// allocation, sized for any parameters the solvers accept.  nw >= 1: a walker
+// group, its scratch sized for `params` (basis block * steps fields, LOBPCG
+// sets only for LOBPCG) plus slots for each walker's spins, modes and descent
+// copies, in nw slices of one allocation (slice stride a multiple of 256 B).
+// ----------------------------------------------------------------------------
+int create_ctx(const moto_model* model, int dtype, const moto_params* params, int nw, moto_ctx** out) {
+  if (!model || !out || !params || nw < 0) return MOTO_ERR_ARG;
+  *out = nullptr;
+  if (model->L1 < 5 || model->L2 < 5) return MOTO_ERR_ARG;
+  if (model->n_shells < 1 || model->n_shells > 3) return MOTO_ERR_ARG;
+  if (dtype != MOTO_F32 && dtype != MOTO_F64) return MOTO_ERR_ARG;
+  if ((long long)model->L1 * model->L2 > (1LL << 30)) return MOTO_ERR_ARG;
+  int rc = check_params(params);
+  if (rc) return rc;
+  moto_ctx* c = new moto_ctx();
+  memset(c, 0, sizeof(*c));
+  c->md.L1 = model->L1;
+  c->md.L2 = model->L2;
+  c->md.N = model->L1 * model->L2;
+  c->md.n_shells = model->n_shells;
+  for (int i = 0; i < 3; ++i) c->md.J[i] = i < model->n_shells ? model->J[i] : 0.0;
+  c->md.D = model->D;
+  c->md.K = model->K;
+  c->md.muB = model->muB;
+  c->dtype = dtype;
+  c->esize = dtype == MOTO_F64 ? 8 : 4;
+  c->p = *params;
+  c->N = c->md.N;
+  c->n3 = 3 * (size_t)c->N;
+  c->ld = (c->n3 + 63) / 64 * 64;
+  c->nw = nw > 0 ? nw : 1;
+  const size_t vb = c->ld * c->esize;
+  const int R = MOTO_MAX_MEM + 1;
+  size_t tb = (size_t)tile_blocks(c->md);
+  size_t part = std::max<size_t>(2 * tb, (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K);
+  part = std::max<size_t>(part, (size_t)kSMs * 8 * MOTO_MAX_K * 4);
+  part = std::max<size_t>(part, (size_t)kStreamBlocks * 9 * MOTO_MAX_K * MOTO_MAX_K * 2);
+  part = std::max<size_t>(part, 2 * (size_t)pair_blocks(c->md));
+  c->part_len = part;
+  const bool group = nw > 0;
+  const int nbasis = group ? std::max(16, params->block * params->krylov_steps) : MOTO_MAX_BASIS;
+  const size_t nlob = (!group || params->solver == MOTO_SOLVER_LOBPCG) ? 12 * MOTO_MAX_K : 0;
+  const int nv = std::max(params->k, params->block);
+  struct A {
+    void** p;
+    size_t n;
+  } allocs[] = {
+      {&c->basis, vb * nbasis},
+      {&c->W, vb * MOTO_MAX_K},
+      {&c->Wt, vb * MOTO_MAX_K},
+      {&c->g, vb},
+      {&c->s, c->ld * c->esize},
+      {&c->ring, vb * (2 * R + 5)},
+      {&c->lob, vb * nlob},  // two sets of [X, W, P, AX, AW, AP]
+      {(void**)&c->dsm, kDsmSize * sizeof(double)},
+      {(void**)&c->pairs, (size_t)MOTO_MAX_PAIRS * 6 * sizeof(double)},
+      {(void**)&c->part, part * sizeof(double)},
+      {(void**)&c->counter, 64 * sizeof(unsigned)},
+      {(void**)&c->st, sizeof(DevState)},
+      {&c->mslot, group ? vb : 0},
+      {&c->Vslot, group ? vb * nv : 0},
+      {&c->mpslot, group ? vb : 0},
+      {&c->mmslot, group ? vb : 0},
+  };
+  if (!group) {
+    for (auto& a : allocs) {
+      if (a.n == 0) continue;
+      if (cudaMalloc(a.p, a.n) != cudaSuccess) {
+        moto_destroy(c);
+        return MOTO_ERR_NOMEM;
+      }
+      c->bytes += a.n;
+      cudaMemset(*a.p, 0, a.n);
+    }
+  } else {
+    size_t off = 0;
+    for (auto& a : allocs) off += (a.n + 255) / 256 * 256;
+    c->wstride = off;
+    if (cudaMalloc(&c->arena, off * (size_t)nw) != cudaSuccess) {
+      c->arena = nullptr;
+      moto_destroy(c);
+      return MOTO_ERR_NOMEM;
+    }
+    off = 0;
+    for (auto& a : allocs) {
+      *a.p = a.n ? static_cast<char*>(c->arena) + off : nullptr;
+      off += (a.n + 255) / 256 * 256;
+    }
+    c->bytes = off * (size_t)nw;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    moto_destroy(c);
+    return MOTO_ERR_CUDA;
+  }
+  c->hvp_force = -1;
+  rc = dtype == MOTO_F32 ? autotune_hvp<float>(c) : autotune_hvp<double>(c);
+  if (rc == MOTO_OK) {
+    // the timing launches wrote the scratch: give the solvers zeroed fields again
+    if (group)
+      cudaMemset(c->arena, 0, c->bytes);
+    else
+      cudaMemset(c->basis, 0, vb * nbasis);
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = MOTO_ERR_CUDA;
+  }
+  if (rc != MOTO_OK) {
+    moto_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MOTO_OK;
+}
+
+// The calling thread's walker grid follows a context for a scope: a group of
+// several walkers launches every kernel over all of them.
+struct WalkerScope {
+  WalkerGrid saved;
+  explicit WalkerScope(const moto_ctx* c) : saved(walker_grid()) {
+    walker_grid() = WalkerGrid{c->nw, c->nw > 1 ? c->wstride : 0};
+  }
+  ~WalkerScope() { walker_grid() = saved; }
+};
+
+// dst <- src (bytes per walker), for every walker of the current grid
+cudaError_t copy_walkers(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  const WalkerGrid wg = walker_grid();
+  if (wg.nw > 1 && wg.ws)
+    return cudaMemcpy2DAsync(dst, wg.ws, src, wg.ws, bytes, (size_t)wg.nw, cudaMemcpyDeviceToDevice, st);
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+}
+
 // ============================================================================
 // C ABI
 // ============================================================================
@@ -708,88 +860,19 @@ const char* moto_status_string(int code) {
 }
 
 int moto_create(const moto_model* model, int dtype, const moto_params* params, moto_ctx** out) {
-  if (!model || !out || !params) return MOTO_ERR_ARG;
-  *out = nullptr;
-  if (model->L1 < 5 || model->L2 < 5) return MOTO_ERR_ARG;
-  if (model->n_shells < 1 || model->n_shells > 3) return MOTO_ERR_ARG;
-  if (dtype != MOTO_F32 && dtype != MOTO_F64) return MOTO_ERR_ARG;
-  if ((long long)model->L1 * model->L2 > (1LL << 30)) return MOTO_ERR_ARG;
-  int rc = check_params(params);
-  if (rc) return rc;
-  moto_ctx* c = new moto_ctx();
-  memset(c, 0, sizeof(*c));
-  c->md.L1 = model->L1;
-  c->md.L2 = model->L2;
-  c->md.N = model->L1 * model->L2;
-  c->md.n_shells = model->n_shells;
-  for (int i = 0; i < 3; ++i) c->md.J[i] = i < model->n_shells ? model->J[i] : 0.0;
-  c->md.D = model->D;
-  c->md.K = model->K;
-  c->md.muB = model->muB;
-  c->dtype = dtype;
-  c->esize = dtype == MOTO_F64 ? 8 : 4;
-  c->p = *params;
-  c->N = c->md.N;
-  c->n3 = 3 * (size_t)c->N;
-  c->ld = (c->n3 + 63) / 64 * 64;
-  const size_t vb = c->ld * c->esize;
-  const int R = MOTO_MAX_MEM + 1;
-  size_t tb = (size_t)tile_blocks(c->md);
-  size_t part = std::max<size_t>(2 * tb, (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K);
-  part = std::max<size_t>(part, (size_t)kSMs * 8 * MOTO_MAX_K * 4);
-  part = std::max<size_t>(part, (size_t)kStreamBlocks * 9 * MOTO_MAX_K * MOTO_MAX_K * 2);
-  part = std::max<size_t>(part, 2 * (size_t)pair_blocks(c->md));
-  c->part_len = part;
-  struct A {
-    void** p;
-    size_t n;
-  } allocs[] = {
-      {&c->basis, vb * MOTO_MAX_BASIS},
-      {&c->W, vb * MOTO_MAX_K},
-      {&c->Wt, vb * MOTO_MAX_K},
-      {&c->g, vb},
-      {&c->s, c->ld * c->esize},
-      {&c->ring, vb * (2 * R + 5)},
-      {&c->lob, vb * 12 * MOTO_MAX_K},  // two sets of [X, W, P, AX, AW, AP]
-      {(void**)&c->dsm, kDsmSize * sizeof(double)},
-      {(void**)&c->pairs, (size_t)MOTO_MAX_PAIRS * 6 * sizeof(double)},
-      {(void**)&c->part, part * sizeof(double)},
-      {(void**)&c->counter, 64 * sizeof(unsigned)},
-      {(void**)&c->st, sizeof(DevState)},
-  };
-  for (auto& a : allocs) {
-    if (cudaMalloc(a.p, a.n) != cudaSuccess) {
-      moto_destroy(c);
-      return MOTO_ERR_NOMEM;
-    }
-    c->bytes += a.n;
-    cudaMemset(*a.p, 0, a.n);
-  }
-  if (cudaDeviceSynchronize() != cudaSuccess) {
-    moto_destroy(c);
-    return MOTO_ERR_CUDA;
-  }
-  c->hvp_force = -1;
-  rc = dtype == MOTO_F32 ? autotune_hvp<float>(c) : autotune_hvp<double>(c);
-  if (rc == MOTO_OK) {
-    // the timing launches wrote the scratch: give the solvers zeroed fields again
-    cudaMemset(c->basis, 0, vb * MOTO_MAX_BASIS);
-    if (cudaDeviceSynchronize() != cudaSuccess) rc = MOTO_ERR_CUDA;
-  }
-  if (rc != MOTO_OK) {
-    moto_destroy(c);
-    return rc;
-  }
-  *out = c;
-  return MOTO_OK;
+  return create_ctx(model, dtype, params, 0, out);
 }
 
 void moto_destroy(moto_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
-  void* ptrs[] = {c->basis, c->W, c->Wt, c->g, c->s, c->ring, c->lob, c->dsm, c->pairs, c->part, c->counter, c->st};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  if (c->arena) {
+    cudaFree(c->arena);
+  } else {
+    void* ptrs[] = {c->basis, c->W, c->Wt, c->g, c->s, c->ring, c->lob, c->dsm, c->pairs, c->part, c->counter, c->st};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
   delete c;
 }
 
@@ -885,7 +968,7 @@ int moto_status(moto_ctx* c, void* stream) {
 
 int moto_clear_status(moto_ctx* c, void* stream) {
   if (!c) return MOTO_ERR_ARG;
-  state_kernel<<<1, 32, 0, S(stream)>>>(c->st, 2);
+  state_kernel<<<wgrid(1), 32, 0, S(stream)>>>(c->st, 2, walker_ws());
   CK(cudaGetLastError());
   return MOTO_OK;
 }
@@ -978,7 +1061,9 @@ int moto_topo_charge(moto_ctx* c, const void* m, double* Q, void* stream) {
 // ============================================================================
 namespace {
 
-__global__ void store_iters_kernel(const DevState* st, double* out) {
+__global__ void store_iters_kernel(const DevState* st, double* out, size_t ws) {
+  st = wofs(st, ws);
+  out = wofs(out, ws);
   if (threadIdx.x == 0) out[0] = (double)st->pad[1];
 }
 
@@ -1039,7 +1124,7 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
     P_cg_coeffs(c, D + kCg, p->gamma0, c->st, st);
     P_cg_direction<T>(c, m, Gcur, pdir, N, D + kCg, p->theta_max, c->part, c->counter, c->st, gate, md, st);
     P_cg_retract<T>(c, m, Gcur, pdir, d, c->st, N, gate, md, st);
-    cudaMemcpyAsync(Gprev, Gcur, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    copy_walkers(Gprev, Gcur, n3 * sizeof(T), st);
     return;
   }
   P_lbfgs_pair<T>(c, m, d, Gprev, Gcur, ring, ld, stage, c->st, N, gate, md, st);
@@ -1048,7 +1133,7 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
   P_lbfgs_direction<T>(c, ring, ld, nb, D + kLbCoef, m, d, N, p->theta_max, c->part, c->counter, c->st, gate, md,
                             st);
   P_retract<T>(c, m, d, c->st, N, gate, md, st);
-  cudaMemcpyAsync(Gprev, Gcur, n3 * sizeof(T), cudaMemcpyDeviceToDevice, st);
+  copy_walkers(Gprev, Gcur, n3 * sizeof(T), st);
 }
 
 int read_state(moto_ctx* c, DevState* h, cudaStream_t st) {
@@ -1068,7 +1153,7 @@ template <typename T>
 int run_opt(moto_ctx* c, T* m, const moto_params* p, T* V, double* trace, int check_every, int max_steps,
             bool ascent, int* steps_out, cudaStream_t st) {
   if (check_every < 1) check_every = 1;
-  state_kernel<<<1, 32, 0, st>>>(c->st, 1);
+  state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 1, walker_ws());
   DevState h;
   memset(&h, 0, sizeof(h));
   for (int t = 0; t <= max_steps; ++t) {
@@ -1103,7 +1188,7 @@ int run_llg(moto_ctx* c, T* m, const moto_params* p, int check_every, int* steps
   double* D = c->dsm;
   int* gate = &c->st->gate;
   const long nmax = (long)std::ceil(p->llg_time / p->llg_dt - 1e-9);
-  state_kernel<<<1, 32, 0, st>>>(c->st, 1);
+  state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 1, walker_ws());
   DevState h;
   memset(&h, 0, sizeof(h));
   for (long t = 0; t <= nmax; ++t) {
@@ -1138,7 +1223,7 @@ int moto_lowest_modes(moto_ctx* c, const void* m, const void* s, const moto_para
   int rc = check_params(p);
   if (rc) return rc;
   cudaStream_t st = S(stream);
-  state_kernel<<<1, 32, 0, st>>>(c->st, 4);
+  state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 4, walker_ws());
   if (c->dtype == MOTO_F32) {
     const float* sp = (const float*)s;
     if (!sp) {
@@ -1157,14 +1242,14 @@ int moto_lowest_modes(moto_ctx* c, const void* m, const void* s, const moto_para
     lowest_modes_impl<double>(c, (const double*)m, sp, p, (const double*)v0, c->n3, (double*)V, c->n3, p->k, lam,
                               st);
   }
-  if (info) info_kernel<<<1, 32, 0, st>>>(c->st, info);
+  if (info) info_kernel<<<wgrid(1), 32, 0, st>>>(c->st, info, walker_ws());
   CK(cudaGetLastError());
   return MOTO_OK;
 }
 
 int moto_lbfgs_reset(moto_ctx* c, void* stream) {
   if (!c) return MOTO_ERR_ARG;
-  state_kernel<<<1, 32, 0, S(stream)>>>(c->st, 1);
+  state_kernel<<<wgrid(1), 32, 0, S(stream)>>>(c->st, 1, walker_ws());
   CK(cudaGetLastError());
   return MOTO_OK;
 }
@@ -1224,7 +1309,7 @@ int moto_descend(moto_ctx* c, const void* m_saddle, const void* v1, const moto_p
     if (e) return e;
     e = moto_topo_charge(c, mo, out + 2 * side + 1, stream);
     if (e) return e;
-    store_iters_kernel<<<1, 32, 0, st>>>(c->st, out + 4 + side);
+    store_iters_kernel<<<wgrid(1), 32, 0, st>>>(c->st, out + 4 + side, walker_ws());
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -1345,14 +1430,18 @@ extern "C" int moto_gram(moto_ctx* c, const void* X, size_t ldx, int nx, const v
 }
 
 // ============================================================================
-// Batched walkers: many independent MMF walkers (one context each, any mix of
-// lattice sizes) advanced together.  One outer step of every walker is
-// captured once into a CUDA graph whose walkers fan out over n_streams
-// streams, so the small kernels of many walkers run concurrently; the graph
-// is replayed until every walker has stopped.  A walker that met its stopping
-// test sets its done gate on the device, after which its nodes return at once
-// (the graph never needs re-capturing).  Every check_every replays one packed
-// copy of all walkers' [converged, status, steps] words reaches the host.
+// Batched walkers.  The walkers are grouped by lattice size; a group is one
+// context whose scratch, spins and modes lie in equally sized slices of one
+// allocation (create_ctx with nw walkers), and every kernel of its outer step
+// runs once for all of its walkers (the walker is blockIdx.z, see
+// WalkerScope).  Walkers whose step met its stopping test set their done gate
+// on the device; their blocks of later launches return at once, so the
+// captured step never changes.  One outer step of every group is captured
+// into a CUDA graph, the groups fanned out over n_streams streams, and the
+// graph is replayed until every walker has stopped; every check_every replays
+// one packed copy of all walkers' [converged, status, steps] words reaches the
+// host.  Parameters whose kernels have no walker dimension (LOBPCG, nonlinear
+// CG) run every walker as a group of one.
 // ============================================================================
 namespace {
 
@@ -1385,18 +1474,26 @@ int status_of(int flags_status) {
   return status_code(h);
 }
 
+bool batchable(const moto_params& p) {
+  return p.solver == MOTO_SOLVER_LANCZOS && p.optimizer == MOTO_OPT_LBFGS && p.descent == MOTO_DESCENT_OPT;
+}
+
 }  // namespace
+
+struct BatchGroup {
+  moto_ctx* c = nullptr;  // nw walkers in slices of one allocation
+  std::vector<int> idx;   // the batch's walker index of each slice
+  int stream = 0;
+};
 
 struct moto_batch {
   int n = 0, dtype = 0, nstreams = 1;
   moto_params p;
-  moto_ctx** ctx = nullptr;
-  void** m = nullptr;
-  void** V = nullptr;
+  std::vector<BatchGroup> groups;
+  std::vector<moto_walker> w;  // the caller's walkers
   DevState** sts_dev = nullptr;  // device array of the walkers' state words
   int* flags_dev = nullptr;
   int* flags_host = nullptr;  // pinned
-  double* rec_scratch = nullptr;  // n x 6 doubles (descent records)
   cudaStream_t master = nullptr;
   cudaStream_t* streams = nullptr;
   cudaEvent_t fork = nullptr;
@@ -1405,10 +1502,20 @@ struct moto_batch {
 
 namespace {
 
+enum BatchSlot { kSlotM = 0, kSlotMP = 1, kSlotMM = 2 };
+
+void* slot_of(const moto_ctx* c, int slot) {
+  return slot == kSlotM ? c->mslot : (slot == kSlotMP ? c->mpslot : c->mmslot);
+}
+// address of a walker's copy of a slice pointer
+template <typename P>
+P* at_walker(const moto_ctx* c, P* p, int z) {
+  return reinterpret_cast<P*>(reinterpret_cast<char*>(p) + (size_t)z * c->wstride);
+}
+
 void batch_free(moto_batch* b) {
   if (!b) return;
-  if (b->ctx)
-    for (int i = 0; i < b->n; ++i) moto_destroy(b->ctx[i]);
+  for (auto& g : b->groups) moto_destroy(g.c);
   if (b->streams)
     for (int k = 0; k < b->nstreams; ++k)
       if (b->streams[k]) cudaStreamDestroy(b->streams[k]);
@@ -1419,27 +1526,24 @@ void batch_free(moto_batch* b) {
   if (b->master) cudaStreamDestroy(b->master);
   if (b->sts_dev) cudaFree(b->sts_dev);
   if (b->flags_dev) cudaFree(b->flags_dev);
-  if (b->rec_scratch) cudaFree(b->rec_scratch);
   if (b->flags_host) cudaFreeHost(b->flags_host);
-  delete[] b->ctx;
-  delete[] b->m;
-  delete[] b->V;
   delete[] b->streams;
   delete[] b->join;
   delete b;
 }
 
-// Records one step of every walker (walker i on stream i % nstreams) and
-// the flag gather, forked from and joined into the master stream.
+// Records one outer step of every group (group g on stream g % nstreams) and
+// the flag gather, forked from and joined into the master stream.  The spins
+// stepped are the groups' slot `slot` (ascent: the walkers' spins; descent:
+// the copies of one side); records go to each walker's dsm + kTmp.
 template <typename T>
-int batch_record_step(moto_batch* b, bool ascent, double* rec, int rec_stride) {
+int batch_record_step(moto_batch* b, bool ascent, int slot, bool update) {
   CK(cudaEventRecord(b->fork, b->master));
   for (int k = 0; k < b->nstreams; ++k) CK(cudaStreamWaitEvent(b->streams[k], b->fork, 0));
-  for (int i = 0; i < b->n; ++i) {
-    moto_ctx* c = b->ctx[i];
-    double* o = rec ? rec + (size_t)rec_stride * i : c->dsm + kTmp;
-    opt_step<T>(c, static_cast<T*>(b->m[i]), &b->p, ascent ? static_cast<T*>(b->V[i]) : nullptr, o, nullptr, ascent,
-                true, b->streams[i % b->nstreams]);
+  for (auto& g : b->groups) {
+    WalkerScope scope(g.c);
+    opt_step<T>(g.c, static_cast<T*>(slot_of(g.c, slot)), &b->p, ascent ? static_cast<T*>(g.c->Vslot) : nullptr,
+                g.c->dsm + kTmp, nullptr, ascent, update, b->streams[g.stream]);
   }
   for (int k = 0; k < b->nstreams; ++k) {
     CK(cudaEventRecord(b->join[k], b->streams[k]));
@@ -1454,8 +1558,8 @@ int batch_record_step(moto_batch* b, bool ascent, double* rec, int rec_stride) {
 // then one evaluation of the stopping test at the final iterate of the
 // walkers still running (as the one-walker loop does).
 template <typename T>
-int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double* rec, int rec_stride,
-              int* status_host, int* steps_host) {
+int batch_run(moto_batch* b, bool ascent, int slot, int max_steps, int check_every, int* status_host,
+              int* steps_host) {
   if (check_every < 1) check_every = 1;
   batch_reset_kernel<<<(b->n + 127) / 128, 128, 0, b->master>>>(b->sts_dev, b->n);
   CK(cudaGetLastError());
@@ -1463,7 +1567,7 @@ int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double
   int t = 0;
   if (!done) {
     // first step uncaptured: it also sets the kernels' one-time attributes
-    int rc = batch_record_step<T>(b, ascent, rec, rec_stride);
+    int rc = batch_record_step<T>(b, ascent, slot, true);
     if (rc) return rc;
     t = 1;
   }
@@ -1471,7 +1575,7 @@ int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double
   cudaGraphExec_t exec = nullptr;
   if (!done && t < max_steps) {
     CK(cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal));
-    int rc = batch_record_step<T>(b, ascent, rec, rec_stride);
+    int rc = batch_record_step<T>(b, ascent, slot, true);
     cudaError_t ce = cudaStreamEndCapture(b->master, &graph);
     if (rc || ce != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
@@ -1508,14 +1612,8 @@ int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double
   if (graph) cudaGraphDestroy(graph);
   if (rc) return rc;
   // stopping test at the final iterate (no update) for walkers still running
-  for (int i = 0; i < b->n; ++i) {
-    moto_ctx* c = b->ctx[i];
-    double* o = rec ? rec + (size_t)rec_stride * i : c->dsm + kTmp;
-    opt_step<T>(c, static_cast<T*>(b->m[i]), &b->p, ascent ? static_cast<T*>(b->V[i]) : nullptr, o, nullptr, ascent,
-                false, b->master);
-  }
-  batch_flags_kernel<<<(b->n + 127) / 128, 128, 0, b->master>>>(b->sts_dev, b->n, b->flags_dev);
-  CK(cudaGetLastError());
+  rc = batch_record_step<T>(b, ascent, slot, false);
+  if (rc) return rc;
   CK(cudaMemcpyAsync(b->flags_host, b->flags_dev, 3 * sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->master));
   CK(cudaStreamSynchronize(b->master));
   int result = MOTO_OK;
@@ -1528,6 +1626,27 @@ int batch_run(moto_batch* b, bool ascent, int max_steps, int check_every, double
     if (code == MOTO_NOT_CONVERGED && result == MOTO_OK) result = MOTO_NOT_CONVERGED;
   }
   return result;
+}
+
+// caller's spins and modes into the slices, or back out
+int batch_copy_walkers(moto_batch* b, bool in) {
+  for (auto& g : b->groups) {
+    const size_t fb = g.c->n3 * g.c->esize;
+    const size_t vbytes = fb * (size_t)std::max(b->p.k, b->p.block);
+    for (size_t z = 0; z < g.idx.size(); ++z) {
+      const moto_walker& w = b->w[g.idx[z]];
+      void* ms = at_walker(g.c, g.c->mslot, (int)z);
+      void* vs = at_walker(g.c, g.c->Vslot, (int)z);
+      if (in) {
+        CK(cudaMemcpyAsync(ms, w.m_dev, fb, cudaMemcpyDeviceToDevice, b->master));
+        CK(cudaMemcpyAsync(vs, w.V_dev, vbytes, cudaMemcpyDeviceToDevice, b->master));
+      } else {
+        CK(cudaMemcpyAsync(w.m_dev, ms, fb, cudaMemcpyDeviceToDevice, b->master));
+        CK(cudaMemcpyAsync(w.V_dev, vs, vbytes, cudaMemcpyDeviceToDevice, b->master));
+      }
+    }
+  }
+  return MOTO_OK;
 }
 
 }  // namespace
@@ -1544,24 +1663,39 @@ int moto_batch_create(const moto_model* model, int dtype, const moto_params* par
   moto_batch* b = new moto_batch();
   b->n = n_walkers;
   b->dtype = dtype;
-  b->nstreams = std::min(n_streams, n_walkers);
   b->p = *params;
-  b->ctx = new moto_ctx*[n_walkers]();
-  b->m = new void*[n_walkers];
-  b->V = new void*[n_walkers];
+  b->w.assign(walkers, walkers + n_walkers);
+  // groups: walkers of equal lattices together (in the order they come)
+  const bool together = batchable(*params);
+  std::vector<std::pair<std::pair<int, int>, std::vector<int>>> sets;
+  for (int i = 0; i < n_walkers; ++i) {
+    const std::pair<int, int> key(walkers[i].L1, walkers[i].L2);
+    bool placed = false;
+    if (together)
+      for (auto& e : sets)
+        if (e.first == key) {
+          e.second.push_back(i);
+          placed = true;
+          break;
+        }
+    if (!placed) sets.push_back({key, std::vector<int>{i}});
+  }
+  b->nstreams = std::max(1, std::min(n_streams, (int)sets.size()));
   b->streams = new cudaStream_t[b->nstreams]();
   b->join = new cudaEvent_t[b->nstreams]();
-  DevState** sts = new DevState*[n_walkers];
+  std::vector<DevState*> sts(n_walkers, nullptr);
   int rc = MOTO_OK;
-  for (int i = 0; i < n_walkers && !rc; ++i) {
+  for (size_t gi = 0; gi < sets.size() && !rc; ++gi) {
     moto_model mw = *model;
-    mw.L1 = walkers[i].L1;
-    mw.L2 = walkers[i].L2;
-    rc = moto_create(&mw, dtype, params, &b->ctx[i]);
+    mw.L1 = sets[gi].first.first;
+    mw.L2 = sets[gi].first.second;
+    BatchGroup g;
+    g.idx = sets[gi].second;
+    g.stream = (int)(gi % b->nstreams);
+    rc = create_ctx(&mw, dtype, params, (int)g.idx.size(), &g.c);
     if (!rc) {
-      b->m[i] = walkers[i].m_dev;
-      b->V[i] = walkers[i].V_dev;
-      sts[i] = b->ctx[i]->st;
+      for (size_t z = 0; z < g.idx.size(); ++z) sts[g.idx[z]] = at_walker(g.c, g.c->st, (int)z);
+      b->groups.push_back(std::move(g));
     }
   }
   if (!rc) {
@@ -1572,12 +1706,10 @@ int moto_batch_create(const moto_model* model, int dtype, const moto_params* par
            cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMalloc(&b->sts_dev, sizeof(DevState*) * n_walkers) == cudaSuccess &&
          cudaMalloc(&b->flags_dev, 3 * sizeof(int) * n_walkers) == cudaSuccess &&
-         cudaMalloc(&b->rec_scratch, 6 * sizeof(double) * n_walkers) == cudaSuccess &&
          cudaMallocHost(&b->flags_host, 3 * sizeof(int) * n_walkers) == cudaSuccess &&
-         cudaMemcpy(b->sts_dev, sts, sizeof(DevState*) * n_walkers, cudaMemcpyHostToDevice) == cudaSuccess;
+         cudaMemcpy(b->sts_dev, sts.data(), sizeof(DevState*) * n_walkers, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) rc = MOTO_ERR_NOMEM;
   }
-  delete[] sts;
   if (rc) {
     batch_free(b);
     return rc;
@@ -1596,9 +1728,21 @@ int moto_batch_ascend(moto_batch* b, int check_every, double* rec_dev, int* stat
                       void* stream) {
   if (!b || !rec_dev) return MOTO_ERR_ARG;
   CK(cudaStreamSynchronize(S(stream)));
-  if (b->dtype == MOTO_F32)
-    return batch_run<float>(b, true, b->p.max_steps, check_every, rec_dev, 6, status_host, steps_host);
-  return batch_run<double>(b, true, b->p.max_steps, check_every, rec_dev, 6, status_host, steps_host);
+  int rc = batch_copy_walkers(b, true);
+  if (rc) return rc;
+  const int result = b->dtype == MOTO_F32
+                         ? batch_run<float>(b, true, kSlotM, b->p.max_steps, check_every, status_host, steps_host)
+                         : batch_run<double>(b, true, kSlotM, b->p.max_steps, check_every, status_host, steps_host);
+  if (result < 0) return result;
+  // records of the last test, and the walkers back to the caller
+  for (auto& g : b->groups)
+    for (size_t z = 0; z < g.idx.size(); ++z)
+      CK(cudaMemcpyAsync(rec_dev + 6 * (size_t)g.idx[z], at_walker(g.c, g.c->dsm, (int)z) + kTmp,
+                         6 * sizeof(double), cudaMemcpyDeviceToDevice, b->master));
+  rc = batch_copy_walkers(b, false);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(b->master));
+  return result;
 }
 
 int moto_batch_descend(moto_batch* b, void* const* m_plus, void* const* m_minus, double* out_dev, int* status_host,
@@ -1608,44 +1752,51 @@ int moto_batch_descend(moto_batch* b, void* const* m_plus, void* const* m_minus,
     if (!m_plus[i] || !m_minus[i]) return MOTO_ERR_ARG;
   CK(cudaStreamSynchronize(S(stream)));
   // the walkers' spins and first modes are the saddles and their v1
-  void** saddle = new void*[b->n];
-  for (int i = 0; i < b->n; ++i) saddle[i] = b->m[i];
+  int rc = batch_copy_walkers(b, true);
+  if (rc) return rc;
   int result = MOTO_OK;
-  int* st_side = new int[b->n];
+  std::vector<int> st_side(b->n);
   for (int side = 0; side < 2 && result >= 0; ++side) {
     const double sign = side == 0 ? 1.0 : -1.0;
-    void* const* dst = side == 0 ? m_plus : m_minus;
-    for (int i = 0; i < b->n; ++i) {
-      moto_ctx* c = b->ctx[i];
+    const int slot = side == 0 ? kSlotMP : kSlotMM;
+    for (auto& g : b->groups) {
+      WalkerScope scope(g.c);
+      moto_ctx* c = g.c;
       if (b->dtype == MOTO_F32)
-        launch_descent_seed<float>((const float*)saddle[i], (const float*)b->V[i], b->p.eta_theta, sign,
-                                   (float*)dst[i], c->N, c->part, c->counter, c->dsm + kTmp, b->master);
+        launch_descent_seed<float>((const float*)c->mslot, (const float*)c->Vslot, b->p.eta_theta, sign,
+                                   (float*)slot_of(c, slot), c->N, c->part, c->counter, c->dsm + kTmp, b->master);
       else
-        launch_descent_seed<double>((const double*)saddle[i], (const double*)b->V[i], b->p.eta_theta, sign,
-                                    (double*)dst[i], c->N, c->part, c->counter, c->dsm + kTmp, b->master);
+        launch_descent_seed<double>((const double*)c->mslot, (const double*)c->Vslot, b->p.eta_theta, sign,
+                                    (double*)slot_of(c, slot), c->N, c->part, c->counter, c->dsm + kTmp,
+                                    b->master);
     }
-    if (cudaGetLastError() != cudaSuccess) {
-      result = MOTO_ERR_CUDA;
-      break;
-    }
-    // descend the copies: point the walkers at them for this side
-    for (int i = 0; i < b->n; ++i) b->m[i] = dst[i];
-    const int rc = b->dtype == MOTO_F32
-                       ? batch_run<float>(b, false, b->p.descent_max_steps, 25, nullptr, 0, st_side, nullptr)
-                       : batch_run<double>(b, false, b->p.descent_max_steps, 25, nullptr, 0, st_side, nullptr);
-    for (int i = 0; i < b->n; ++i) b->m[i] = saddle[i];
+    CK(cudaGetLastError());
+    rc = b->dtype == MOTO_F32 ? batch_run<float>(b, false, slot, b->p.descent_max_steps, 25, st_side.data(), nullptr)
+                              : batch_run<double>(b, false, slot, b->p.descent_max_steps, 25, st_side.data(), nullptr);
     if (rc < 0) {
       result = rc;
       break;
     }
-    for (int i = 0; i < b->n; ++i) {
-      moto_ctx* c = b->ctx[i];
-      double* o = out_dev + 6 * (size_t)i;
-      if (moto_energy(c, dst[i], o + 2 * side, b->master) || moto_topo_charge(c, dst[i], o + 2 * side + 1, b->master)) {
-        result = MOTO_ERR_CUDA;
-        break;
+    // FP64-arithmetic energy, charge and steps of each minimum (a walker's
+    // dsm + kBout: [E+, Q+, E-, Q-, steps+, steps-])
+    for (auto& g : b->groups) {
+      WalkerScope scope(g.c);
+      moto_ctx* c = g.c;
+      double* o = c->dsm + kBout;
+      if (b->dtype == MOTO_F32) {
+        launch_energy_grad<float>(c->md, (const float*)slot_of(c, slot), nullptr, nullptr, c->part, c->counter,
+                                  o + 2 * side, &c->st->status, true, b->master);
+        launch_topo<float>(c->md, (const float*)slot_of(c, slot), c->part, c->counter, o + 2 * side + 1, b->master);
+      } else {
+        launch_energy_grad<double>(c->md, (const double*)slot_of(c, slot), nullptr, nullptr, c->part, c->counter,
+                                   o + 2 * side, &c->st->status, true, b->master);
+        launch_topo<double>(c->md, (const double*)slot_of(c, slot), c->part, c->counter, o + 2 * side + 1,
+                            b->master);
       }
-      store_iters_kernel<<<1, 32, 0, b->master>>>(c->st, o + 4 + side);
+      store_iters_kernel<<<wgrid(1), 32, 0, b->master>>>(c->st, o + 4 + side, walker_ws());
+    }
+    CK(cudaGetLastError());
+    for (int i = 0; i < b->n; ++i) {
       if (status_host) {
         const int prev = side == 0 ? MOTO_OK : status_host[i];
         int code = st_side[i];
@@ -1655,8 +1806,19 @@ int moto_batch_descend(moto_batch* b, void* const* m_plus, void* const* m_minus,
     }
     if (rc == MOTO_NOT_CONVERGED && result == MOTO_OK) result = MOTO_NOT_CONVERGED;
   }
-  delete[] st_side;
-  delete[] saddle;
+  if (result >= 0) {
+    for (auto& g : b->groups) {
+      const size_t fb = g.c->n3 * g.c->esize;
+      for (size_t z = 0; z < g.idx.size(); ++z) {
+        const int i = g.idx[z];
+        CK(cudaMemcpyAsync(out_dev + 6 * (size_t)i, at_walker(g.c, g.c->dsm, (int)z) + kBout, 6 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, b->master));
+        CK(cudaMemcpyAsync(m_plus[i], at_walker(g.c, g.c->mpslot, (int)z), fb, cudaMemcpyDeviceToDevice, b->master));
+        CK(cudaMemcpyAsync(m_minus[i], at_walker(g.c, g.c->mmslot, (int)z), fb, cudaMemcpyDeviceToDevice,
+                           b->master));
+      }
+    }
+  }
   if (cudaStreamSynchronize(b->master) != cudaSuccess) return MOTO_ERR_CUDA;
   return result;
 }

@@ -35,6 +35,16 @@ enum : int {
   kStatusTimeout = 8,
 };
 
+// Walker batches: a launch may serve several walkers whose scratch and fields
+// lie at equal offsets of equally sized slices of one allocation.  The walker
+// is blockIdx.z; its pointers are the first walker's plus z * ws bytes
+// (ws == 0: a single walker, pointers unchanged).
+template <typename P>
+__device__ __forceinline__ P* wofs(P* p, size_t ws) {
+  return (ws != 0 && p != nullptr) ? reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(p) + (size_t)blockIdx.z * ws)
+                                   : p;
+}
+
 __device__ __forceinline__ int wrap(int a, int L) {
   a %= L;
   return a < 0 ? a + L : a;

@@ -8,6 +8,24 @@
 
 namespace moto {
 
+// ---- walker batches ----
+// The sequences of a walker group set the calling thread's current walker
+// grid: every launch then gets gridDim.z = nw and the slice stride ws (bytes)
+// as its last argument; kernels offset their pointers with wofs().  Single
+// contexts run with {1, 0}.
+struct WalkerGrid {
+  int nw;
+  size_t ws;
+};
+WalkerGrid& walker_grid();
+inline dim3 wgrid(dim3 g) {
+  g.z = (unsigned)walker_grid().nw;
+  return g;
+}
+inline dim3 wgrid(int x) { return wgrid(dim3((unsigned)x)); }
+inline dim3 wgrid(unsigned x) { return wgrid(dim3(x)); }
+inline size_t walker_ws() { return walker_grid().ws; }
+
 // ---- gate bits: kernels given (gate, mask) return at once if (*gate & mask) ----
 enum : int {
   kGateKrylov = 1,  // the Krylov recurrence broke down; skip its remaining steps

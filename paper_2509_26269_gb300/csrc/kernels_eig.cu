@@ -53,7 +53,11 @@ size_t eig_smem_bytes() {
 
 template <typename R>
 __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restrict__ Tm, int ldT, int band,
-                                                          double* theta, double* Y, int k, DevState* st) {
+                                                          double* theta, double* Y, int k, DevState* st, size_t ws) {
+  Tm = wofs(Tm, ws);
+  theta = wofs(theta, ws);
+  Y = wofs(Y, ws);
+  st = wofs(st, ws);
   if (st->gate & kGateDone) return;
   extern __shared__ double sm[];
   double* d = sm;                              // diagonal
@@ -456,7 +460,7 @@ void launch_tridiag_eig(const double* T, int ldT, int band, int fp64, double* th
                            (int)eig_smem_bytes<double>());
       attr = true;
     }
-    tridiag_eig_kernel<double><<<1, 256, eig_smem_bytes<double>(), s>>>(T, ldT, band, theta, Y, k, st);
+    tridiag_eig_kernel<double><<<wgrid(1), 256, eig_smem_bytes<double>(), s>>>(T, ldT, band, theta, Y, k, st, walker_ws());
   } else {
     static bool attr = false;
     if (!attr) {
@@ -464,7 +468,7 @@ void launch_tridiag_eig(const double* T, int ldT, int band, int fp64, double* th
                            (int)eig_smem_bytes<float>());
       attr = true;
     }
-    tridiag_eig_kernel<float><<<1, 256, eig_smem_bytes<float>(), s>>>(T, ldT, band, theta, Y, k, st);
+    tridiag_eig_kernel<float><<<wgrid(1), 256, eig_smem_bytes<float>(), s>>>(T, ldT, band, theta, Y, k, st, walker_ws());
   }
 }
 

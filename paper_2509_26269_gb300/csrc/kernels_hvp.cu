@@ -52,7 +52,12 @@ template <typename T, int SW, int WY, bool MREG>
 __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights<T> hw, const T* __restrict__ m,
                                                             const T* __restrict__ s, const T* __restrict__ V,
                                                             size_t ldv, T* __restrict__ HV, size_t ldhv, int nvec,
-                                                            int aligned, const int* gate, int mask) {
+                                                            int aligned, const int* gate, int mask, size_t ws) {
+  m = wofs(m, ws);
+  s = wofs(s, ws);
+  V = wofs(V, ws);
+  HV = wofs(HV, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   constexpr int TY = SW * WY;
   typedef Dims<TY> DM;
@@ -183,8 +188,8 @@ void hvp_launch_v(const ModelDev& md, const Weights<T>& hw, const T* m, const T*
     cudaFuncSetAttribute(hvp_strip_kernel<T, SW, WY, MREG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  hvp_strip_kernel<T, SW, WY, MREG><<<grid, 32 * WY, smem, st>>>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate,
-                                                                 mask);
+  hvp_strip_kernel<T, SW, WY, MREG><<<wgrid(grid), 32 * WY, smem, st>>>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate,
+                                                                 mask, walker_ws());
 }
 
 template <typename T>

@@ -38,7 +38,11 @@ __device__ __forceinline__ double tblk(const double* T, int ldT, int b, int i, i
 // right-hand side, thread (k, c) solves one column of the triangular system.
 __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, const double* T, int ldT,
                                                               const double* Rn, double* Om, DevState* st,
-                                                              double eps) {
+                                                              double eps, size_t ws) {
+  T = wofs(T, ws);
+  Rn = wofs(Rn, ws);
+  Om = wofs(Om, ws);
+  st = wofs(st, ws);
   if (st->gate & (kGateKrylov | kGateDone)) return;
   __shared__ double Bn[MOTO_MAX_K][MOTO_MAX_K];
   __shared__ double M[MOTO_MAX_BASIS * MOTO_MAX_K];  // [k][r][c], k < j
@@ -113,7 +117,10 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
 // After a full pass of step j (runs only when the step was reorthogonalised):
 // the estimates of block row j + 1 restart at nu; a pass the estimate asked
 // for forces one on the next step too, a forced pass does not.
-__global__ void omega_reset_kernel(int b, int j, const double* Rn, double* Om, DevState* st, double eps) {
+__global__ void omega_reset_kernel(int b, int j, const double* Rn, double* Om, DevState* st, double eps, size_t ws) {
+  Rn = wofs(Rn, ws);
+  Om = wofs(Om, ws);
+  st = wofs(st, ws);
   if (st->gate & (kGateKrylov | kGateDone | kGateNoReorth)) return;
   __shared__ double nu_s;
   const int t = threadIdx.x;
@@ -135,11 +142,11 @@ __global__ void omega_reset_kernel(int b, int j, const double* Rn, double* Om, D
 
 void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, DevState* st,
                            double eps, cudaStream_t s) {
-  omega_estimate_kernel<<<1, 1024, 0, s>>>(b, j, T, ldT, Rn, Om, st, eps);
+  omega_estimate_kernel<<<wgrid(1), 1024, 0, s>>>(b, j, T, ldT, Rn, Om, st, eps, walker_ws());
 }
 
 void launch_omega_reset(int b, int j, const double* Rn, double* Om, DevState* st, double eps, cudaStream_t s) {
-  omega_reset_kernel<<<1, 256, 0, s>>>(b, j, Rn, Om, st, eps);
+  omega_reset_kernel<<<wgrid(1), 256, 0, s>>>(b, j, Rn, Om, st, eps, walker_ws());
 }
 
 }  // namespace moto

@@ -54,7 +54,14 @@ template <typename T, typename A>
 __global__ void __launch_bounds__(kThreads) energy_grad_kernel(ModelDev md, const T* __restrict__ m,
                                                                T* __restrict__ g, T* __restrict__ s,
                                                                double* part, unsigned* counter, double* out,
-                                                               int* status, int euclid) {
+                                                               int* status, int euclid, size_t ws) {
+  m = wofs(m, ws);
+  g = wofs(g, ws);
+  s = wofs(s, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  out = wofs(out, ws);
+  status = wofs(status, ws);
   __shared__ Tile<T> tile;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   load_tile(m, md.N, md.L1, md.L2, x0, y0, tile);
@@ -330,7 +337,14 @@ __global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md,
                                                                     const T* __restrict__ m, T* __restrict__ g,
                                                                     T* __restrict__ s, double* part, unsigned* counter,
                                                                     double* out, int* status, int aligned, int ntx,
-                                                                    int ntiles) {
+                                                                    int ntiles, size_t ws) {
+  m = wofs(m, ws);
+  g = wofs(g, ws);
+  s = wofs(s, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  out = wofs(out, ws);
+  status = wofs(status, ws);
   using namespace strip;
   constexpr int TY = SW * WY;
   typedef Dims<TY> DM;
@@ -446,7 +460,11 @@ __device__ __forceinline__ T solid_angle(T ax, T ay, T az, T bx, T by, T bz, T c
 template <typename T, int SW, int WY>
 __global__ void __launch_bounds__(32 * WY) topo_strip_kernel(ModelDev md, const T* __restrict__ m, double* part,
                                                              unsigned* counter, double* out, int aligned, int ntx,
-                                                             int ntiles) {
+                                                             int ntiles, size_t ws) {
+  m = wofs(m, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  out = wofs(out, ws);
   using namespace strip;
   constexpr int TY = SW * WY;
   typedef Dims<TY> DM;
@@ -567,8 +585,8 @@ void launch_energy_grad_strip(const ModelDev& md, const T* m, T* g, T* s, double
   const int grid = std::min(ntiles, kSMs * bps);
   constexpr int kE = 16 / (int)sizeof(T);
   const int aligned = (md.L1 % kE == 0) && al16<T>(m) && al16<T>(g) && al16<T>(s);
-  energy_grad_strip_kernel<T, SW, WY><<<grid, 32 * WY, smem, st>>>(
-      md, strip::make_weights<T>(md), (T)md.muB, m, g, s, part, counter, out, status, aligned, ntx, ntiles);
+  energy_grad_strip_kernel<T, SW, WY><<<wgrid(grid), 32 * WY, smem, st>>>(
+      md, strip::make_weights<T>(md), (T)md.muB, m, g, s, part, counter, out, status, aligned, ntx, ntiles, walker_ws());
 }
 
 }  // namespace
@@ -586,9 +604,9 @@ void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part
   }
   const int e = euclid ? 1 : 0;
   if (fp64_arith)
-    energy_grad_kernel<T, double><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e);
+    energy_grad_kernel<T, double><<<wgrid(tile_grid(md)), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e, walker_ws());
   else
-    energy_grad_kernel<T, T><<<tile_grid(md), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e);
+    energy_grad_kernel<T, T><<<wgrid(tile_grid(md)), kThreads, 0, st>>>(md, m, g, s, part, counter, out, status, e, walker_ws());
 }
 
 template <typename T>
@@ -621,7 +639,7 @@ void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter
   const int grid = std::min(ntiles, kSMs * bps);
   constexpr int kE = 16 / (int)sizeof(T);
   const int aligned = (md.L1 % kE == 0) && al16<T>(m);
-  topo_strip_kernel<T, SW, WY><<<grid, 32 * WY, smem, st>>>(md, m, part, counter, out, aligned, ntx, ntiles);
+  topo_strip_kernel<T, SW, WY><<<wgrid(grid), 32 * WY, smem, st>>>(md, m, part, counter, out, aligned, ntx, ntiles, walker_ws());
 }
 
 #define INST(T)                                                                                               \

@@ -253,7 +253,17 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
     tile2d_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int nx, int ny,
                   int u0, int nu, size_t n, const double* __restrict__ C, const double* __restrict__ Cadd, int uadd,
                   int nadd, T* __restrict__ Yout, size_t ldo, double* out, double* part, unsigned* counter, int nst,
-                  int tps, const int* gate, int mask, int* status, int polls) {
+                  int tps, const int* gate, int mask, int* status, int polls, size_t ws) {
+  // walker batches: tensor coordinate z = walker, the other pointers offset
+  C = wofs(C, ws);
+  Cadd = wofs(Cadd, ws);
+  Yout = wofs(Yout, ws);
+  out = wofs(out, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  gate = wofs(gate, ws);
+  status = wofs(status, ws);
+  const int wz = ws ? (int)blockIdx.z : -1;
   if (gate && (*gate & mask)) return;
   typedef TileT<T> TT;
   typedef typename TT::Acc Acc;
@@ -352,8 +362,13 @@ __global__ void __maxnreg__(MOTO_TILE_MAXREG)
         mbar_expect_tx(&full[s], tx_bytes);
         for (int q = 0; q < tps; ++q) {
           const int x = (int)(((blockIdx.x + (size_t)it * gridDim.x) * tps + q) * TE);
-          tma_load_2d(buf + (size_t)q * tile_b, &tmX, x, 0, &full[s]);
-          if (MODE != 3) tma_load_2d(buf + (size_t)q * tile_b + yoff, &tmY, x, 0, &full[s]);
+          if (wz < 0) {
+            tma_load_2d(buf + (size_t)q * tile_b, &tmX, x, 0, &full[s]);
+            if (MODE != 3) tma_load_2d(buf + (size_t)q * tile_b + yoff, &tmY, x, 0, &full[s]);
+          } else {
+            tma_load_3d(buf + (size_t)q * tile_b, &tmX, x, 0, wz, &full[s]);
+            if (MODE != 3) tma_load_3d(buf + (size_t)q * tile_b + yoff, &tmY, x, 0, wz, &full[s]);
+          }
         }
       }
     }
@@ -643,17 +658,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2D map over `rows` fields of n elements, field stride ld; box [rows][TB
-// bytes], no swizzle
+// bytes], no swizzle.  For a walker batch (nw > 1) a 3D map whose third
+// dimension steps from walker to walker by ws bytes (box depth 1).
 template <typename T>
-bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld, int tb) {
+bool make_map(CUtensorMap* map, const T* base, size_t n, int rows, size_t ld, int tb, int nw = 1, size_t ws = 0) {
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(T))};
-  cuuint32_t box[2] = {(cuuint32_t)(tb / sizeof(T)), (cuuint32_t)rows};
-  cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
-  return fn(map, dt, 2, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)rows, (cuuint64_t)nw};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * sizeof(T)), (cuuint64_t)ws};
+  cuuint32_t box[3] = {(cuuint32_t)(tb / sizeof(T)), (cuuint32_t)rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t rank = nw > 1 ? 3 : 2;
+  if (nw > 1 && (ws % 16 != 0 || ws < (size_t)rows * ld * sizeof(T))) return false;
+  return fn(map, dt, rank, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
@@ -705,8 +723,9 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   if (want > cap) want = cap;
   const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
   const int grid = (int)(ngroups < want ? (ngroups > 0 ? ngroups : 1) : want);
-  tile2d_kernel<T, MODE, R, CW, NRL, TB><<<grid, kThrT, smem, st>>>(mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out,
-                                                                    part, counter, nst, tps, gate, mask, status, polls);
+  tile2d_kernel<T, MODE, R, CW, NRL, TB><<<wgrid(grid), kThrT, smem, st>>>(
+      mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, nst, tps, gate, mask, status,
+      polls, walker_ws());
 }
 
 // Gram lane layouts (R rows x CW columns a lane, NRL row lanes): FP32 fits
@@ -785,9 +804,10 @@ bool launch_tile(int mode, const T* X, size_t ldx, int nx, int u0, int nu, const
   }
   const int tb = tile_bytes<T>(mode, nx, ny);
   CUtensorMap mx, my;
-  if (!make_map<T>(&mx, X, n, nx, ldx, tb)) return false;
+  const WalkerGrid wg = walker_grid();
+  if (!make_map<T>(&mx, X, n, nx, ldx, tb, wg.nw, wg.ws)) return false;
   if (mode != 3) {
-    if (!make_map<T>(&my, Y, n, ny, ldy, tb)) return false;
+    if (!make_map<T>(&my, Y, n, ny, ldy, tb, wg.nw, wg.ws)) return false;
   } else {
     my = mx;
   }

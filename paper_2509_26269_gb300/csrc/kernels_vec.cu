@@ -32,7 +32,13 @@ template <typename T, int NY>
 __global__ void __launch_bounds__(kThreads) gram_kernel(const T* __restrict__ X, size_t ldx, int nx,
                                                         const T* __restrict__ Y, size_t ldy, int ny, size_t n,
                                                         double* out, double* part, unsigned* counter,
-                                                        const int* gate, int mask) {
+                                                        const int* gate, int mask, size_t ws) {
+  X = wofs(X, ws);
+  Y = wofs(Y, ws);
+  out = wofs(out, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int npairs = (nx + 1) >> 1;
@@ -147,7 +153,7 @@ static void gram_launch_ny(const T* X, size_t ldx, int nx, const T* Y, size_t ld
   }
   const size_t ntiles = (n + kGramKT - 1) / kGramKT;
   const int grid = (int)(ntiles < (size_t)kStreamBlocks ? ntiles : (size_t)kStreamBlocks);
-  gram_kernel<T, NY><<<grid, kThreads, smem, st>>>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask);
+  gram_kernel<T, NY><<<wgrid(grid), kThreads, smem, st>>>(X, ldx, nx, Y, ldy, ny, n, out, part, counter, gate, mask, walker_ws());
 }
 
 static int* g_gram_status = nullptr;
@@ -177,7 +183,14 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const T* __restrict__
                                                            const int* nx_dev, const double* __restrict__ C, int ny,
                                                            const T* Y, size_t ldy, T beta, T sigma, T* out,
                                                            size_t ldo, const T* __restrict__ m, int N,
-                                                           const int* gate, int mask) {
+                                                           const int* gate, int mask, size_t ws) {
+  X = wofs(X, ws);
+  nx_dev = wofs(nx_dev, ws);
+  C = wofs(C, ws);
+  Y = wofs(Y, ws);
+  out = wofs(out, ws);
+  m = wofs(m, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   if (nx_dev) nx = min(*nx_dev, nx);
   __shared__ T Cs[MOTO_MAX_BASIS * NY];
@@ -244,17 +257,17 @@ void launch_combine(const T* X, size_t ldx, int nx, const int* nx_dev, const dou
                     int mask, cudaStream_t st) {
   const int g = stream_grid(N);
   if (ny <= 1)
-    combine_kernel<T, 1><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
-                                                 N, gate, mask);
+    combine_kernel<T, 1><<<wgrid(g), kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask, walker_ws());
   else if (ny <= 2)
-    combine_kernel<T, 2><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
-                                                 N, gate, mask);
+    combine_kernel<T, 2><<<wgrid(g), kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask, walker_ws());
   else if (ny <= 4)
-    combine_kernel<T, 4><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
-                                                 N, gate, mask);
+    combine_kernel<T, 4><<<wgrid(g), kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask, walker_ws());
   else
-    combine_kernel<T, 8><<<g, kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
-                                                 N, gate, mask);
+    combine_kernel<T, 8><<<wgrid(g), kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
+                                                 N, gate, mask, walker_ws());
 }
 
 namespace {
@@ -320,7 +333,13 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __restrict__ X, size_t ldx, int nx,
                                                                  const double* __restrict__ P, size_t n,
                                                                  double* out, double* part, unsigned* counter,
-                                                                 const int* gate, int mask) {
+                                                                 const int* gate, int mask, size_t ws) {
+  X = wofs(X, ws);
+  P = wofs(P, ws);
+  out = wofs(out, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   __shared__ __align__(16) T Ps[64];
   __shared__ double red[kThreads / 32][kUpdSelf];
@@ -443,7 +462,13 @@ __global__ void __launch_bounds__(kThreads) combine2_kernel(const T* __restrict_
                                                             const double* __restrict__ P1,
                                                             const double* __restrict__ P2, T* out, size_t ldo,
                                                             const T* __restrict__ m, int N, const int* gate,
-                                                            int mask) {
+                                                            int mask, size_t ws) {
+  X = wofs(X, ws);
+  P1 = wofs(P1, ws);
+  P2 = wofs(P2, ws);
+  out = wofs(out, ws);
+  m = wofs(m, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   __shared__ __align__(16) T P1s[64], P2s[64];
   stage_tri(P1s, P1, nx);
@@ -540,18 +565,18 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
     const size_t cap = (size_t)kSMs * 2;  // one wave at two blocks per SM
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    chol2_gram_kernel<T><<<(int)g, kThreads, 0, st>>>(X, ldx, nx, P1, n, S2, part, counter, gate, mask);
+    chol2_gram_kernel<T><<<wgrid((int)g), kThreads, 0, st>>>(X, ldx, nx, P1, n, S2, part, counter, gate, mask, walker_ws());
   } else {
     const bool pair = sizeof(T) == 4 && N % 2 == 0 && ldx % 2 == 0 && ldq % 2 == 0 && (uintptr_t)X % 8 == 0 &&
                       (uintptr_t)Q % 8 == 0 && (!m || (uintptr_t)m % 8 == 0);
     if constexpr (sizeof(T) == 4) {
       if (pair) {
-        combine2_kernel<T, true><<<stream_grid(N / 2), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate,
-                                                                          mask);
+        combine2_kernel<T, true><<<wgrid(stream_grid(N / 2)), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate,
+                                                                          mask, walker_ws());
         return true;
       }
     }
-    combine2_kernel<T, false><<<stream_grid(N), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask);
+    combine2_kernel<T, false><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask, walker_ws());
   }
   return true;
 }
@@ -561,7 +586,11 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
 // ===========================================================================
 template <typename T>
 __global__ void project_kernel(const T* __restrict__ m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N,
-                               const int* gate, int mask) {
+                               const int* gate, int mask, size_t ws) {
+  m = wofs(m, ws);
+  in = wofs(in, ws);
+  out = wofs(out, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
@@ -580,7 +609,7 @@ __global__ void project_kernel(const T* __restrict__ m, const T* in, size_t ldi,
 template <typename T>
 void launch_project(const T* m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N, const int* gate,
                     int mask, cudaStream_t st) {
-  project_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, in, ldi, out, ldo, nvec, N, gate, mask);
+  project_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, in, ldi, out, ldo, nvec, N, gate, mask, walker_ws());
 }
 
 // argmax with ties to the lowest index: (abs, idx) pairs
@@ -608,7 +637,13 @@ __device__ __forceinline__ void amax_merge_t(A& a, int& ai, A& av, A b, int bi, 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__ m, const T* __restrict__ V,
                                                            size_t ldv, int k, int N, double* part, unsigned* counter,
-                                                           double* scal, const int* gate, int mask) {
+                                                           double* scal, const int* gate, int mask, size_t ws) {
+  m = wofs(m, ws);
+  V = wofs(V, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  scal = wofs(scal, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   T nrm_t[MOTO_MAX_K], amx_t[MOTO_MAX_K], aval_t[MOTO_MAX_K];
   int aidx_t[MOTO_MAX_K];
@@ -727,7 +762,11 @@ __global__ void __launch_bounds__(kThreads) finish1_kernel(const T* __restrict__
 // pass 2: V_c <- scal_c P(V_c) (the projection recomputed exactly as in pass 1)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) finish2_kernel(const T* __restrict__ m, T* V, size_t ldv, int k, int N,
-                                                           const double* scal, const int* gate, int mask) {
+                                                           const double* scal, const int* gate, int mask, size_t ws) {
+  m = wofs(m, ws);
+  V = wofs(V, ws);
+  scal = wofs(scal, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   __shared__ T sc[MOTO_MAX_K];
   if (threadIdx.x < MOTO_MAX_K) sc[threadIdx.x] = threadIdx.x < k ? (T)scal[threadIdx.x] : (T)0;
@@ -757,14 +796,18 @@ void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, uns
   const int g = stream_grid(N);
   // two blocks an SM for the reducing pass: fewer partials for its last block
   const int g1 = g < 2 * kSMs ? g : 2 * kSMs;
-  finish1_kernel<T><<<g1, kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask);
-  finish2_kernel<T><<<g, kThreads, 0, st>>>(m, V, ldv, k, N, scal, gate, mask);
+  finish1_kernel<T><<<wgrid(g1), kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask, walker_ws());
+  finish2_kernel<T><<<wgrid(g), kThreads, 0, st>>>(m, V, ldv, k, N, scal, gate, mask, walker_ws());
 }
 
 // ===========================================================================
 // small dense FP64 steps (one block)
 // ===========================================================================
-__global__ void lanczos_coeffs_kernel(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st) {
+__global__ void lanczos_coeffs_kernel(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st, size_t ws) {
+  A = wofs(A, ws);
+  T = wofs(T, ws);
+  C3 = wofs(C3, ws);
+  st = wofs(st, ws);
   if (st->gate & (kGateKrylov | kGateDone)) return;
   // one thread per (r, c) of a b x b block
   const int r = threadIdx.x >> 3, c = threadIdx.x & 7;
@@ -780,7 +823,7 @@ __global__ void lanczos_coeffs_kernel(const double* A, int b, int j, double* T, 
 
 void launch_lanczos_coeffs(const double* A, int b, int j, double* T, int ldT, double* C3, DevState* st,
                            cudaStream_t s) {
-  lanczos_coeffs_kernel<<<1, 64, 0, s>>>(A, b, j, T, ldT, C3, st);
+  lanczos_coeffs_kernel<<<wgrid(1), 64, 0, s>>>(A, b, j, T, ldT, C3, st, walker_ws());
 }
 
 __global__ void arnoldi_diag_kernel(const double* G1, int b, int jr, int j, double* T, int ldT, DevState* st) {
@@ -808,7 +851,12 @@ void launch_arnoldi_diag(const double* G1, int b, int jr, int j, double* T, int 
 // product are trees or split sums.
 __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int second, int j, double* Rinv,
                                                     double* Racc, double* T, int ldT, DevState* st, double rel_tol,
-                                                    int skip) {
+                                                    int skip, size_t ws) {
+  G = wofs(G, ws);
+  Rinv = wofs(Rinv, ws);
+  Racc = wofs(Racc, ws);
+  T = wofs(T, ws);
+  st = wofs(st, ws);
   // j >= 0: block Lanczos step j; j == -1: start block; j == -2: LOBPCG block
   __shared__ double Ls[MOTO_MAX_K][MOTO_MAX_K], Gs[MOTO_MAX_K][MOTO_MAX_K], Us[MOTO_MAX_K][MOTO_MAX_K];
   __shared__ double Ra[MOTO_MAX_K][MOTO_MAX_K];
@@ -957,7 +1005,7 @@ __global__ void __launch_bounds__(64) cholqr_kernel(const double* G, int b, int 
 
 void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, double* Racc, double* T, int ldT,
                    DevState* st, double rel_tol, cudaStream_t s, int skip) {
-  cholqr_kernel<<<1, 64, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol, skip);
+  cholqr_kernel<<<wgrid(1), 64, 0, s>>>(G, b, second, j, Rinv, Racc, T, ldT, st, rel_tol, skip, walker_ws());
 }
 
 // Cyclic Jacobi with round-robin (parallel) ordering on an n x n symmetric
@@ -1255,7 +1303,15 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict__ g, const T* __restrict__ V,
                                                              size_t ldv, int nv, const double* dots, T* G, int N,
                                                              double* part, unsigned* counter, double* fmax_out,
-                                                             const int* gate, int mask) {
+                                                             const int* gate, int mask, size_t ws) {
+  g = wofs(g, ws);
+  V = wofs(V, ws);
+  dots = wofs(dots, ws);
+  G = wofs(G, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  fmax_out = wofs(fmax_out, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   __shared__ T a[MOTO_MAX_K];
   if (threadIdx.x < MOTO_MAX_K) a[threadIdx.x] = (int)threadIdx.x < nv ? (T)(2.0 * dots[threadIdx.x]) : (T)0;
@@ -1289,8 +1345,8 @@ __global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict
 template <typename T>
 void launch_mmf_force(const T* g, const T* V, size_t ldv, int nv, const double* dots, T* G, int N, double* part,
                       unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
-  mmf_force_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(g, nv > 0 ? V : nullptr, ldv, nv, dots, G, N, part,
-                                                           counter, fmax_out, gate, mask);
+  mmf_force_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(g, nv > 0 ? V : nullptr, ldv, nv, dots, G, N, part,
+                                                           counter, fmax_out, gate, mask, walker_ws());
 }
 
 // ---- nonlinear CG (Polak-Ribiere+, spectral step; see internal.h) ----
@@ -1390,7 +1446,15 @@ void launch_cg_direction(const T* m, const T* G, T* p, int N, const double* cg, 
 template <typename T>
 __global__ void lbfgs_pair_kernel(const T* __restrict__ m, const T* __restrict__ d_prev,
                                   const T* __restrict__ G_prev, const T* __restrict__ G, T* ring, size_t ld,
-                                  T* stage, const DevState* dst, int N, const int* gate, int mask) {
+                                  T* stage, const DevState* dst, int N, const int* gate, int mask, size_t ws) {
+  m = wofs(m, ws);
+  d_prev = wofs(d_prev, ws);
+  G_prev = wofs(G_prev, ws);
+  G = wofs(G, ws);
+  ring = wofs(ring, ws);
+  stage = wofs(stage, ws);
+  dst = wofs(dst, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   if (!dst->lb_have_prev) return;
   T* s_out = ring + (size_t)(2 * dst->lb_head) * ld;
@@ -1422,8 +1486,8 @@ __global__ void lbfgs_pair_kernel(const T* __restrict__ m, const T* __restrict__
 template <typename T>
 void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
                        const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
-  lbfgs_pair_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, d_prev, G_prev, G, ring, ld, stage, dst, N, gate,
-                                                            mask);
+  lbfgs_pair_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, d_prev, G_prev, G, ring, ld, stage, dst, N, gate,
+                                                            mask, walker_ws());
 }
 
 // Two-loop recursion in coefficient space over the basis
@@ -1435,7 +1499,11 @@ void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G,
 // t, its dots with G, the candidate s and the candidate y at 3 t, 3 t + 1 and
 // 3 t + 2.
 __global__ void lbfgs_solve_kernel(double* Mg, int mem, const double* newdots, double gamma0, double* coef,
-                                   DevState* dst) {
+                                   DevState* dst, size_t ws) {
+  Mg = wofs(Mg, ws);
+  newdots = wofs(newdots, ws);
+  coef = wofs(coef, ws);
+  dst = wofs(dst, ws);
   if (dst->gate & kGateDone) return;
   const int R = mem + 1;
   const int nb = 2 * R + 1, gi = 2 * R;
@@ -1519,7 +1587,7 @@ __global__ void lbfgs_solve_kernel(double* Mg, int mem, const double* newdots, d
 
 void launch_lbfgs_solve(double* M, int mem, const double* newdots, double gamma0, double* coef, DevState* dst,
                         cudaStream_t st) {
-  lbfgs_solve_kernel<<<1, 32, 0, st>>>(M, mem, newdots, gamma0, coef, dst);
+  lbfgs_solve_kernel<<<wgrid(1), 32, 0, st>>>(M, mem, newdots, gamma0, coef, dst, walker_ws());
 }
 
 // d = P(sum_t coef_t b_t); max_i |d_i| -> step scale min(1, theta_max / max).
@@ -1528,7 +1596,15 @@ __global__ void __launch_bounds__(kThreads) lbfgs_direction_kernel(const T* __re
                                                                    const double* coef, const T* __restrict__ m,
                                                                    T* d, int N, double theta_max, double* part,
                                                                    unsigned* counter, DevState* dst,
-                                                                   const int* gate, int mask) {
+                                                                   const int* gate, int mask, size_t ws) {
+  basis = wofs(basis, ws);
+  coef = wofs(coef, ws);
+  m = wofs(m, ws);
+  d = wofs(d, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  dst = wofs(dst, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   __shared__ T cf[2 * MOTO_MAX_MEM + 3];
   if (threadIdx.x < nb) cf[threadIdx.x] = (T)coef[threadIdx.x];
@@ -1572,8 +1648,8 @@ template <typename T>
 void launch_lbfgs_direction(const T* basis, size_t ld, int nb, const double* coef, const T* m, T* d, int N,
                             double theta_max, double* part, unsigned* counter, DevState* dst, const int* gate,
                             int mask, cudaStream_t st) {
-  lbfgs_direction_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(basis, ld, nb, coef, m, d, N, theta_max, part,
-                                                                 counter, dst, gate, mask);
+  lbfgs_direction_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(basis, ld, nb, coef, m, d, N, theta_max, part,
+                                                                 counter, dst, gate, mask, walker_ws());
 }
 
 // d <- scale d;  m_i <- m_i cos|d_i| + d_i/|d_i| sin|d_i|, renormalised.
@@ -1605,7 +1681,11 @@ __device__ __forceinline__ void rodrigues(T& m0, T& m1, T& m2, T d0, T d1, T d2)
 }
 
 template <typename T>
-__global__ void retract_kernel(T* m, T* d, const DevState* dst, int N, const int* gate, int mask) {
+__global__ void retract_kernel(T* m, T* d, const DevState* dst, int N, const int* gate, int mask, size_t ws) {
+  m = wofs(m, ws);
+  d = wofs(d, ws);
+  dst = wofs(dst, ws);
+  gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   const T sc = (T)dst->scale;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
@@ -1623,7 +1703,7 @@ __global__ void retract_kernel(T* m, T* d, const DevState* dst, int N, const int
 
 template <typename T>
 void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
-  retract_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, d, dst, N, gate, mask);
+  retract_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, d, dst, N, gate, mask, walker_ws());
 }
 
 template <typename T>
@@ -1735,7 +1815,11 @@ void launch_llg_correct(T* m, const T* g0, const T* mp, const T* g1, double alph
 // Descent seed: out = Rodrigues(m, sign * eta * v1), eta = eta_theta / max|v1_i|.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) vmax_kernel(const T* v, int N, double* part, unsigned* counter,
-                                                        double* out) {
+                                                        double* out, size_t ws) {
+  v = wofs(v, ws);
+  part = wofs(part, ws);
+  counter = wofs(counter, ws);
+  out = wofs(out, ws);
   double mx = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const double a = v[i], b = v[N + i], c = v[2 * (size_t)N + i];
@@ -1756,7 +1840,11 @@ __global__ void __launch_bounds__(kThreads) vmax_kernel(const T* v, int N, doubl
 
 template <typename T>
 __global__ void seed_kernel(const T* m, const T* v1, const double* vmax, double eta_theta, double sign, T* out,
-                            int N) {
+                            int N, size_t ws) {
+  m = wofs(m, ws);
+  v1 = wofs(v1, ws);
+  vmax = wofs(vmax, ws);
+  out = wofs(out, ws);
   const T f = (T)(sign * eta_theta / vmax[0]);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     T m0 = m[i], m1 = m[N + i], m2 = m[2 * (size_t)N + i];
@@ -1770,15 +1858,22 @@ __global__ void seed_kernel(const T* m, const T* v1, const double* vmax, double 
 template <typename T>
 void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign, T* out, int N, double* part,
                          unsigned* counter, double* scal, cudaStream_t st) {
-  vmax_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(v1, N, part, counter, scal);
-  seed_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, v1, scal, eta_theta, sign, out, N);
+  vmax_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(v1, N, part, counter, scal, walker_ws());
+  seed_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, v1, scal, eta_theta, sign, out, N, walker_ws());
 }
 
 // Saddle / minimum test and the per-step output vector.
 // last: the final test of a run (no step follows it, so none is counted)
 __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
                                    double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst,
-                                   int ascent, int last) {
+                                   int ascent, int last, size_t ws) {
+  eg_out = wofs(eg_out, ws);
+  fmax = wofs(fmax, ws);
+  lam = wofs(lam, ws);
+  gdot = wofs(gdot, ws);
+  out6 = wofs(out6, ws);
+  status_out = wofs(status_out, ws);
+  dst = wofs(dst, ws);
   if (threadIdx.x != 0) return;
   if (dst->gate & kGateDone) {
     if (status_out) *status_out = 1;
@@ -1818,8 +1913,8 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
                         double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst, int ascent,
                         int last, cudaStream_t st) {
-  saddle_test_kernel<<<1, 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, tau_lambda, out6, status_out, dst, ascent,
-                                       last);
+  saddle_test_kernel<<<wgrid(1), 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, tau_lambda, out6, status_out, dst, ascent,
+                                       last, walker_ws());
 }
 
 #define INST(T)                                                                                                   \

@@ -60,8 +60,12 @@ def _run_single(walkers, dtype, params):
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_batch_equals_walkers_run_alone(dtype):
+    """Walkers of equal lattices form one group whose every kernel runs once
+    for all of them (walker = blockIdx.z): three 20 x 20 walkers, two 24 x 18,
+    one 16 x 16.  Each walker's per-walker grids are those of a lone walker,
+    so the results are bit-equal."""
     require_gpu()
-    sizes = [(20, 20), (24, 18), (16, 16), (20, 20)]
+    sizes = [(20, 20), (24, 18), (16, 16), (20, 20), (20, 20), (24, 18)]
     params = dict(k=1, block=1, krylov_steps=40, max_steps=120, descent_max_steps=400)
     walkers = _walkers(sizes, dtype, 1, 4100)
     b = _run_batch(walkers, dtype, params)
@@ -75,6 +79,45 @@ def test_batch_equals_walkers_run_alone(dtype):
         np.testing.assert_array_equal(b["mp"][i], s["mp"][i])
         np.testing.assert_array_equal(b["mm"][i], s["mm"][i])
         np.testing.assert_array_equal(b["out"][i][:4], s["out"][i][:4])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32])
+def test_batch_block_lanczos_selective_group(dtype):
+    """A group of four equal walkers with k = 2 block Lanczos and selective
+    reorthogonalisation (the saddle-search configuration of the batched
+    explorer) equals the walkers run alone."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    sizes = [(24, 24)] * 4
+    params = dict(k=2, block=2, krylov_steps=12, max_steps=60, descent_max_steps=200,
+                  reorth=mo.MOTO_REORTH_SELECTIVE, tau_lambda=1e-4)
+    walkers = _walkers(sizes, dtype, 2, 4300)
+    b = _run_batch(walkers, dtype, params)
+    s = _run_single(walkers, dtype, params)
+    assert b["status"] == s["status"]
+    assert b["steps"] == s["steps"]
+    for i in range(len(sizes)):
+        np.testing.assert_array_equal(b["m"][i], s["m"][i])
+        np.testing.assert_array_equal(b["V"][i], s["V"][i])
+        np.testing.assert_array_equal(b["rec"][i], s["rec"][i])
+        np.testing.assert_array_equal(b["mp"][i], s["mp"][i])
+        np.testing.assert_array_equal(b["out"][i][:4], s["out"][i][:4])
+
+
+def test_batch_with_cg_runs_walkers_alone():
+    """Nonlinear CG has no walker dimension: each walker is a group of one,
+    and the batch still equals the walkers run alone."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    sizes = [(20, 20), (20, 20)]
+    params = dict(k=2, block=2, krylov_steps=15, max_steps=80, descent_max_steps=200, optimizer=mo.MOTO_OPT_CG)
+    walkers = _walkers(sizes, torch.float64, 2, 4500)
+    b = _run_batch(walkers, torch.float64, params)
+    s = _run_single(walkers, torch.float64, params)
+    assert b["status"] == s["status"] and b["steps"] == s["steps"]
+    for i in range(len(sizes)):
+        np.testing.assert_array_equal(b["m"][i], s["m"][i])
+        np.testing.assert_array_equal(b["rec"][i], s["rec"][i])
 
 
 def oracle_certify(M, m_gpu, V_gpu, steps=30, dense_max_sites=1600, max_refine=50, tau_lambda=0.0):
