@@ -95,8 +95,8 @@ enum {
 #define MOTO_MAX_BASIS 96   /* Krylov basis vectors (block * steps) */
 #define MOTO_MAX_MEM 8      /* L-BFGS pairs */
 #define MOTO_MAX_POP 64     /* candidates of one pairwise-distance call */
-#define MOTO_MAX_PAIRS 128  /* ordered pairs of a pair-list Hamiltonian */
-#define MOTO_MAX_REACH 8    /* largest |d1|, |d2| of a pair offset */
+#define MOTO_MAX_PAIRS 512  /* ordered pairs of a pair-list Hamiltonian */
+#define MOTO_MAX_REACH 12   /* largest |d1|, |d2| of a pair offset */
 
 /* Spin Hamiltonian of Eq. param-hamiltonian (Methods, "Spin Hamiltonian and
  * manifold gradient"), read with ordered-pair sums (each bond counted twice):

@@ -321,3 +321,93 @@ def random_pairs(seed: int, reach: int, n_offsets: int):
         out.append((d1, d2, J, D))
         out.append((-d1, -d2, J, tuple(-x for x in D)))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Pd/Fe/Ir(111) pair list from the paper's printed parameter tables
+# ----------------------------------------------------------------------------
+MRY_TO_MEV = 13.605693122994  # 1 mRy in meV (Rydberg energy 13.605693122994 eV)
+
+
+def pdfeir_table():
+    """The 360 printed rows of Supplementary Note 4 (exchange and DMI tables,
+    same pair order): array of [J, Dx, Dy, Dz, |r|] in mRy and the printed
+    length unit (nearest neighbours at 0.707107)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "pdfeir_supp_note4.txt")
+    return np.loadtxt(path, comments="#")
+
+
+def _shell_offsets(n2: int, reach: int):
+    """Index-space offsets (d1, d2) with d1^2 + d1 d2 + d2^2 = n2 (squared
+    length in nearest-neighbour units on the triangular lattice)."""
+    return [(d1, d2) for d1 in range(-reach, reach + 1) for d2 in range(-reach, reach + 1)
+            if d1 * d1 + d1 * d2 + d2 * d2 == n2]
+
+
+def pdfeir_assignment(reach: int = 12):
+    """The row-to-offset assignment of reading R23 (see pdfeir_pairs): a list
+    of (row, d1, d2, Dx, Dy) with the in-plane DMI components of the row in the
+    rotated frame (mRy)."""
+    tab = pdfeir_table()
+    rnn = 0.7071067811865476
+    n2 = np.rint((tab[:, 4] / rnn) ** 2).astype(int)
+    # frame: the nearest-neighbour D vectors' in-plane angles minus 90 degrees
+    # are the bond angles; rotate them onto multiples of 60 degrees
+    nn = tab[n2 == 1]
+    bond = np.arctan2(nn[:, 2], nn[:, 1]) - 0.5 * math.pi
+    rot = -np.angle(np.exp(6j * bond).mean()) / 6.0
+    c, s = math.cos(rot), math.sin(rot)
+    out = []
+    for sh in sorted(set(n2.tolist())):
+        rows = np.nonzero(n2 == sh)[0]
+        offs = _shell_offsets(int(sh), reach)
+        if len(offs) != len(rows):
+            raise ValueError(f"shell {sh}: {len(rows)} rows for {len(offs)} offsets")
+        Dx = c * tab[rows, 1] - s * tab[rows, 2]
+        Dy = s * tab[rows, 1] + c * tab[rows, 2]
+        ang_rows = np.arctan2(Dy, Dx)
+        # z x r_hat for r = d1 a1 + d2 a2 (a1 = (1, 0), a2 = (1/2, sqrt(3)/2))
+        ang_offs = np.array([math.atan2(d1 + 0.5 * d2, -(math.sqrt(3) / 2) * d2) for d1, d2 in offs])
+        ir = np.argsort(ang_rows, kind="stable")
+        io = np.argsort(ang_offs, kind="stable")
+        best, best_shift = None, 0
+        for sft in range(len(rows)):
+            dif = np.angle(np.exp(1j * (ang_rows[ir] - ang_offs[np.roll(io, -sft)])))
+            cost = float(np.sum(dif * dif))
+            if best is None or cost < best - 1e-12:
+                best, best_shift = cost, sft
+        io = np.roll(io, -best_shift)
+        for a, b in zip(ir, io):
+            out.append((int(rows[a]), offs[b][0], offs[b][1], float(Dx[a]), float(Dy[a])))
+    return out
+
+
+def pdfeir_pairs(reach: int = 12):
+    """Pair list (d1, d2, J, (Dx, Dy, Dz)) in meV for the general pair-list
+    Hamiltonian, from the printed tables (reading R23):
+
+    * |r| in units of the printed nearest-neighbour distance (0.707107) gives
+      the shell n2 = |r|^2, whose triangular-lattice offsets the table's rows
+      of that length populate (the row counts equal the shell sizes).
+    * The tables give no bond directions.  The frame is rotated about z so that
+      the nearest-neighbour DMI vectors are Neel, D = |D| z x r_hat, with the
+      bonds along a1 and its 60-degree images; in every shell the rows, sorted
+      by the angle of the in-plane part of D, are matched in that cyclic order
+      to the offsets sorted by the angle of z x r_hat, with the cyclic shift of
+      least angular mismatch.  Each row's J goes with its D (one pair order).
+    * Of the two rows of a bond (d and -d) the one on the half plane d1 > 0 or
+      (d1 == 0, d2 > 0) is kept and its reverse is set to (J, -D), which is the
+      closure an ordered-pair sum needs.
+    * mRy -> meV by the Rydberg energy."""
+    tab = pdfeir_table()
+    out = {}
+    for row, d1, d2, Dx, Dy in pdfeir_assignment(reach):
+        if d1 > 0 or (d1 == 0 and d2 > 0):
+            out[(d1, d2)] = (float(tab[row, 0]) * MRY_TO_MEV,
+                             (Dx * MRY_TO_MEV, Dy * MRY_TO_MEV, float(tab[row, 3]) * MRY_TO_MEV))
+    pairs = []
+    for (d1, d2), (J, D) in sorted(out.items()):
+        pairs.append((d1, d2, J, D))
+        pairs.append((-d1, -d2, J, (-D[0], -D[1], -D[2])))
+    return pairs

@@ -24,7 +24,7 @@ MOTO_OPT_LBFGS, MOTO_OPT_CG = 0, 1
 MOTO_DESCENT_OPT, MOTO_DESCENT_LLG = 0, 1
 MOTO_REORTH_FULL, MOTO_REORTH_SELECTIVE = 0, 1
 MOTO_MAX_POP = 64
-MOTO_MAX_PAIRS, MOTO_MAX_REACH = 128, 8
+MOTO_MAX_PAIRS, MOTO_MAX_REACH = 512, 12
 MOTO_MAX_K, MOTO_MAX_BASIS, MOTO_MAX_MEM = 8, 96, 8
 
 

@@ -1,6 +1,8 @@
 """GPU parity of the general pair-list Hamiltonian: energy, Riemannian
 gradient, tangent HVP and the Euclidean derivatives against the pair-list
-oracle (FP64, FP32; ragged lattices, reach 3 and the maximal reach 8), the
+oracle (FP64, FP32; ragged lattices, reach 3 and 8, and the paper's own
+Pd/Fe/Ir(111) parameter tables: 360 ordered pairs out to reach 11 on a
+100 x 100 lattice), the
 shell model entered as a pair list matching the built-in stencils, and the
 eigensolver running on a pair-list context against the dense spectrum."""
 import numpy as np
@@ -25,10 +27,15 @@ def _pair_ctx(L1, L2, pl, dtype, K=0.07, muB=0.03):
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
-@pytest.mark.parametrize("L1,L2,reach,nofs", [(37, 29, 3, 12), (40, 36, 8, 40)])
+@pytest.mark.parametrize("L1,L2,reach,nofs", [(37, 29, 3, 12), (40, 36, 8, 40), (100, 100, 11, "paper")])
 def test_pair_stencils_match_the_oracle(dtype, tol, L1, L2, reach, nofs):
     require_gpu()
-    pl = inputs.random_pairs(300 + reach, reach=reach, n_offsets=nofs)
+    if nofs == "paper":
+        # the Supplementary Note 4 tables (reading R23), K and muB at stated readings
+        pl = inputs.pdfeir_pairs()
+        assert len(pl) == 360 and max(max(abs(p[0]), abs(p[1])) for p in pl) == reach
+    else:
+        pl = inputs.random_pairs(300 + reach, reach=reach, n_offsets=nofs)
     ctx, pm = _pair_ctx(L1, L2, pl, dtype)
     m = inputs.add_noise(inputs.skyrmion(L1, L2, 4.0), 0.1, 310 + reach)
     md = to_dev(m, dtype)
