@@ -4,9 +4,18 @@
 anisotropy, Zeeman; FP32 spin fields; biskyrmion Q = 2 start).
 
 A step = moto_mmf_step (energy + Riemannian gradient; k = 8 block Lanczos,
-block 8 x 12 steps = 96 HVPs with FP64-accumulated CGS2 reorthogonalisation and
-FP64 Rayleigh-Ritz; reflected force F - 2 (F.v1) v1; saddle test; L-BFGS
-direction; Rodrigues retraction) followed by the topological charge.
+block 8 x 12 steps = 96 HVPs, selective reorthogonalisation against the basis
+driven by the block omega estimate (the full pass runs when the estimated
+loss of orthogonality crosses sqrt(eps)) with two-float accumulated sums, FP64
+Rayleigh-Ritz; reflected force F - 2 (F.v1) v1; saddle test; L-BFGS
+direction; Rodrigues retraction) followed by the topological charge.  The
+step with a full reorthogonalisation pass every block is reported beside it
+(variants.full_reorth).
+
+A second leg measures the batched explorer workload (128 x 128 walkers,
+random-charge textures with masked perturbations, k = 2): certified saddles
+per second of walkers batched in FP32 (one walker-indexed launch per phase)
+against the plain FP64 path run one walker at a time.
 
 metric: spin-HVP throughput of the whole step, N * (HVPs per step) / step time.
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
@@ -36,11 +45,13 @@ HVP_PER_STEP = BLOCK * STEPS
 METRIC = "spin-HVP Gspin/s"
 UNIT = "Gspin-HVP/s"
 TILE_CLASSES = ("gram", "reorth_gram", "reorth_update")
-# DRAM bytes (read + write) per tile2d launch of one MMF step, measured with
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum) at 1024 x 1024; every
-# launch scales with the number of sites
-TILE_TRAFFIC_1024 = 516.74e6
-WORKLOAD = "roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12)"
+# DRAM bytes (read + write) per launch of the dominant kernel class, measured
+# with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 1024 x 1024
+# case of the same step (profiles/), scaled by sites; None until measured for
+# the current kernels
+TRAFFIC_1024 = {}
+WORKLOAD = ("roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12), "
+            "selective reorthogonalisation")
 
 
 def dist_env():
@@ -156,14 +167,50 @@ def oracle_sample(m, v_block, n_hvp):
     return time.perf_counter() - t0
 
 
+def _pool_worker(args):
+    """One process of the all-cores oracle leg: builds the workload's state
+    (untimed), then times n_hvp tangent HVPs; returns its compute interval on
+    the host's monotonic clock."""
+    seed, n_hvp, lat = args
+    global L
+    L = lat
+    from oracle import spin
+    from oracle.model import model_from_workload
+    M = model_from_workload(dict(inputs.WORKLOADS[4], L1=L, L2=L))
+    m = inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, 0))
+    _, s = spin.riemann_grad(M, m)
+    v = spin.project(m, inputs.gaussian_field(seed, L, L))
+    t0 = time.perf_counter()
+    for _ in range(n_hvp):
+        spin.hvp(M, m, s, v)
+    return t0, time.perf_counter()
+
+
 def cpu_baseline(m, n_hvp=8):
+    """The FP64 oracle on the host: one core (energy + gradient and n_hvp HVPs
+    in this process), then every core (a spawn-started process pool, one
+    process per core, each timing 2 HVPs on the full lattice; the wall interval
+    from the first start to the last end)."""
     from oracle import spin
     v = [spin.project(m, x) for x in start_block(2, 4242)]
     t = oracle_sample(m, v, n_hvp)
-    value = L * L * n_hvp / t / 1e9
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"energy+gradient and {n_hvp} tangent HVPs of the numpy FP64 oracle on the full "
-                      f"2048x2048 lattice ({t:.1f} s); numpy elementwise ops run on one host core"}
+    one = L * L * n_hvp / t / 1e9
+    cores = min(os.cpu_count() or 1, 64)
+    allc = None
+    try:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_pool_worker, [(5000 + k, 2, L) for k in range(cores)])
+        wall = max(b for _, b in res) - min(a for a, _ in res)
+        allc = L * L * 2 * cores / wall / 1e9
+    except Exception as e:  # the single-core figure still stands
+        print(f"all-cores oracle leg skipped: {e}", file=sys.stderr)
+    value = allc if allc is not None else one
+    return {"value": value, "unit": UNIT, "cores": cores if allc is not None else 1, "kind": "oracle",
+            "sample": f"numpy FP64 oracle on the full {L}x{L} lattice: {cores} spawned processes x 2 tangent "
+                      f"HVPs each (all host cores); one core: energy+gradient and {n_hvp} HVPs in {t:.1f} s",
+            "one_core": {"value": one, "unit": UNIT, "cores": 1}}
 
 
 def run_reference(args, rank, world):
@@ -190,6 +237,71 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+# batched explorer walkers: certified saddles per second
+# ----------------------------------------------------------------------------
+SADDLE_L = 128
+SADDLE_PARAMS = dict(k=2, block=2, krylov_steps=30, tau_F=1e-3, tau_lambda=1e-4)
+
+
+def saddle_walkers(ws, dtype):
+    import torch
+    out = []
+    for w in ws:
+        m = inputs.workload3_walker(w, SADDLE_L)
+        V = np.stack([inputs.gaussian_field(inputs.workload_seed(3, 500 + 10 * w + j), SADDLE_L, SADDLE_L)
+                      for j in range(2)])
+        out.append((torch.from_numpy(m).to("cuda", dtype), torch.from_numpy(V).to("cuda", dtype)))
+    return out
+
+
+def saddle_leg(n_batch, n_fp64, max_steps):
+    """Walkers 0 .. n_batch-1 of the batched explorer workload in one FP32
+    batch (selective reorthogonalisation), and walkers 0 .. n_fp64-1 in FP64
+    one at a time through the plain one-walker path (full reorthogonalisation,
+    the library defaults); both with tau_F = 1e-3 meV/rad (1e-6 eV/rad),
+    tau_lambda = 1e-4 meV and the same step cap.  A saddle counts when the
+    walker's saddle test passed.  Times are host wall clock around the
+    synchronous ascent calls (contexts created beforehand)."""
+    import torch
+    import paper_2509_26269_gb300 as mo
+    from paper_2509_26269_gb300 import Batch, Context
+    p = inputs.WORKLOADS[3]
+    model = dict(J=p["J"], D=p["D"], K=p["K"], muB=p["muB"])
+    res = {"lattice": f"{SADDLE_L}x{SADDLE_L}", "max_steps": max_steps, "tau_F_meV_per_rad": 1e-3,
+           "tau_lambda_meV": 1e-4, "k": 2, "krylov": "block Lanczos 2 x 30"}
+    walk = saddle_walkers(range(n_batch), torch.float32)
+    b = Batch(walk, dtype=torch.float32, n_streams=4, max_steps=max_steps, reorth=mo.MOTO_REORTH_SELECTIVE,
+              **model, **SADDLE_PARAMS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, status, steps, rec = b.ascend(check_every=50)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    b.close()
+    conv = int(sum(1 for x in status if x == 0))
+    res["fp32_batched"] = {"walkers": n_batch, "saddles": conv, "seconds": t, "saddles_per_s": conv / t,
+                           "mean_steps": float(np.mean(steps)), "max_steps_taken": int(max(steps)),
+                           "reorth": "selective"}
+    tot, conv64, st64 = 0.0, 0, []
+    for w, (m, V) in enumerate(saddle_walkers(range(n_fp64), torch.float64)):
+        ctx = Context(SADDLE_L, SADDLE_L, dtype=torch.float64, max_steps=max_steps, **model, **SADDLE_PARAMS)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, s, _ = ctx.ascend(m, V, check_every=50)
+        torch.cuda.synchronize()
+        tot += time.perf_counter() - t0
+        conv64 += rc == 0
+        st64.append(s)
+        ctx.close()
+    res["fp64_one_walker"] = {"walkers": n_fp64, "saddles": conv64, "seconds": tot,
+                              "saddles_per_s": conv64 / tot if tot > 0 else 0.0,
+                              "mean_steps": float(np.mean(st64)) if st64 else 0.0, "reorth": "full"}
+    f64 = res["fp64_one_walker"]["saddles_per_s"]
+    res["ratio"] = res["fp32_batched"]["saddles_per_s"] / f64 if f64 > 0 else None
+    return res
+
+
+# ----------------------------------------------------------------------------
 # GPU leg
 # ----------------------------------------------------------------------------
 def run_ours(args, rank, world, local):
@@ -204,7 +316,7 @@ def run_ours(args, rank, world, local):
 
     p = inputs.WORKLOADS[4]
     ctx = Context(L, L, J=p["J"], D=p["D"], K=p["K"], muB=p["muB"], dtype=torch.float32,
-                  k=K_MODES, block=BLOCK, krylov_steps=STEPS)
+                  k=K_MODES, block=BLOCK, krylov_steps=STEPS, reorth=mo.MOTO_REORTH_SELECTIVE)
     walker = walker_of(rank)
     m_host = inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, walker))
     m0 = torch.from_numpy(m_host).to(device="cuda", dtype=torch.float32)
@@ -299,8 +411,8 @@ def run_ours(args, rank, world, local):
     # nonlinear CG instead of L-BFGS, and the subspace reflection over all k
     # modes: a few steps each from the same start, CUDA-event timed
     variants = {}
-    for vname, over in (("cg", {"optimizer": mo.MOTO_OPT_CG}), ("subspace_k8", {"subspace": 1}),
-                        ("selective_reorth", {"reorth": mo.MOTO_REORTH_SELECTIVE})):
+    for vname, over in (("full_reorth", {"reorth": mo.MOTO_REORTH_FULL}), ("cg", {"optimizer": mo.MOTO_OPT_CG}),
+                        ("subspace_k8", {"subspace": 1})):
         pv = mo.make_params(**{f: getattr(params, f) for f, _ in params._fields_})
         for f, v in over.items():
             setattr(pv, f, v)
@@ -364,6 +476,11 @@ def run_ours(args, rank, world, local):
            "note": "one Heun step = two energy/gradient stencils + predictor + corrector; includes the seeds, "
                    "the end energies and charges and two host reads of the status word"}
 
+    # ---- batched explorer walkers (saddles/s), rank 0 at one GPU only ---------
+    saddles = None
+    if world == 1 and args.saddle_walkers > 0:
+        saddles = saddle_leg(args.saddle_walkers, args.saddle_fp64, args.saddle_steps)
+
     line = None
     if rank == 0:
         cpu = cpu_baseline(m_host) if (world == 1 and not args.no_cpu_baseline) else None
@@ -374,7 +491,7 @@ def run_ours(args, rank, world, local):
             "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single"}),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": TILE_TRAFFIC_1024 * (L / 1024) ** 2 if dom == "tile2d" else None,
+                         "traffic": TRAFFIC_1024[dom] * (L / 1024) ** 2 if dom in TRAFFIC_1024 else None,
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at "
                                            "1024x1024, scaled by sites",
                          "peak_source": peak_kind,
@@ -385,6 +502,7 @@ def run_ours(args, rank, world, local):
             "hvp_gspin_s": (L * L * HVP_PER_STEP) / (hvp[1] * 1e-3) / 1e9 if hvp[1] else 0.0,
             "e2e": e2e,
             "variants": variants,
+            "saddles": saddles,
             "explorer": explorer,
             "llg_descent": llg,
             "gpu_launches": launches * args.steps,
@@ -406,6 +524,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--saddle-walkers", type=int, default=64,
+                    help="walkers of the batched FP32 arm of the saddles/s leg (0: leg off)")
+    ap.add_argument("--saddle-fp64", type=int, default=2, help="walkers of the one-at-a-time FP64 arm")
+    ap.add_argument("--saddle-steps", type=int, default=3000, help="ascent step cap of the saddles/s leg")
     ap.add_argument("--lattice", type=int, default=2048,
                     help="lattice side; values other than 2048 are small cases for profiler captures")
     args = ap.parse_args()
