@@ -313,7 +313,24 @@ __device__ __forceinline__ void last_block_totals(const typename strip::Red<T>::
   __shared__ double shm[32];
   R a = RD::of((T)0);
   double mx = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+  // eight blocks' partials in flight at a time (L2 latency, not arithmetic,
+  // bounds this loop), added in block order
+  int b = threadIdx.x;
+  for (; b + 7 * (int)blockDim.x < nb; b += 8 * (int)blockDim.x) {
+    R v[8];
+    double w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      v[u] = psum[b + u * blockDim.x];
+      w[u] = pmax ? __ldcg(pmax + b + u * blockDim.x) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      a = radd(a, v[u]);
+      mx = fmax(mx, w[u]);
+    }
+  }
+  for (; b < nb; b += blockDim.x) {
     a = radd(a, psum[b]);
     if (pmax) mx = fmax(mx, __ldcg(pmax + b));
   }

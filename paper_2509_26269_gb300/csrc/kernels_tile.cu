@@ -722,6 +722,14 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   const size_t cap = (size_t)kStreamBlocks * MOTO_MAX_BASIS * MOTO_MAX_K / ((size_t)na * ny);
   if (want > cap) want = cap;
   const size_t ngroups = ((n + TE - 1) / TE + tps - 1) / tps;
+  // a CTA (one an SM) pays a few microseconds of set-up and reduction, so it
+  // streams at least ~256 KB: small fields (the walkers of a batch, the local
+  // passes on small lattices) get fewer CTAs, large ones still one an SM.
+  // The rule depends on the field size only, so a walker of a batch and the
+  // same walker alone sum in the same order.
+  const size_t per_cta = std::max<size_t>(1, (262144 + tps * loaded - 1) / (tps * loaded));
+  const size_t need = (ngroups + per_cta - 1) / per_cta;
+  if (want > need) want = need;
   const int grid = (int)(ngroups < want ? (ngroups > 0 ? ngroups : 1) : want);
   tile2d_kernel<T, MODE, R, CW, NRL, TB><<<wgrid(grid), kThrT, smem, st>>>(
       mx, my, nx, ny, u0, nu, n, C, Cadd, uadd, nadd, Yout, ldo, out, part, counter, nst, tps, gate, mask, status,

@@ -245,8 +245,11 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const T* __restrict__
   }
 }
 
+// Blocks of a site-wise kernel: four sites a thread at least (a block's set-up
+// and, where there is one, its reduction are then amortised on small lattices,
+// e.g. the walkers of a batch), at most eight blocks an SM.
 static int stream_grid(size_t sites) {
-  size_t b = (sites + kThreads - 1) / kThreads;
+  size_t b = (sites + 4 * kThreads - 1) / (4 * kThreads);
   const size_t cap = (size_t)kSMs * 8;
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
@@ -561,7 +564,8 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
   if (gram) {
     if (((uintptr_t)X % (2 * sizeof(T))) || (ldx % 2)) return false;
     const size_t n = 3 * (size_t)N;
-    size_t g = ((sizeof(T) == 4 ? (n + 1) / 2 : n) + kThreads - 1) / kThreads;
+    // at least 64 KB of the fields a block (small fields: fewer blocks)
+    size_t g = (nx * n * sizeof(T) + 65535) / 65536;
     const size_t cap = (size_t)kSMs * 2;  // one wave at two blocks per SM
     if (g > cap) g = cap;
     if (g < 1) g = 1;

@@ -297,6 +297,15 @@ __device__ __forceinline__ void cp_elem(T* dst, const T* src) {
     cp_async8(dst, src);
 }
 
+// Periodic index for a coordinate at most one period outside [0, L) (the
+// staged tiles reach a few sites past the lattice): two compares; a general
+// modulo only for lattices smaller than the reach.
+__device__ __forceinline__ int wrap_near(int a, int L) {
+  if (a < 0) a += L;
+  if (a >= L) a -= L;
+  return (a >= 0 && a < L) ? a : wrap(a, L);
+}
+
 // Starts the copy of a field's staged tile: staged (ly, lx) holds lattice
 // site (x0 - kPadL + lx, y0 - 2 + ly), periodic, for ly < SY.  `vec16`: the
 // block's staged columns lie inside the lattice and every staged row starts
@@ -318,7 +327,7 @@ __device__ __forceinline__ void stage_tile(T* tile, const T* __restrict__ v, siz
   } else {
     for (int idx = threadIdx.x; idx < kSX * SY; idx += blockDim.x) {
       const int ly = idx / kSX, lx = idx - ly * kSX;
-      const int gx = wrap(x0 - kPadL + lx, L1), gy = wrap(y0 - 2 + ly, L2);
+      const int gx = wrap_near(x0 - kPadL + lx, L1), gy = wrap_near(y0 - 2 + ly, L2);
       const size_t g = (size_t)gy * L1 + gx;
       cp_elem(tile + idx, v + g);
       cp_elem(tile + kPlane + idx, v + N + g);
