@@ -526,7 +526,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--saddle-walkers", type=int, default=64,
                     help="walkers of the batched FP32 arm of the saddles/s leg (0: leg off)")
-    ap.add_argument("--saddle-fp64", type=int, default=2, help="walkers of the one-at-a-time FP64 arm")
+    ap.add_argument("--saddle-fp64", type=int, default=4, help="walkers of the one-at-a-time FP64 arm")
     ap.add_argument("--saddle-steps", type=int, default=3000, help="ascent step cap of the saddles/s leg")
     ap.add_argument("--lattice", type=int, default=2048,
                     help="lattice side; values other than 2048 are small cases for profiler captures")

@@ -417,7 +417,9 @@ const char* moto_status_string(int code);
  *   projected-matrix eigensolver, 7 block Lanczos local pass + Gram against
  *   the basis (read-only sweep), 8 block Lanczos full update + Cholesky Gram,
  *   9 second Cholesky QR Gram
- * and the algorithmic bytes of the launch (every field read or written once).
+ * and the algorithmic bytes of the launch (every field read or written once;
+ * a launch of the full pass of a selective Lanczos step counts its bytes only
+ * if the step took the pass, as the device's log of the last solve records).
  * moto_profile_end synchronises, writes per class (nkinds entries each,
  * NULL to skip) the number of launches, the summed event time in ms and the
  * summed algorithmic bytes, and releases the events.  Launches beyond

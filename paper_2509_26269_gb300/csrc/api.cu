@@ -54,6 +54,8 @@ struct moto_ctx {
   cudaEvent_t* prof_ev;
   int* prof_kind;
   double* prof_bytes;
+  int* prof_cond;    // >= 0: the launch ran only if step prof_cond's full pass was taken
+  int prof_cond_cur;  // the step of the conditional launches being enqueued (-1: none)
   cudaStream_t prof_stream;
   // bound of the streaming kernel's consumer waits (moto_set_wait_limit; 0 = default)
   int wait_polls;
@@ -83,6 +85,7 @@ struct ProfScope {
       on = true;
       c->prof_kind[c->prof_n] = kind;
       c->prof_bytes[c->prof_n] = bytes;
+      c->prof_cond[c->prof_n] = c->prof_cond_cur;
       cudaEventRecord(c->prof_ev[2 * c->prof_n], st);
       c->prof_stream = st;
     }
@@ -337,7 +340,8 @@ constexpr size_t kMmfDots = kLobAux + 64 * MOTO_MAX_K;             // MAX_K: g .
 constexpr size_t kCg = kMmfDots + MOTO_MAX_K;                      // 12: Gram of [G, s, y], |G_prev|^2, beta, alpha
 constexpr size_t kOm = kCg + 12;                                   // MAX_BASIS^2: orthogonality estimates
 constexpr size_t kBout = kOm + MOTO_MAX_BASIS * MOTO_MAX_BASIS;  // 8: a batch walker's descent record
-constexpr size_t kDsmSize = kBout + 8;
+constexpr size_t kRlog = kBout + 8;                                // MAX_BASIS: full pass taken at step j (1/0)
+constexpr size_t kDsmSize = kRlog + MOTO_MAX_BASIS;
 
 constexpr int kLd = MOTO_MAX_BASIS;  // leading dimension of T
 
@@ -488,11 +492,13 @@ void block_lanczos(moto_ctx* c, const T* m, const T* s, const T* v0, size_t ld0,
       // update with the Cholesky Gram) runs this step
       P_tile<T>(c, 2, Q + (size_t)(j - jl) * b * ld, (jl + 1) * b, 0, 0, W, b, D + kC3, W, D + kG, gate, mk, st);
       P_cholqr(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, st);
-      P_omega_estimate(c, b, j, D + kT, kLd, D + kRacc, D + kOm, c->st, eps, st);
+      P_omega_estimate(c, b, j, D + kT, kLd, D + kRacc, D + kOm, D + kRlog, c->st, eps, st);
+      c->prof_cond_cur = j;  // the launches below do their work only if the estimate asked
       P_tile<T>(c, 0, Q, nq, 0, 0, W, b, nullptr, nullptr, D + kC2, gate, mk | kGateNoReorth, st);
       P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk | kGateNoReorth, st);
       P_cholqr_skip(c, D + kG, b, 0, j, D + kRinv, D + kRacc, D + kT, kLd, c->st, rel, kGateNoReorth, st);
       P_omega_reset(c, b, j, D + kRacc, D + kOm, c->st, eps, st);
+      c->prof_cond_cur = -1;
     } else {
       P_tile<T>(c, 1, Q, nq, (j - jl) * b, (jl + 1) * b, W, b, D + kC3, nullptr, D + kC2, gate, mk, st);
       P_tile<T>(c, 2, Q, nq, 0, nq, W, b, D + kC2, W, D + kG, gate, mk, st, D + kC3, (j - jl) * b, (jl + 1) * b);
@@ -701,6 +707,7 @@ int create_ctx(const moto_model* model, int dtype, const moto_params* params, in
   if (rc) return rc;
   moto_ctx* c = new moto_ctx();
   memset(c, 0, sizeof(*c));
+  c->prof_cond_cur = -1;
   c->md.L1 = model->L1;
   c->md.L2 = model->L2;
   c->md.N = model->L1 * model->L2;
@@ -1329,12 +1336,15 @@ int moto_profile_begin(moto_ctx* c, int capacity) {
   c->prof_ev = new cudaEvent_t[2 * (size_t)capacity];
   c->prof_kind = new int[capacity];
   c->prof_bytes = new double[capacity];
+  c->prof_cond = new int[capacity];
+  c->prof_cond_cur = -1;
   for (int i = 0; i < 2 * capacity; ++i) {
     if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) {
       for (int j = 0; j < i; ++j) cudaEventDestroy(c->prof_ev[j]);
       delete[] c->prof_ev;
       delete[] c->prof_kind;
       delete[] c->prof_bytes;
+      delete[] c->prof_cond;
       c->prof_ev = nullptr;
       return MOTO_ERR_CUDA;
     }
@@ -1355,7 +1365,19 @@ int moto_profile_end(moto_ctx* c, int nkinds, int* launches, double* ms, double*
     if (ms) ms[k] = 0.0;
     if (bytes) bytes[k] = 0.0;
   }
+  // conditional launches (the full pass of a selective Lanczos step) moved
+  // their bytes only if the step took the pass: the device log of the last
+  // solve says which did
+  double rlog[MOTO_MAX_BASIS];
+  bool have_log = false;
+  for (int i = 0; i < c->prof_n; ++i)
+    if (c->prof_cond[i] >= 0) have_log = true;
+  if (rc == MOTO_OK && have_log &&
+      cudaMemcpy(rlog, c->dsm + kRlog, sizeof(rlog), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = MOTO_ERR_CUDA;
   for (int i = 0; rc == MOTO_OK && i < c->prof_n; ++i) {
+    if (c->prof_cond[i] >= 0 && c->prof_cond[i] < MOTO_MAX_BASIS && rlog[c->prof_cond[i]] == 0.0)
+      c->prof_bytes[i] = 0.0;
     float t = 0.f;
     if (cudaEventElapsedTime(&t, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]) != cudaSuccess) {
       rc = MOTO_ERR_CUDA;
@@ -1372,6 +1394,7 @@ int moto_profile_end(moto_ctx* c, int nkinds, int* launches, double* ms, double*
   delete[] c->prof_ev;
   delete[] c->prof_kind;
   delete[] c->prof_bytes;
+  delete[] c->prof_cond;
   c->prof_ev = nullptr;
   c->prof_cap = c->prof_n = 0;
   return rc;

@@ -171,8 +171,8 @@ void launch_cholqr(const double* G, int b, int second, int j, double* Rinv, doub
 // Selective reorthogonalisation (kernels_omega.cu): estimates of Q_{j+1}^T Q_k
 // from the block recurrence, the decision (gate bit kGateNoReorth), and the
 // restart of the estimates after a full pass.  Om: MOTO_MAX_BASIS^2 doubles.
-void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, DevState* st,
-                           double eps, cudaStream_t s);
+void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, double* rlog,
+                           DevState* st, double eps, cudaStream_t s);
 void launch_omega_reset(int b, int j, const double* Rn, double* Om, DevState* st, double eps, cudaStream_t s);
 // Symmetric eigensolver (cyclic Jacobi, FP64) on the leading nT x nT block of
 // T (nT read from st->nT, <= 96): theta ascending (MOTO_MAX_BASIS entries,

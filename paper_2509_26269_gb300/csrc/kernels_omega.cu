@@ -37,11 +37,12 @@ __device__ __forceinline__ double tblk(const double* T, int ldT, int b, int i, i
 // One block of 1024 threads; thread (k, r, c) forms one entry of the
 // right-hand side, thread (k, c) solves one column of the triangular system.
 __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, const double* T, int ldT,
-                                                              const double* Rn, double* Om, DevState* st,
-                                                              double eps, size_t ws) {
+                                                              const double* Rn, double* Om, double* rlog,
+                                                              DevState* st, double eps, size_t ws) {
   T = wofs(T, ws);
   Rn = wofs(Rn, ws);
   Om = wofs(Om, ws);
+  rlog = wofs(rlog, ws);
   st = wofs(st, ws);
   if (st->gate & (kGateKrylov | kGateDone)) return;
   __shared__ double Bn[MOTO_MAX_K][MOTO_MAX_K];
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
     const bool forced = st->pad[3] != 0;
     const bool need = forced || !(m2 <= sqrt(eps));
     st->pad[5] = forced ? 1 : 0;
+    rlog[j] = need ? 1.0 : 0.0;  // for the launch profiler: did step j take the full pass
     if (need)
       st->gate &= ~kGateNoReorth;
     else
@@ -140,9 +142,9 @@ __global__ void omega_reset_kernel(int b, int j, const double* Rn, double* Om, D
   }
 }
 
-void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, DevState* st,
-                           double eps, cudaStream_t s) {
-  omega_estimate_kernel<<<wgrid(1), 1024, 0, s>>>(b, j, T, ldT, Rn, Om, st, eps, walker_ws());
+void launch_omega_estimate(int b, int j, const double* T, int ldT, const double* Rn, double* Om, double* rlog,
+                           DevState* st, double eps, cudaStream_t s) {
+  omega_estimate_kernel<<<wgrid(1), 1024, 0, s>>>(b, j, T, ldT, Rn, Om, rlog, st, eps, walker_ws());
 }
 
 void launch_omega_reset(int b, int j, const double* Rn, double* Om, DevState* st, double eps, cudaStream_t s) {
