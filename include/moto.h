@@ -391,6 +391,14 @@ int moto_krylov_basis(moto_ctx* ctx, const void** basis_dev, size_t* ld, int* nv
  * range); the pair-list model has its own kernel and ignores it. */
 int moto_hvp_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
 int moto_set_hvp_variant(moto_ctx* ctx, int variant);
+/* The same for the energy / gradient stencil of moto_energy_grad and the
+ * solvers (variants: staged tiles and blocks an SM; g and s are bit-identical
+ * across them, the energy's sum follows each variant's grid), timed by
+ * moto_create and recorded for (L1, L2, precision).  moto_topo_charge uses
+ * the recorded variant's layout.  The pair-list model and the FP64-arithmetic
+ * energy use their own kernels. */
+int moto_stencil_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
+int moto_set_stencil_variant(moto_ctx* ctx, int variant);
 
 /* Failure-detection control (host side only).  Every wait inside the
  * library's kernels is bounded: a consumer warp of the streaming

@@ -93,6 +93,8 @@ def _load():
         "moto_set_wait_limit": (I, [P, I]),
         "moto_hvp_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), I]),
         "moto_set_hvp_variant": (I, [P, I]),
+        "moto_stencil_tuning": (I, [P, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_float), I]),
+        "moto_set_stencil_variant": (I, [P, I]),
         "moto_krylov_basis": (I, [P, ctypes.POINTER(P), ctypes.POINTER(Z), ctypes.POINTER(I), ctypes.POINTER(I),
                                   P]),
         "moto_pairwise_l1": (I, [P, P, Z, I, P, P]),
@@ -117,7 +119,8 @@ EXPORTED = (
     "moto_status", "moto_clear_status", "moto_status_string", "moto_workspace_bytes", "moto_profile_begin",
     "moto_profile_end", "moto_energy_grad_noalloc", "moto_gram", "moto_energy_euclid_grad", "moto_euclid_hvp",
     "moto_perturb", "moto_pairwise_l1", "moto_set_pairs", "moto_set_wait_limit",
-    "moto_hvp_tuning", "moto_set_hvp_variant", "moto_krylov_basis",
+    "moto_hvp_tuning", "moto_set_hvp_variant", "moto_krylov_basis", "moto_stencil_tuning",
+    "moto_set_stencil_variant",
     "moto_batch_create", "moto_batch_destroy", "moto_batch_ascend", "moto_batch_descend",
 )
 PROFILE_KINDS = ("hvp", "gram", "combine", "stencil", "small", "vec", "eig", "reorth_gram", "reorth_update",
@@ -292,6 +295,21 @@ def moto_krylov_basis(ctx, stream=None):
     _check(_lib.moto_krylov_basis(ctx, ctypes.byref(b), ctypes.byref(ld), ctypes.byref(nv), ctypes.byref(nr),
                                   _stream(stream)), "moto_krylov_basis")
     return b.value, ld.value, nv.value, nr.value
+
+
+def moto_stencil_tuning(ctx):
+    """(energy-stencil variant in use, [ms per launch of each variant, zeros
+    unless this context ran the autotuner])."""
+    v = ctypes.c_int()
+    ms = (ctypes.c_float * 4)()
+    n = _lib.moto_stencil_tuning(ctx, ctypes.byref(v), ms, 4)
+    if n < 0:
+        raise MotoError(f"moto_stencil_tuning: {moto_status_string(n)}")
+    return v.value, [float(ms[i]) for i in range(n)]
+
+
+def moto_set_stencil_variant(ctx, variant: int):
+    _check(_lib.moto_set_stencil_variant(ctx, int(variant)), "moto_set_stencil_variant")
 
 
 def moto_set_hvp_variant(ctx, variant: int):

@@ -65,6 +65,10 @@ struct moto_ctx {
   int hvp_nvec;
   float hvp_ms[16];
   int hvp_tuned_here;
+  // energy / gradient stencil variant: forced (>= 0) or the autotuner's
+  int stencil_force;
+  float stencil_ms[4];
+  int stencil_tuned_here;
   int last_selective;  // the last block Lanczos solve reorthogonalised selectively
   // walker group (batches): nw walkers whose scratch and fields lie in
   // equally sized slices (wstride bytes) of one allocation, `arena`; the
@@ -149,7 +153,10 @@ template <typename T>
 void P_energy_grad(moto_ctx* c, const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
                    double* out, int* status, bool fp64, cudaStream_t st) {
   PROF(kPkStencil, (3.0 + (g ? 3.0 : 0.0) + (s ? 1.0 : 0.0)) * md.N * sizeof(T));
-  launch_energy_grad<T>(md, m, g, s, part, counter, out, status, fp64, st);
+  if (c->stencil_force >= 0 && md.npairs == 0 && !fp64)
+    launch_energy_grad_variant<T>(c->stencil_force, md, m, g, s, part, counter, out, status, st);
+  else
+    launch_energy_grad<T>(md, m, g, s, part, counter, out, status, fp64, st);
 }
 template <typename T>
 void P_project(moto_ctx* c, const T* m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N, const int* gate,
@@ -689,6 +696,52 @@ int autotune_hvp(moto_ctx* c) {
   return MOTO_OK;
 }
 
+// The persistent energy / gradient stencil's variants, timed like the HVP's
+// (gradient and s stored, one warm-up and three timed launches each) and
+// recorded process-wide for (L1, L2, precision).
+template <typename T>
+int autotune_stencil(moto_ctx* c) {
+  const int esz = (int)sizeof(T);
+  if (stencil_tuned_variant(c->md.L1, c->md.L2, esz) >= 0) return MOTO_OK;
+  const char* env = getenv("MOTO_AUTOTUNE");
+  if (env && strcmp(env, "0") == 0) {
+    stencil_record_variant(c->md.L1, c->md.L2, esz, 0);
+    return MOTO_OK;
+  }
+  const T* m = static_cast<const T*>(c->W);
+  T* g = static_cast<T*>(c->g);
+  T* s = static_cast<T*>(c->s);
+  double* out = c->dsm + kTmp;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < stencil_variant_count() && v < 4; ++v) {
+    launch_energy_grad_variant<T>(v, c->md, m, g, s, c->part, c->counter, out, &c->st->status, 0);
+    cudaEventRecord(e0, 0);
+    for (int r = 0; r < 3; ++r)
+      launch_energy_grad_variant<T>(v, c->md, m, g, s, c->part, c->counter, out, &c->st->status, 0);
+    cudaEventRecord(e1, 0);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(cudaGetLastError(), "autotuner timing", __LINE__);
+    }
+    c->stencil_ms[v] = ms / 3.f;
+    if (v == 0 || c->stencil_ms[v] < best_ms) {
+      best = v;
+      best_ms = c->stencil_ms[v];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  stencil_record_variant(c->md.L1, c->md.L2, esz, best);
+  c->stencil_tuned_here = 1;
+  return MOTO_OK;
+}
+
 // ----------------------------------------------------------------------------
 // Context creation.  nw == 0: one walker, every scratch area its own
 // allocation, sized for any parameters the solvers accept.  nw >= 1: a walker
@@ -787,7 +840,9 @@ int create_ctx(const moto_model* model, int dtype, const moto_params* params, in
     return MOTO_ERR_CUDA;
   }
   c->hvp_force = -1;
+  c->stencil_force = -1;
   rc = dtype == MOTO_F32 ? autotune_hvp<float>(c) : autotune_hvp<double>(c);
+  if (rc == MOTO_OK) rc = dtype == MOTO_F32 ? autotune_stencil<float>(c) : autotune_stencil<double>(c);
   if (rc == MOTO_OK) {
     // the timing launches wrote the scratch: give the solvers zeroed fields again
     if (group)
@@ -898,6 +953,24 @@ int moto_hvp_tuning(const moto_ctx* c, int* variant, float* ms, int cap) {
   }
   if (ms)
     for (int v = 0; v < cap && v < nv; ++v) ms[v] = c->hvp_tuned_here ? c->hvp_ms[v] : 0.f;
+  return nv;
+}
+
+int moto_set_stencil_variant(moto_ctx* c, int variant) {
+  if (!c || variant < -1 || variant >= stencil_variant_count()) return MOTO_ERR_ARG;
+  c->stencil_force = variant;
+  return MOTO_OK;
+}
+
+int moto_stencil_tuning(const moto_ctx* c, int* variant, float* ms, int cap) {
+  if (!c) return MOTO_ERR_ARG;
+  const int nv = stencil_variant_count();
+  if (variant) {
+    const int t = stencil_tuned_variant(c->md.L1, c->md.L2, (int)c->esize);
+    *variant = c->stencil_force >= 0 ? c->stencil_force : (t < 0 ? 0 : t);
+  }
+  if (ms)
+    for (int v = 0; v < cap && v < nv; ++v) ms[v] = c->stencil_tuned_here ? c->stencil_ms[v] : 0.f;
   return nv;
 }
 

@@ -89,6 +89,16 @@ int hvp_variant_count();
 template <typename T>
 void launch_hvp_strip_variant(int variant, const ModelDev& md, const T* m, const T* s, const T* V, size_t ldv, T* HV,
                               size_t ldhv, int nvec, const int* gate, int mask, cudaStream_t st);
+// The persistent energy / gradient and charge stencils come in variants
+// (staged tiles, blocks an SM); the autotuner records one per lattice and
+// precision (-1: none, variant 0 used).  g and s are bit-identical across
+// variants; the energy's sum follows the grid.
+int stencil_variant_count();
+int stencil_tuned_variant(int L1, int L2, int esize);
+void stencil_record_variant(int L1, int L2, int esize, int variant);
+template <typename T>
+void launch_energy_grad_variant(int variant, const ModelDev& md, const T* m, T* g, T* s, double* part,
+                                unsigned* counter, double* out, int* status, cudaStream_t st);
 // process-wide autotuner record: (L1, L2, element size, nvec) -> variant (-1: none)
 int hvp_tuned_variant(int L1, int L2, int esize, int nvec);
 void hvp_record_variant(int L1, int L2, int esize, int nvec, int variant);

@@ -12,6 +12,8 @@
 // kernel below evaluates the energy in FP64 arithmetic (moto_energy) and the
 // Euclidean gradient of the autograd path.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "internal.h"
 #include "stencil.cuh"
@@ -232,9 +234,7 @@ __device__ __forceinline__ void tile_origin(int t, int ntx, int ty_sites, int& x
 }
 
 // Tile ring of the persistent kernels: tile t + i grid is staged in buffer
-// (it + i) % kStages, so kStages - 1 tiles are in flight while one is used.
-constexpr int kStages = 3;
-
+// (it + i) % NST, so NST - 1 tiles are in flight while one is used.
 template <typename T, int TY>
 __device__ __forceinline__ void stage_one(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int t, int buf,
                                           int aligned) {
@@ -244,30 +244,32 @@ __device__ __forceinline__ void stage_one(T* tiles, const T* m, size_t N, int L1
                                             aligned && strip::tile_inside<TY>(x0, y0, L1, L2));
 }
 
-// the first kStages - 1 tiles of the block
-template <typename T, int TY>
+// the first NST - 1 tiles of the block
+template <int NST, typename T, int TY>
 __device__ __forceinline__ void stage_prologue(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int ntiles,
                                                int t0, int aligned) {
 #pragma unroll
-  for (int i = 0; i < kStages - 1; ++i) {
+  for (int i = 0; i < NST - 1; ++i) {
     const int t = t0 + i * (int)gridDim.x;
     if (t < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, t, i, aligned);
   }
 }
 
-// Before using tile t (the block's it-th): stage the tile kStages - 1
-// iterations ahead (its buffer was released by the barrier at the end of the
-// previous iteration), then wait until tile t has landed: the copy groups
-// issued after it may stay pending.
-template <typename T, int TY>
+// Before using tile t (the block's it-th): stage the tile NST - 1 iterations
+// ahead (its buffer was released by the barrier at the end of the previous
+// iteration), then wait until tile t has landed: the copy groups issued after
+// it may stay pending.
+template <int NST, typename T, int TY>
 __device__ __forceinline__ void stage_next(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int ntiles, int t,
                                            int it, int aligned) {
-  const int ahead = t + (kStages - 1) * (int)gridDim.x;
-  if (ahead < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, ahead, (it + kStages - 1) % kStages, aligned);
+  static_assert(NST >= 2 && NST <= 3, "two or three staged tiles");
+  const int ahead = t + (NST - 1) * (int)gridDim.x;
+  if (ahead < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, ahead, (it + NST - 1) % NST, aligned);
   const int later = (ntiles - 1 - t) / (int)gridDim.x;  // tiles of this block after t
-  if (later >= 2)
+  const int pend = later < NST - 1 ? later : NST - 1;
+  if (pend >= 2)
     strip::cp_async_wait<2>();
-  else if (later == 1)
+  else if (pend == 1)
     strip::cp_async_wait<1>();
   else
     strip::cp_async_wait<0>();
@@ -349,8 +351,8 @@ __device__ __forceinline__ void last_block_totals(const typename strip::Red<T>::
 // g_i = grad_i E - s_i m_i; E = sum_i (s_i - muB m_iz) / 2 (E is quadratic in
 // m).  out = [E, max_i |g_i|].  Partials: part[0 .. grid) the block energies
 // (8-byte reduction values), part[grid .. 2 grid) the block maxima of |g|^2.
-template <typename T, int SW, int WY>
-__global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md, strip::Weights<T> hw, T muB,
+template <typename T, int SW, int WY, int NST, int MINB>
+__global__ void __launch_bounds__(32 * WY, MINB) energy_grad_strip_kernel(ModelDev md, strip::Weights<T> hw, T muB,
                                                                     const T* __restrict__ m, T* __restrict__ g,
                                                                     T* __restrict__ s, double* part, unsigned* counter,
                                                                     double* out, int* status, int aligned, int ntx,
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md,
   typedef Red<T> RD;
   typedef typename RD::R R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tiles = reinterpret_cast<T*>(smem_raw);  // [kStages][3][SY][kSX]
+  T* tiles = reinterpret_cast<T*>(smem_raw);  // [NST][3][SY][kSX]
   __shared__ R shr[WY];
   __shared__ T shm[WY];
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
@@ -382,14 +384,14 @@ __global__ void __launch_bounds__(32 * WY) energy_grad_strip_kernel(ModelDev md,
   T gmax = (T)0;
   bool bad = false;
   int t = blockIdx.x, x0, y0;
-  stage_prologue<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
+  stage_prologue<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    stage_next<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
+    stage_next<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
     __syncthreads();
     tile_origin(t, ntx, TY, x0, y0);
     SpinsOnSite<T, SW> os;
     VP ax[SW], ay[SW], az[SW];
-    walk<T, SW, DM::SY>(tiles + (size_t)(it % kStages) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
+    walk<T, SW, DM::SY>(tiles + (size_t)(it % NST) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
     const int x = x0 + 2 * lane;
     const bool two = x + 1 < L1;
     const bool pair_store = aligned && two;
@@ -474,8 +476,8 @@ __device__ __forceinline__ T solid_angle(T ax, T ay, T az, T bx, T by, T bz, T c
   return (T)2 * atan2(num, den);
 }
 
-template <typename T, int SW, int WY>
-__global__ void __launch_bounds__(32 * WY) topo_strip_kernel(ModelDev md, const T* __restrict__ m, double* part,
+template <typename T, int SW, int WY, int NST, int MINB>
+__global__ void __launch_bounds__(32 * WY, MINB) topo_strip_kernel(ModelDev md, const T* __restrict__ m, double* part,
                                                              unsigned* counter, double* out, int aligned, int ntx,
                                                              int ntiles, size_t ws) {
   m = wofs(m, ws);
@@ -495,12 +497,12 @@ __global__ void __launch_bounds__(32 * WY) topo_strip_kernel(ModelDev md, const 
   const size_t N = md.N;
   R acc = RD::of((T)0);
   int t = blockIdx.x, x0, y0;
-  stage_prologue<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
+  stage_prologue<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    stage_next<T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
+    stage_next<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
     __syncthreads();
     tile_origin(t, ntx, TY, x0, y0);
-    const T* tile = tiles + (size_t)(it % kStages) * DM::kTile;
+    const T* tile = tiles + (size_t)(it % NST) * DM::kTile;
     const int x = x0 + 2 * lane;
     T qt = (T)0;
     if (x < L1) {
@@ -590,20 +592,63 @@ bool al16(const void* p) {
   return p == nullptr || ((uintptr_t)p % 16) == 0;
 }
 
-template <typename T>
-void launch_energy_grad_strip(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
-                              double* out, int* status, cudaStream_t st) {
+// The persistent stencils' variants: (staged tiles, blocks an SM the
+// registers must allow).  The per-site arithmetic is the same in both; the
+// block partition, and so the order of the energy's sum, follows the grid.
+template <typename T, int NST, int MINB>
+void energy_strip_v(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
+                    int* status, cudaStream_t st) {
   constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
   const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
   const int ntiles = ntx * nty;
-  const size_t smem = kStages * strip::Dims<TY>::kTile * sizeof(T);
+  const size_t smem = NST * strip::Dims<TY>::kTile * sizeof(T);
   static int bps_cache = 0;
-  const int bps = strip_bps(energy_grad_strip_kernel<T, SW, WY>, 32 * WY, smem, bps_cache);
+  const int bps = strip_bps(energy_grad_strip_kernel<T, SW, WY, NST, MINB>, 32 * WY, smem, bps_cache);
   const int grid = std::min(ntiles, kSMs * bps);
   constexpr int kE = 16 / (int)sizeof(T);
   const int aligned = (md.L1 % kE == 0) && al16<T>(m) && al16<T>(g) && al16<T>(s);
-  energy_grad_strip_kernel<T, SW, WY><<<wgrid(grid), 32 * WY, smem, st>>>(
-      md, strip::make_weights<T>(md), (T)md.muB, m, g, s, part, counter, out, status, aligned, ntx, ntiles, walker_ws());
+  energy_grad_strip_kernel<T, SW, WY, NST, MINB><<<wgrid(grid), 32 * WY, smem, st>>>(
+      md, strip::make_weights<T>(md), (T)md.muB, m, g, s, part, counter, out, status, aligned, ntx, ntiles,
+      walker_ws());
+}
+
+template <typename T, int NST, int MINB>
+void topo_strip_v(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st) {
+  constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
+  const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  const size_t smem = NST * strip::Dims<TY>::kTile * sizeof(T);
+  static int bps_cache = 0;
+  const int bps = strip_bps(topo_strip_kernel<T, SW, WY, NST, MINB>, 32 * WY, smem, bps_cache);
+  const int grid = std::min(ntiles, kSMs * bps);
+  constexpr int kE = 16 / (int)sizeof(T);
+  const int aligned = (md.L1 % kE == 0) && al16<T>(m);
+  topo_strip_kernel<T, SW, WY, NST, MINB><<<wgrid(grid), 32 * WY, smem, st>>>(md, m, part, counter, out, aligned,
+                                                                             ntx, ntiles, walker_ws());
+}
+
+// Process-wide choices of the autotuner: (L1, L2, element size) -> variant.
+struct StencilChoice {
+  int L1, L2, esize, variant;
+};
+std::mutex g_stencil_mutex;
+std::vector<StencilChoice> g_stencil_choices;
+
+int stencil_choice(int L1, int L2, int esize) {
+  std::lock_guard<std::mutex> lock(g_stencil_mutex);
+  for (const StencilChoice& c : g_stencil_choices)
+    if (c.L1 == L1 && c.L2 == L2 && c.esize == esize) return c.variant;
+  return -1;
+}
+
+template <typename T>
+void launch_energy_grad_strip(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
+                              double* out, int* status, cudaStream_t st, int variant) {
+  if (variant < 0) variant = std::max(0, stencil_choice(md.L1, md.L2, (int)sizeof(T)));
+  if (variant == 1)
+    energy_strip_v<T, 2, 5>(md, m, g, s, part, counter, out, status, st);
+  else
+    energy_strip_v<T, 3, 1>(md, m, g, s, part, counter, out, status, st);
 }
 
 }  // namespace
@@ -616,7 +661,7 @@ void launch_energy_grad(const ModelDev& md, const T* m, T* g, T* s, double* part
     return;
   }
   if (!fp64_arith && !euclid) {
-    launch_energy_grad_strip<T>(md, m, g, s, part, counter, out, status, st);
+    launch_energy_grad_strip<T>(md, m, g, s, part, counter, out, status, st, -1);
     return;
   }
   const int e = euclid ? 1 : 0;
@@ -647,16 +692,28 @@ void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t l
 
 template <typename T>
 void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st) {
-  constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
-  const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
-  const int ntiles = ntx * nty;
-  const size_t smem = kStages * strip::Dims<TY>::kTile * sizeof(T);
-  static int bps_cache = 0;
-  const int bps = strip_bps(topo_strip_kernel<T, SW, WY>, 32 * WY, smem, bps_cache);
-  const int grid = std::min(ntiles, kSMs * bps);
-  constexpr int kE = 16 / (int)sizeof(T);
-  const int aligned = (md.L1 % kE == 0) && al16<T>(m);
-  topo_strip_kernel<T, SW, WY><<<wgrid(grid), 32 * WY, smem, st>>>(md, m, part, counter, out, aligned, ntx, ntiles, walker_ws());
+  if (stencil_choice(md.L1, md.L2, (int)sizeof(T)) == 1)
+    topo_strip_v<T, 2, 5>(md, m, part, counter, out, st);
+  else
+    topo_strip_v<T, 3, 1>(md, m, part, counter, out, st);
+}
+
+int stencil_variant_count() { return 2; }
+int stencil_tuned_variant(int L1, int L2, int esize) { return stencil_choice(L1, L2, esize); }
+void stencil_record_variant(int L1, int L2, int esize, int variant) {
+  std::lock_guard<std::mutex> lock(g_stencil_mutex);
+  for (StencilChoice& c : g_stencil_choices)
+    if (c.L1 == L1 && c.L2 == L2 && c.esize == esize) {
+      c.variant = variant;
+      return;
+    }
+  g_stencil_choices.push_back(StencilChoice{L1, L2, esize, variant});
+}
+
+template <typename T>
+void launch_energy_grad_variant(int variant, const ModelDev& md, const T* m, T* g, T* s, double* part,
+                                unsigned* counter, double* out, int* status, cudaStream_t st) {
+  launch_energy_grad_strip<T>(md, m, g, s, part, counter, out, status, st, variant);
 }
 
 #define INST(T)                                                                                               \
@@ -665,7 +722,9 @@ void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter
   template void launch_euclid_hvp<T>(const ModelDev&, const T*, size_t, T*, size_t, int, cudaStream_t);      \
   template void launch_hvp<T>(const ModelDev&, const T*, const T*, const T*, size_t, T*, size_t, int,        \
                               const int*, int, cudaStream_t);                                                 \
-  template void launch_topo<T>(const ModelDev&, const T*, double*, unsigned*, double*, cudaStream_t);
+  template void launch_topo<T>(const ModelDev&, const T*, double*, unsigned*, double*, cudaStream_t);        \
+  template void launch_energy_grad_variant<T>(int, const ModelDev&, const T*, T*, T*, double*, unsigned*,    \
+                                              double*, int*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

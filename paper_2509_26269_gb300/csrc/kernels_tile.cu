@@ -727,7 +727,9 @@ void tile_launch(const CUtensorMap& mx, const CUtensorMap& my, int nx, int ny, i
   // passes on small lattices) get fewer CTAs, large ones still one an SM.
   // The rule depends on the field size only, so a walker of a batch and the
   // same walker alone sum in the same order.
-  const size_t per_cta = std::max<size_t>(1, (262144 + tps * loaded - 1) / (tps * loaded));
+  // (FP64 fields: 32 KB, the FP64 arithmetic of a CTA being the slower part)
+  const size_t target = sizeof(T) == 4 ? 262144 : 32768;
+  const size_t per_cta = std::max<size_t>(1, (target + tps * loaded - 1) / (tps * loaded));
   const size_t need = (ngroups + per_cta - 1) / per_cta;
   if (want > need) want = need;
   const int grid = (int)(ngroups < want ? (ngroups > 0 ? ngroups : 1) : want);

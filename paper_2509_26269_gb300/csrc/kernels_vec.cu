@@ -245,20 +245,26 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const T* __restrict__
   }
 }
 
-// Blocks of a site-wise kernel: four sites a thread at least (a block's set-up
-// and, where there is one, its reduction are then amortised on small lattices,
-// e.g. the walkers of a batch), at most eight blocks an SM.
-static int stream_grid(size_t sites) {
-  size_t b = (sites + 4 * kThreads - 1) / (4 * kThreads);
+// Blocks of a site-wise kernel: in FP32 four sites a thread at least (a
+// block's set-up and, where there is one, its reduction are then amortised on
+// small lattices, e.g. the walkers of a batch); in FP64, whose arithmetic
+// GB300 runs at a small fraction of the FP32 rate, one site a thread; at
+// most eight blocks an SM.
+static int stream_grid(size_t sites, size_t per_thread) {
+  size_t b = (sites + per_thread * kThreads - 1) / (per_thread * kThreads);
   const size_t cap = (size_t)kSMs * 8;
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+template <typename T>
+static int stream_grid(size_t sites) {
+  return stream_grid(sites, sizeof(T) == 4 ? 4 : 1);
 }
 
 template <typename T>
 void launch_combine(const T* X, size_t ldx, int nx, const int* nx_dev, const double* C, int ny, const T* Y,
                     size_t ldy, double beta, double sigma, T* out, size_t ldo, const T* m, int N, const int* gate,
                     int mask, cudaStream_t st) {
-  const int g = stream_grid(N);
+  const int g = stream_grid<T>(N);
   if (ny <= 1)
     combine_kernel<T, 1><<<wgrid(g), kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,
                                                  N, gate, mask, walker_ws());
@@ -564,8 +570,10 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
   if (gram) {
     if (((uintptr_t)X % (2 * sizeof(T))) || (ldx % 2)) return false;
     const size_t n = 3 * (size_t)N;
-    // at least 64 KB of the fields a block (small fields: fewer blocks)
-    size_t g = (nx * n * sizeof(T) + 65535) / 65536;
+    // at least 64 KB of FP32 fields a block (small fields: fewer blocks);
+    // FP64 arithmetic is slow on GB300, so FP64 blocks take 8 KB
+    const size_t per_block = sizeof(T) == 4 ? 65536 : 8192;
+    size_t g = (nx * n * sizeof(T) + per_block - 1) / per_block;
     const size_t cap = (size_t)kSMs * 2;  // one wave at two blocks per SM
     if (g > cap) g = cap;
     if (g < 1) g = 1;
@@ -575,12 +583,12 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
                       (uintptr_t)Q % 8 == 0 && (!m || (uintptr_t)m % 8 == 0);
     if constexpr (sizeof(T) == 4) {
       if (pair) {
-        combine2_kernel<T, true><<<wgrid(stream_grid(N / 2)), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate,
+        combine2_kernel<T, true><<<wgrid(stream_grid<T>(N / 2)), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate,
                                                                           mask, walker_ws());
         return true;
       }
     }
-    combine2_kernel<T, false><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask, walker_ws());
+    combine2_kernel<T, false><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(X, ldx, nx, P1, P2, Q, ldq, m, N, gate, mask, walker_ws());
   }
   return true;
 }
@@ -613,7 +621,7 @@ __global__ void project_kernel(const T* __restrict__ m, const T* in, size_t ldi,
 template <typename T>
 void launch_project(const T* m, const T* in, size_t ldi, T* out, size_t ldo, int nvec, int N, const int* gate,
                     int mask, cudaStream_t st) {
-  project_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, in, ldi, out, ldo, nvec, N, gate, mask, walker_ws());
+  project_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(m, in, ldi, out, ldo, nvec, N, gate, mask, walker_ws());
 }
 
 // argmax with ties to the lowest index: (abs, idx) pairs
@@ -797,7 +805,7 @@ __global__ void __launch_bounds__(kThreads) finish2_kernel(const T* __restrict__
 template <typename T>
 void launch_finish(const T* m, T* V, size_t ldv, int k, int N, double* part, unsigned* counter, double* scal,
                    const int* gate, int mask, cudaStream_t st) {
-  const int g = stream_grid(N);
+  const int g = stream_grid<T>(N);
   // two blocks an SM for the reducing pass: fewer partials for its last block
   const int g1 = g < 2 * kSMs ? g : 2 * kSMs;
   finish1_kernel<T><<<wgrid(g1), kThreads, 0, st>>>(m, V, ldv, k, N, part, counter, scal, gate, mask, walker_ws());
@@ -1349,7 +1357,7 @@ __global__ void __launch_bounds__(kThreads) mmf_force_kernel(const T* __restrict
 template <typename T>
 void launch_mmf_force(const T* g, const T* V, size_t ldv, int nv, const double* dots, T* G, int N, double* part,
                       unsigned* counter, double* fmax_out, const int* gate, int mask, cudaStream_t st) {
-  mmf_force_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(g, nv > 0 ? V : nullptr, ldv, nv, dots, G, N, part,
+  mmf_force_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(g, nv > 0 ? V : nullptr, ldv, nv, dots, G, N, part,
                                                            counter, fmax_out, gate, mask, walker_ws());
 }
 
@@ -1440,7 +1448,7 @@ __global__ void __launch_bounds__(kThreads) cg_direction_kernel(const T* __restr
 template <typename T>
 void launch_cg_direction(const T* m, const T* G, T* p, int N, const double* cg, double theta_max, double* part,
                          unsigned* counter, DevState* dst, const int* gate, int mask, cudaStream_t st) {
-  cg_direction_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, G, p, N, cg, theta_max, part, counter, dst, gate,
+  cg_direction_kernel<T><<<stream_grid<T>(N), kThreads, 0, st>>>(m, G, p, N, cg, theta_max, part, counter, dst, gate,
                                                               mask);
 }
 
@@ -1490,7 +1498,7 @@ __global__ void lbfgs_pair_kernel(const T* __restrict__ m, const T* __restrict__
 template <typename T>
 void launch_lbfgs_pair(const T* m, const T* d_prev, const T* G_prev, const T* G, T* ring, size_t ld, T* stage,
                        const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
-  lbfgs_pair_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, d_prev, G_prev, G, ring, ld, stage, dst, N, gate,
+  lbfgs_pair_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(m, d_prev, G_prev, G, ring, ld, stage, dst, N, gate,
                                                             mask, walker_ws());
 }
 
@@ -1652,7 +1660,7 @@ template <typename T>
 void launch_lbfgs_direction(const T* basis, size_t ld, int nb, const double* coef, const T* m, T* d, int N,
                             double theta_max, double* part, unsigned* counter, DevState* dst, const int* gate,
                             int mask, cudaStream_t st) {
-  lbfgs_direction_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(basis, ld, nb, coef, m, d, N, theta_max, part,
+  lbfgs_direction_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(basis, ld, nb, coef, m, d, N, theta_max, part,
                                                                  counter, dst, gate, mask, walker_ws());
 }
 
@@ -1707,7 +1715,7 @@ __global__ void retract_kernel(T* m, T* d, const DevState* dst, int N, const int
 
 template <typename T>
 void launch_retract(T* m, T* d, const DevState* dst, int N, const int* gate, int mask, cudaStream_t st) {
-  retract_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, d, dst, N, gate, mask, walker_ws());
+  retract_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(m, d, dst, N, gate, mask, walker_ws());
 }
 
 template <typename T>
@@ -1740,7 +1748,7 @@ __global__ void cg_retract_kernel(T* m, const T* __restrict__ G, T* p, T* d, con
 template <typename T>
 void launch_cg_retract(T* m, const T* G, T* p, T* d, const DevState* dst, int N, const int* gate, int mask,
                        cudaStream_t st) {
-  cg_retract_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, G, p, d, dst, N, gate, mask);
+  cg_retract_kernel<T><<<stream_grid<T>(N), kThreads, 0, st>>>(m, G, p, d, dst, N, gate, mask);
 }
 
 // ---- damped spin dynamics (Landau-Lifshitz-Gilbert, Heun; see internal.h) ----
@@ -1805,14 +1813,14 @@ template <typename T>
 void launch_llg_predict(const T* m, const T* g, T* mp, double alpha, double dt, int N, const int* gate, int mask,
                         cudaStream_t st) {
   const double d = 1.0 + alpha * alpha;
-  llg_predict_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, g, mp, (T)(1.0 / d), (T)(alpha / d), (T)dt, N, gate,
+  llg_predict_kernel<T><<<stream_grid<T>(N), kThreads, 0, st>>>(m, g, mp, (T)(1.0 / d), (T)(alpha / d), (T)dt, N, gate,
                                                              mask);
 }
 template <typename T>
 void launch_llg_correct(T* m, const T* g0, const T* mp, const T* g1, double alpha, double dt, int N,
                         const int* gate, int mask, cudaStream_t st) {
   const double d = 1.0 + alpha * alpha;
-  llg_correct_kernel<T><<<stream_grid(N), kThreads, 0, st>>>(m, g0, mp, g1, (T)(1.0 / d), (T)(alpha / d),
+  llg_correct_kernel<T><<<stream_grid<T>(N), kThreads, 0, st>>>(m, g0, mp, g1, (T)(1.0 / d), (T)(alpha / d),
                                                              (T)(0.5 * dt), N, gate, mask);
 }
 
@@ -1862,8 +1870,8 @@ __global__ void seed_kernel(const T* m, const T* v1, const double* vmax, double 
 template <typename T>
 void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign, T* out, int N, double* part,
                          unsigned* counter, double* scal, cudaStream_t st) {
-  vmax_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(v1, N, part, counter, scal, walker_ws());
-  seed_kernel<T><<<wgrid(stream_grid(N)), kThreads, 0, st>>>(m, v1, scal, eta_theta, sign, out, N, walker_ws());
+  vmax_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(v1, N, part, counter, scal, walker_ws());
+  seed_kernel<T><<<wgrid(stream_grid<T>(N)), kThreads, 0, st>>>(m, v1, scal, eta_theta, sign, out, N, walker_ws());
 }
 
 // Saddle / minimum test and the per-step output vector.

@@ -49,3 +49,35 @@ def test_hvp_variants_are_bit_identical(dtype, L1, L2):
     with pytest.raises(mo.MotoError):
         mo.moto_set_hvp_variant(ctx.handle, len(ms))
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("L1,L2", [(128, 64), (37, 29), (6, 7)])
+def test_energy_stencil_variants(dtype, L1, L2):
+    """The energy / gradient stencil's variants (two or three staged tiles,
+    four or five blocks an SM) give bit-identical g and s and energies within
+    the rounding of a differently partitioned sum; each matches the oracle."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    M = Model(L1, L2, **FULL)
+    m = rand_spins(L1, L2, 7300 + L1)
+    ctx = context(M, dtype)
+    variant, ms = mo.moto_stencil_tuning(ctx.handle)
+    assert 0 <= variant < len(ms) == 2
+    md = to_dev(m, dtype)
+    res = []
+    for v in range(len(ms)):
+        mo.moto_set_stencil_variant(ctx.handle, v)
+        out, g, s = ctx.energy_grad(md)
+        res.append((to_np(out), to_np(g), to_np(s)))
+    mo.moto_set_stencil_variant(ctx.handle, -1)
+    for o, g, s in res[1:]:
+        np.testing.assert_array_equal(g, res[0][1])
+        np.testing.assert_array_equal(s, res[0][2])
+        assert o[0] == pytest.approx(res[0][0][0], rel=1e-13 if dtype == torch.float64 else 1e-6)
+        assert o[1] == res[0][0][1]
+    mo_ = to_np(md)
+    g_ref, _ = spin.riemann_grad(M, mo_)
+    err = np.linalg.norm(res[0][1] - g_ref) / np.linalg.norm(spin.euclid_grad(M, mo_))
+    assert err <= TOL[dtype]
+    ctx.close()
