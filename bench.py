@@ -45,11 +45,11 @@ HVP_PER_STEP = BLOCK * STEPS
 METRIC = "spin-HVP Gspin/s"
 UNIT = "Gspin-HVP/s"
 TILE_CLASSES = ("gram", "reorth_gram", "reorth_update")
-# DRAM bytes (read + write) per launch of the dominant kernel class, measured
-# with ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 1024 x 1024
-# case of the same step (profiles/), scaled by sites; None until measured for
-# the current kernels
-TRAFFIC_1024 = {}
+# DRAM bytes (read + write) per launch of the dominant kernel class, averaged
+# over the class's launches of one step: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of every launch of a 2048 x 2048 bench step
+# (profiles/traffic_tile2d_step_2048.md); reported at that lattice only
+TRAFFIC_2048 = {"tile2d": 579.87e6}
 WORKLOAD = ("roofline-2048x2048: 4,194,304 spins, 3 shells, FP32 fields, biskyrmion Q=2, k=8 block Lanczos (8x12), "
             "selective reorthogonalisation")
 
@@ -167,43 +167,65 @@ def oracle_sample(m, v_block, n_hvp):
     return time.perf_counter() - t0
 
 
-def _pool_worker(args):
-    """One process of the all-cores oracle leg: builds the workload's state
-    (untimed), then times n_hvp tangent HVPs; returns its compute interval on
-    the host's monotonic clock."""
-    seed, n_hvp, lat = args
-    global L
-    L = lat
+_POOL = {}
+
+
+def _pool_init(lat):
+    """Initializer of the all-cores oracle pool (runs once in each spawned
+    process, untimed): the workload's model, state and one tangent field."""
     from oracle import spin
     from oracle.model import model_from_workload
-    M = model_from_workload(dict(inputs.WORKLOADS[4], L1=L, L2=L))
-    m = inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, 0))
+    M = model_from_workload(dict(inputs.WORKLOADS[4], L1=lat, L2=lat))
+    m = inputs.add_noise(inputs.biskyrmion(lat, lat, 8.0), 0.01, inputs.workload_seed(4, 0))
     _, s = spin.riemann_grad(M, m)
-    v = spin.project(m, inputs.gaussian_field(seed, L, L))
+    _POOL.update(M=M, m=m, s=s, lat=lat)
+
+
+def _pool_worker(args):
+    """One task of the all-cores oracle leg: n_hvp tangent HVPs of a seeded
+    direction on the full lattice; returns its compute interval on the host's
+    monotonic clock."""
+    seed, n_hvp = args
+    from oracle import spin
+    M, m, s, lat = _POOL["M"], _POOL["m"], _POOL["s"], _POOL["lat"]
+    v = spin.project(m, inputs.gaussian_field(seed, lat, lat))
     t0 = time.perf_counter()
     for _ in range(n_hvp):
         spin.hvp(M, m, s, v)
     return t0, time.perf_counter()
 
 
+def pool_cores():
+    return min(os.cpu_count() or 1, 64)
+
+
+def oracle_pool(cores):
+    """A spawn-started process pool of the oracle, one process per core (spawn:
+    the CUDA context of this process must not be forked)."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(cores, initializer=_pool_init, initargs=(L,))
+
+
+def pool_step(pool, cores, step, n_hvp=2):
+    """One all-cores sample: every process times n_hvp HVPs; returns the wall
+    interval from the first start to the last end."""
+    res = pool.map(_pool_worker, [(5000 + 97 * step + k, n_hvp) for k in range(cores)])
+    return max(b for _, b in res) - min(a for a, _ in res)
+
+
 def cpu_baseline(m, n_hvp=8):
     """The FP64 oracle on the host: one core (energy + gradient and n_hvp HVPs
-    in this process), then every core (a spawn-started process pool, one
-    process per core, each timing 2 HVPs on the full lattice; the wall interval
-    from the first start to the last end)."""
+    in this process), then every core (one pool sample of 2 HVPs a process on
+    the full lattice)."""
     from oracle import spin
     v = [spin.project(m, x) for x in start_block(2, 4242)]
     t = oracle_sample(m, v, n_hvp)
     one = L * L * n_hvp / t / 1e9
-    cores = min(os.cpu_count() or 1, 64)
+    cores = pool_cores()
     allc = None
     try:
-        import multiprocessing as mp
-        ctx = mp.get_context("spawn")
-        with ctx.Pool(cores) as pool:
-            res = pool.map(_pool_worker, [(5000 + k, 2, L) for k in range(cores)])
-        wall = max(b for _, b in res) - min(a for a, _ in res)
-        allc = L * L * 2 * cores / wall / 1e9
+        with oracle_pool(cores) as pool:
+            allc = L * L * 2 * cores / pool_step(pool, cores, 0) / 1e9
     except Exception as e:  # the single-core figure still stands
         print(f"all-cores oracle leg skipped: {e}", file=sys.stderr)
     value = allc if allc is not None else one
@@ -214,23 +236,25 @@ def cpu_baseline(m, n_hvp=8):
 
 
 def run_reference(args, rank, world):
+    """The oracle as it stands on every host core: each step is one pool sample
+    (every process: 2 tangent HVPs on the full lattice); the pool and its
+    per-process state are built before the warm-up, untimed."""
     if rank != 0:
         return 0
-    m = inputs.workload4_state()
-    from oracle import spin
-    v = [spin.project(m, x) for x in start_block(2, 4242)]
+    cores = pool_cores()
     n_hvp = 2
-    for _ in range(args.warmup):
-        oracle_sample(m, v, n_hvp)
-    ts = [oracle_sample(m, v, n_hvp) for _ in range(args.steps)]
+    with oracle_pool(cores) as pool:
+        for w in range(max(args.warmup, 0)):
+            pool_step(pool, cores, 1000 + w, n_hvp)
+        ts = [pool_step(pool, cores, st, n_hvp) for st in range(args.steps)]
     t = sum(ts)
-    value = L * L * n_hvp * args.steps / t / 1e9
+    value = L * L * n_hvp * cores * args.steps / t / 1e9
+    sample = f"per step: {cores} spawned processes x {n_hvp} tangent HVPs on the full {L}x{L} lattice (FP64 numpy oracle)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config({"sample": "per step: energy+gradient and 2 HVPs (FP64 numpy oracle)"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: energy+gradient and 2 tangent HVPs on the full lattice"},
+            "config": config({"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -491,9 +515,9 @@ def run_ours(args, rank, world, local):
             "config": config({"parallelism": f"replicas x{world}" if world > 1 else "single"}),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": TRAFFIC_1024[dom] * (L / 1024) ** 2 if dom in TRAFFIC_1024 else None,
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at "
-                                           "1024x1024, scaled by sites",
+                         "traffic": TRAFFIC_2048[dom] if (dom in TRAFFIC_2048 and L == 2048) else None,
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, every launch of "
+                                           "one 2048x2048 step, per launch",
                          "peak_source": peak_kind,
                          "launches_in_step": n_l, "ms_in_step": dom_ms},
             "kernel_classes": {k: {"launches": v[0], "ms": v[1], "GBps": (v[2] / (v[1] * 1e-3) / 1e9 if v[1] else 0.0)}
