@@ -443,7 +443,8 @@ def run_ours(args, rank, world, local):
         m.copy_(m0)
         V.copy_(V0)
         mo.moto_lbfgs_reset(ctx.handle)
-        mo.moto_mmf_step(ctx.handle, m, pv, V, out, status)
+        for _ in range(2):  # the second call with these arguments captures the step's graph
+            mo.moto_mmf_step(ctx.handle, m, pv, V, out, status)
         torch.cuda.synchronize()
         nv_steps = 3
         e0.record()
@@ -541,6 +542,36 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+def run_probe(args):
+    """Profiling aid, no timing and no JSON line: launches one kernel family
+    of the step three times on the workload's state at the bench's lattice
+    (the autotuner off, the variant forced), for single-kernel captures
+    (`ncu -k <kernel> -s 1 -c 1`).  hvp: 8-vector tangent HVPs of the bench's
+    seeded start block; stencil: energy + gradient + s."""
+    os.environ["MOTO_AUTOTUNE"] = "0"
+    import torch
+    import paper_2509_26269_gb300 as mo
+    from paper_2509_26269_gb300 import Context
+    p = inputs.WORKLOADS[4]
+    ctx = Context(L, L, J=p["J"], D=p["D"], K=p["K"], muB=p["muB"], dtype=torch.float32,
+                  k=K_MODES, block=BLOCK, krylov_steps=STEPS)
+    m = torch.from_numpy(inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, 0))).to(
+        "cuda", torch.float32)
+    if args.probe == "hvp":
+        mo.moto_set_hvp_variant(ctx.handle, args.variant)
+        _, _, s = ctx.energy_grad(m)
+        V = torch.from_numpy(start_block(BLOCK, inputs.workload_seed(4, 0) + 17)).to("cuda", torch.float32)
+        for _ in range(3):
+            ctx.hvp(m, s, V)
+    else:
+        mo.moto_set_stencil_variant(ctx.handle, args.variant)
+        for _ in range(3):
+            ctx.energy_grad(m)
+    torch.cuda.synchronize()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,11 +585,16 @@ def main():
     ap.add_argument("--saddle-steps", type=int, default=3000, help="ascent step cap of the saddles/s leg")
     ap.add_argument("--lattice", type=int, default=2048,
                     help="lattice side; values other than 2048 are small cases for profiler captures")
+    ap.add_argument("--probe", choices=["hvp", "stencil"], default=None,
+                    help="profiling aid: launch one kernel family three times and exit (no timing)")
+    ap.add_argument("--variant", type=int, default=0, help="kernel variant forced by --probe")
     args = ap.parse_args()
     global L, WORKLOAD
     if args.lattice != L:
         L = args.lattice
         WORKLOAD = f"profiling case {L}x{L} (same path as the 2048x2048 workload)"
+    if args.probe:
+        return run_probe(args)
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)

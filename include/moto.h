@@ -290,7 +290,12 @@ int moto_lbfgs_reset(moto_ctx* ctx, void* stream);
  *   out_dev: out, 6 doubles [E, max|F_mmf,i|, lambda_1, lambda_2, max|g_i|, F.v1]
  *            at the m the step started from.
  *   status_dev: out, 1 int: 1 if the saddle test passed (m unchanged), else 0.
- * The L-BFGS history persists in the context between calls. */
+ * The L-BFGS history persists in the context between calls.  Called again
+ * with the same pointers and parameter values (block Lanczos solver, no
+ * launch profile recording), the step is captured once as a CUDA graph and
+ * later calls replay it on `stream`; the results are bit-identical to the
+ * kernel-by-kernel launches (MOTO_GRAPHS=0 in the environment).  Changing a
+ * variant, the wait limit or the pair list discards the captured step. */
 int moto_mmf_step(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V_dev,
                   double* out_dev, int* status_dev, void* stream);
 
@@ -298,7 +303,13 @@ int moto_mmf_step(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V
  * were taken, reading the status word back every `check_every` steps
  * (synchronises the stream).  trace_dev (optional, 6 doubles per step,
  * max_steps+1 rows) receives each step's out vector.  *steps_out: steps
- * taken.  Returns MOTO_OK at a saddle, MOTO_NOT_CONVERGED at the cap. */
+ * taken.  Returns MOTO_OK at a saddle, MOTO_NOT_CONVERGED at the cap.
+ * With the block Lanczos solver (and no launch profile recording) the first
+ * step runs launch by launch and the update step is then captured once as a
+ * CUDA graph on a private stream, joined back to `stream`, and replayed; the
+ * trace row of each replay is picked on the device from the steps taken.
+ * moto_descend does the same for its steps.  Results are bit-identical to
+ * launching every kernel (MOTO_GRAPHS=0 in the environment). */
 int moto_ascend(moto_ctx* ctx, void* m_dev, const moto_params* params, void* V_dev,
                 double* trace_dev, int check_every, int* steps_out, void* stream);
 
@@ -377,8 +388,9 @@ int moto_krylov_basis(moto_ctx* ctx, const void** basis_dev, size_t* ld, int* nv
                       void* stream);
 
 /* HVP autotuner.  The strip HVP kernel exists in several variants (strip
- * length, warps per block, spins held in registers) that give bit-identical
- * results and differ only in speed.  moto_create times each variant once on
+ * length, warps per block, spins held in registers, FP32 pair arithmetic as
+ * packed f32x2 or scalar instructions) that give bit-identical results and
+ * differ only in speed.  moto_create times each variant once on
  * its own scratch (vectors per call: params.block for block Lanczos,
  * params.k for LOBPCG) and records the fastest for (L1, L2, precision,
  * vectors) process-wide; later contexts of the same lattice reuse the record.
@@ -392,7 +404,8 @@ int moto_krylov_basis(moto_ctx* ctx, const void** basis_dev, size_t* ld, int* nv
 int moto_hvp_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
 int moto_set_hvp_variant(moto_ctx* ctx, int variant);
 /* The same for the energy / gradient stencil of moto_energy_grad and the
- * solvers (variants: staged tiles and blocks an SM; g and s are bit-identical
+ * solvers (variants: staged tiles and blocks an SM, FP32 pair arithmetic
+ * packed or scalar; g and s are bit-identical
  * across them, the energy's sum follows each variant's grid), timed by
  * moto_create and recorded for (L1, L2, precision).  moto_topo_charge uses
  * the recorded variant's layout.  The pair-list model and the FP64-arithmetic

@@ -301,8 +301,8 @@ def moto_stencil_tuning(ctx):
     """(energy-stencil variant in use, [ms per launch of each variant, zeros
     unless this context ran the autotuner])."""
     v = ctypes.c_int()
-    ms = (ctypes.c_float * 4)()
-    n = _lib.moto_stencil_tuning(ctx, ctypes.byref(v), ms, 4)
+    ms = (ctypes.c_float * 8)()
+    n = _lib.moto_stencil_tuning(ctx, ctypes.byref(v), ms, 8)
     if n < 0:
         raise MotoError(f"moto_stencil_tuning: {moto_status_string(n)}")
     return v.value, [float(ms[i]) for i in range(n)]

@@ -67,7 +67,7 @@ struct moto_ctx {
   int hvp_tuned_here;
   // energy / gradient stencil variant: forced (>= 0) or the autotuner's
   int stencil_force;
-  float stencil_ms[4];
+  float stencil_ms[8];
   int stencil_tuned_here;
   int last_selective;  // the last block Lanczos solve reorthogonalised selectively
   // walker group (batches): nw walkers whose scratch and fields lie in
@@ -78,6 +78,19 @@ struct moto_ctx {
   size_t wstride;
   void* arena;
   void *mslot, *Vslot, *mpslot, *mmslot;
+  // moto_mmf_step replayed as a CUDA graph when the same arguments come back:
+  // the key of the last call, how many calls in a row had it, the captured
+  // step (on a private stream), and a generation that every setter of a
+  // captured launch parameter bumps
+  int gen;
+  int step_seen;
+  int step_gen;
+  void *step_m, *step_V;
+  double* step_out;
+  int* step_status;
+  moto_params step_p;
+  cudaStream_t step_stream;
+  cudaGraphExec_t step_exec;
 };
 
 namespace {
@@ -717,7 +730,7 @@ int autotune_stencil(moto_ctx* c) {
   CK(cudaEventCreate(&e1));
   int best = 0;
   float best_ms = 0.f;
-  for (int v = 0; v < stencil_variant_count() && v < 4; ++v) {
+  for (int v = 0; v < stencil_variant_count() && v < 8; ++v) {
     launch_energy_grad_variant<T>(v, c->md, m, g, s, c->part, c->counter, out, &c->st->status, 0);
     cudaEventRecord(e0, 0);
     for (int r = 0; r < 3; ++r)
@@ -928,6 +941,8 @@ int moto_create(const moto_model* model, int dtype, const moto_params* params, m
 void moto_destroy(moto_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_stream) cudaStreamDestroy(c->step_stream);
   if (c->arena) {
     cudaFree(c->arena);
   } else {
@@ -941,6 +956,7 @@ void moto_destroy(moto_ctx* c) {
 int moto_set_hvp_variant(moto_ctx* c, int variant) {
   if (!c || variant < -1 || variant >= hvp_variant_count()) return MOTO_ERR_ARG;
   c->hvp_force = variant;
+  c->gen += 1;
   return MOTO_OK;
 }
 
@@ -959,6 +975,7 @@ int moto_hvp_tuning(const moto_ctx* c, int* variant, float* ms, int cap) {
 int moto_set_stencil_variant(moto_ctx* c, int variant) {
   if (!c || variant < -1 || variant >= stencil_variant_count()) return MOTO_ERR_ARG;
   c->stencil_force = variant;
+  c->gen += 1;
   return MOTO_OK;
 }
 
@@ -990,11 +1007,13 @@ int moto_krylov_basis(moto_ctx* c, const void** basis_dev, size_t* ld, int* nvec
 int moto_set_wait_limit(moto_ctx* c, int polls) {
   if (!c || polls < 0) return MOTO_ERR_ARG;
   c->wait_polls = polls;
+  c->gen += 1;
   return MOTO_OK;
 }
 
 int moto_set_pairs(moto_ctx* c, const moto_pair* pairs, int n) {
   if (!c || n < 0 || n > MOTO_MAX_PAIRS || (n > 0 && !pairs)) return MOTO_ERR_ARG;
+  c->gen += 1;
   int reach = 0;
   std::vector<double> rec((size_t)n * 6);
   for (int p = 0; p < n; ++p) {
@@ -1160,9 +1179,11 @@ void lowest_modes_impl(moto_ctx* c, const T* m, const T* s, const moto_params* p
 
 // One outer step.  ascent: reflected force and min-mode solve; otherwise plain
 // descent on g.  update == false evaluates the stopping test only.
+// trace_rows > 0: out6 is a trace of that many rows, the step's record goes
+// to the row of the steps taken so far (read on the device).
 template <typename T>
 void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* status, bool ascent, bool update,
-              cudaStream_t st) {
+              cudaStream_t st, int trace_rows = 0) {
   const int N = c->N;
   const size_t ld = c->ld, n3 = c->n3;
   T* g = static_cast<T*>(c->g);
@@ -1191,7 +1212,7 @@ void opt_step(moto_ctx* c, T* m, const moto_params* p, T* V, double* out6, int* 
     P_mmf_force<T>(c, g, nullptr, n3, 0, D + kMmfDots, Gcur, N, c->part, c->counter, D + kFmax, gate, md, st);
   }
   P_saddle_test(c, D + kEG, D + kFmax, lam, D + kMmfDots, p->tau_F, p->tau_lambda, out6, status, c->st,
-                ascent ? 1 : 0, update ? 0 : 1, st);
+                ascent ? 1 : 0, update ? 0 : 1, trace_rows, st);
   if (!update) return;
   if (p->optimizer == MOTO_OPT_CG) {
     // nonlinear CG: the pair s = P d_prev, y = G - P G_prev (staging fields),
@@ -1229,6 +1250,33 @@ int status_code(const DevState& h) {
   return MOTO_OK;
 }
 
+bool same_params(const moto_params& a, const moto_params& b) {
+  return a.k == b.k && a.solver == b.solver && a.block == b.block && a.krylov_steps == b.krylov_steps &&
+         a.max_iter == b.max_iter && a.tol == b.tol && a.lbfgs_mem == b.lbfgs_mem && a.theta_max == b.theta_max &&
+         a.gamma0 == b.gamma0 && a.tau_F == b.tau_F && a.eta_theta == b.eta_theta && a.max_steps == b.max_steps &&
+         a.descent_max_steps == b.descent_max_steps && a.optimizer == b.optimizer && a.subspace == b.subspace &&
+         a.descent == b.descent && a.llg_alpha == b.llg_alpha && a.llg_dt == b.llg_dt && a.llg_time == b.llg_time &&
+         a.reorth == b.reorth && a.tau_lambda == b.tau_lambda;
+}
+
+// Whether the outer step can be replayed as a captured CUDA graph: every
+// decision of a descent step and of a block Lanczos ascent step is taken on
+// the device (gate bits), while LOBPCG leaves its iteration early from the
+// host and the launch profiler records events around each launch.
+// MOTO_GRAPHS=0 in the environment launches every step's kernels one by one
+// instead.
+bool step_graphable(const moto_ctx* c, const moto_params* p, bool ascent) {
+  if ((ascent && p->solver != MOTO_SOLVER_LANCZOS) || c->prof_ev) return false;
+  const char* env = getenv("MOTO_GRAPHS");
+  return !(env && strcmp(env, "0") == 0);
+}
+
+// The outer loop of one walker: steps 0 .. max_steps - 1 update, the last
+// evaluates the stopping test only; the host reads the state word every
+// check_every steps.  Step 0 runs uncaptured (it also sets the kernels'
+// one-time attributes); when the step is graphable, the update step is then
+// captured once on a private stream and replayed, the records going to the
+// trace row of the device's step count.
 template <typename T>
 int run_opt(moto_ctx* c, T* m, const moto_params* p, T* V, double* trace, int check_every, int max_steps,
             bool ascent, int* steps_out, cudaStream_t st) {
@@ -1236,17 +1284,62 @@ int run_opt(moto_ctx* c, T* m, const moto_params* p, T* V, double* trace, int ch
   state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 1, walker_ws());
   DevState h;
   memset(&h, 0, sizeof(h));
+  double* o = trace ? trace : c->dsm + kTmp;
+  const int rows = trace ? max_steps + 1 : 0;
+  cudaStream_t run = st;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (max_steps > 1 && step_graphable(c, p, ascent) && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, st) == cudaSuccess &&
+        cudaStreamWaitEvent(cs, ev, 0) == cudaSuccess)
+      run = cs;
+  }
+  int rc = MOTO_OK;
   for (int t = 0; t <= max_steps; ++t) {
-    double* o = trace ? trace + 6 * (size_t)t : c->dsm + kTmp;
-    opt_step<T>(c, m, p, V, o, nullptr, ascent, t < max_steps, st);
-    const cudaError_t le = cudaGetLastError();
-    if (le != cudaSuccess) return cuda_fail(le, "a launch of the outer step", __LINE__);
+    const bool update = t < max_steps;
+    if (update && t == 1 && run == cs) {
+      // capture failures fall back to plain launches
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        opt_step<T>(c, m, p, V, o, nullptr, ascent, true, cs, rows);
+        const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        if (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          graph = nullptr;
+          exec = nullptr;
+        }
+      }
+      cudaGetLastError();
+    }
+    if (update && exec) {
+      const cudaError_t le = cudaGraphLaunch(exec, cs);
+      if (le != cudaSuccess) {
+        rc = cuda_fail(le, "cudaGraphLaunch", __LINE__);
+        break;
+      }
+    } else {
+      opt_step<T>(c, m, p, V, o, nullptr, ascent, update, run, rows);
+      const cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) {
+        rc = cuda_fail(le, "a launch of the outer step", __LINE__);
+        break;
+      }
+    }
     if ((t + 1) % check_every == 0 || t == max_steps) {
-      int rc = read_state(c, &h, st);
-      if (rc) return rc;
+      rc = read_state(c, &h, run);
+      if (rc) break;
       if (h.converged || status_code(h)) break;
     }
   }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) {
+    if (ev && cudaEventRecord(ev, cs) == cudaSuccess) cudaStreamWaitEvent(st, ev, 0);
+    cudaStreamDestroy(cs);
+  }
+  if (ev) cudaEventDestroy(ev);
+  if (rc) return rc;
   if (steps_out) *steps_out = h.pad[1];
   int sc = status_code(h);
   if (sc) return sc;
@@ -1274,7 +1367,7 @@ int run_llg(moto_ctx* c, T* m, const moto_params* p, int check_every, int* steps
   for (long t = 0; t <= nmax; ++t) {
     P_energy_grad<T>(c, c->md, m, g0, nullptr, c->part, c->counter, D + kEG, &c->st->status, false, st);
     P_saddle_test(c, D + kEG, D + kFmax, D + kTheta, D + kMmfDots, p->tau_F, p->tau_lambda, D + kTmp, nullptr,
-                  c->st, 0, t == nmax ? 1 : 0, st);
+                  c->st, 0, t == nmax ? 1 : 0, 0, st);
     if (t < nmax) {
       P_llg_predict<T>(c, m, g0, mp, p->llg_alpha, p->llg_dt, N, gate, kGateDone, st);
       P_energy_grad<T>(c, c->md, mp, g1, nullptr, c->part, c->counter, D + kTmp + 2, &c->st->status, false, st);
@@ -1339,10 +1432,47 @@ int moto_mmf_step(moto_ctx* c, void* m, const moto_params* p, void* V, double* o
   int rc = check_params(p);
   if (rc) return rc;
   if (p->lbfgs_mem != c->p.lbfgs_mem) return MOTO_ERR_ARG;
+  cudaStream_t st = S(stream);
+  // the same arguments as the last call: the second such call captures the
+  // step once, later ones replay it (the step's decisions are all taken on
+  // the device); anything else launches the step kernel by kernel
+  const bool same = c->step_seen > 0 && c->step_m == m && c->step_V == V && c->step_out == out &&
+                    c->step_status == status && c->step_gen == c->gen && same_params(c->step_p, *p);
+  if (!same) {
+    if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+    c->step_seen = 0;
+    c->step_m = m;
+    c->step_V = V;
+    c->step_out = out;
+    c->step_status = status;
+    c->step_p = *p;
+    c->step_gen = c->gen;
+  }
+  c->step_seen += 1;
+  if (c->step_seen >= 2 && !c->step_exec && step_graphable(c, p, true)) {
+    if (!c->step_stream) cudaStreamCreateWithFlags(&c->step_stream, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (c->step_stream && cudaStreamBeginCapture(c->step_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      if (c->dtype == MOTO_F32)
+        opt_step<float>(c, (float*)m, p, (float*)V, out, status, true, true, c->step_stream);
+      else
+        opt_step<double>(c, (double*)m, p, (double*)V, out, status, true, true, c->step_stream);
+      if (cudaStreamEndCapture(c->step_stream, &graph) != cudaSuccess ||
+          cudaGraphInstantiate(&c->step_exec, graph, 0) != cudaSuccess)
+        c->step_exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();  // a failed capture falls back to plain launches
+  }
+  if (c->step_exec && !c->prof_ev) {
+    CK(cudaGraphLaunch(c->step_exec, st));
+    return MOTO_OK;
+  }
   if (c->dtype == MOTO_F32)
-    opt_step<float>(c, (float*)m, p, (float*)V, out, status, true, true, S(stream));
+    opt_step<float>(c, (float*)m, p, (float*)V, out, status, true, true, st);
   else
-    opt_step<double>(c, (double*)m, p, (double*)V, out, status, true, true, S(stream));
+    opt_step<double>(c, (double*)m, p, (double*)V, out, status, true, true, st);
   CK(cudaGetLastError());
   return MOTO_OK;
 }

@@ -254,8 +254,10 @@ template <typename T>
 void launch_llg_correct(T* m, const T* g0, const T* mp, const T* g1, double alpha, double dt, int N,
                         const int* gate, int mask, cudaStream_t st);
 
+// indexed > 0: out6 is a trace of `indexed` rows, the record goes to row
+// min(outer steps taken, indexed - 1); 0: out6 is the record itself
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
                         double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst, int ascent,
-                        int last, cudaStream_t st);
+                        int last, int indexed, cudaStream_t st);
 
 }  // namespace moto

@@ -27,14 +27,13 @@ namespace {
 
 // on-site hook of the HVP walk: (hx, hy, hz) += -s v - 2 K v_z z at the
 // site's own row
-template <typename T, int SW>
+template <typename T, int SW, class P>
 struct HvpOnSite {
   typename PK<T>::V nsi[SW];  // -s_i of the strip's site pairs
   typename PK<T>::V twoK;
   template <int S>
   __device__ __forceinline__ void center(const RowP<T>& r, typename PK<T>::V& hx, typename PK<T>::V& hy,
                                          typename PK<T>::V& hz) {
-    typedef PK<T> P;
     hx = P::fma(nsi[S], r.x[2], hx);
     hy = P::fma(nsi[S], r.y[2], hy);
     hz = P::fma(P::sub(nsi[S], twoK), r.z[2], hz);
@@ -45,10 +44,12 @@ struct HvpOnSite {
 
 // m and s of the block's sites are staged once; with MREG the thread moves
 // its sites' m into registers for all vectors, otherwise it re-reads them from
-// shared memory per vector.  `aligned`: L1 and the field strides are
-// multiples of 16 bytes / sizeof(T) and the fields start on 16-byte
-// boundaries (interior blocks then stage with 16-byte copies).
-template <typename T, int SW, int WY, bool MREG>
+// shared memory per vector.  AR: FP32 pair arithmetic as packed f32x2
+// instructions (1) or scalar pairs (0) (PA; the same sums bit for bit).
+// `aligned`: L1 and the field strides are multiples of 16 bytes / sizeof(T)
+// and the fields start on 16-byte boundaries (interior blocks then stage
+// with 16-byte copies).
+template <typename T, int SW, int WY, bool MREG, int AR>
 __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights<T> hw, const T* __restrict__ m,
                                                             const T* __restrict__ s, const T* __restrict__ V,
                                                             size_t ldv, T* __restrict__ HV, size_t ldhv, int nvec,
@@ -61,8 +62,8 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
   if (gate && (*gate & mask)) return;
   constexpr int TY = SW * WY;
   typedef Dims<TY> DM;
-  typedef PK<T> P;
-  typedef typename P::V VP;
+  typedef typename PA<T, AR>::P P;
+  typedef typename PK<T>::V VP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][SY][kSX]
   T* ms = tiles + 2 * DM::kTile;               // [4][TY][kTX]: m_x, m_y, m_z, s
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
   stage_tile<T, DM::SY>(tiles, V, N, L1, L2, x0, y0, vec16);
   const int x = x0 + 2 * lane;  // the thread's columns x, x + 1
   const bool pair_store = aligned && x + 1 < L1;
-  HvpOnSite<T, SW> os;
+  HvpOnSite<T, SW, P> os;
   os.twoK = P::bc(hw.twoK);
   VP mr[MREG ? SW : 1][3];
   for (int j = 0; j < nvec; ++j) {
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
       }
     }
     VP ax[SW], ay[SW], az[SW];
-    walk<T, SW, DM::SY>(tile, wy * SW, lane, ax, ay, az, w, os);
+    walk<T, SW, DM::SY, P>(tile, wy * SW, lane, ax, ay, az, w, os);
     if (x < L1) {
 #pragma unroll
       for (int k = 0; k < SW; ++k) {
@@ -172,23 +173,25 @@ namespace {
 
 // The variants the launcher chooses from (all give bit-identical results).
 struct HvpVariant {
-  int sw, wy, mreg;
+  int sw, wy, mreg, ar;
 };
-constexpr HvpVariant kHvpVariants[] = {{4, 4, 1}, {4, 4, 0}, {8, 2, 0}, {2, 8, 1}, {8, 4, 0}};
+constexpr HvpVariant kHvpVariants[] = {{4, 4, 1, 0}, {4, 4, 0, 0}, {8, 2, 0, 0}, {2, 8, 1, 0},
+                                       {2, 8, 1, 1}, {4, 4, 1, 1}, {4, 4, 0, 1}, {8, 2, 0, 1}};
 constexpr int kNumHvpVariants = sizeof(kHvpVariants) / sizeof(kHvpVariants[0]);
 
-template <typename T, int SW, int WY, bool MREG>
+template <typename T, int SW, int WY, bool MREG, int AR0>
 void hvp_launch_v(const ModelDev& md, const Weights<T>& hw, const T* m, const T* s, const T* V, size_t ldv, T* HV,
                   size_t ldhv, int nvec, int aligned, const int* gate, int mask, cudaStream_t st) {
+  constexpr int AR = sizeof(T) == 4 ? AR0 : 1;  // FP64 pairs are scalar in every form
   constexpr int TY = SW * WY;
   const dim3 grid((md.L1 + kTX - 1) / kTX, (md.L2 + TY - 1) / TY);
   const size_t smem = (2 * Dims<TY>::kTile + 4 * (size_t)TY * kTX) * sizeof(T);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(hvp_strip_kernel<T, SW, WY, MREG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(hvp_strip_kernel<T, SW, WY, MREG, AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  hvp_strip_kernel<T, SW, WY, MREG><<<wgrid(grid), 32 * WY, smem, st>>>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate,
+  hvp_strip_kernel<T, SW, WY, MREG, AR><<<wgrid(grid), 32 * WY, smem, st>>>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate,
                                                                  mask, walker_ws());
 }
 
@@ -196,11 +199,14 @@ template <typename T>
 void hvp_launch_index(int v, const ModelDev& md, const Weights<T>& hw, const T* m, const T* s, const T* V, size_t ldv,
                       T* HV, size_t ldhv, int nvec, int aligned, const int* gate, int mask, cudaStream_t st) {
   switch (v) {
-    case 1: hvp_launch_v<T, 4, 4, false>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
-    case 2: hvp_launch_v<T, 8, 2, false>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
-    case 3: hvp_launch_v<T, 2, 8, true>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
-    case 4: hvp_launch_v<T, 8, 4, false>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
-    default: hvp_launch_v<T, 4, 4, true>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 1: hvp_launch_v<T, 4, 4, false, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 2: hvp_launch_v<T, 8, 2, false, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 3: hvp_launch_v<T, 2, 8, true, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 4: hvp_launch_v<T, 2, 8, true, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 5: hvp_launch_v<T, 4, 4, true, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 6: hvp_launch_v<T, 4, 4, false, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    case 7: hvp_launch_v<T, 8, 2, false, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
+    default: hvp_launch_v<T, 4, 4, true, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
   }
 }
 

@@ -351,7 +351,7 @@ __device__ __forceinline__ void last_block_totals(const typename strip::Red<T>::
 // g_i = grad_i E - s_i m_i; E = sum_i (s_i - muB m_iz) / 2 (E is quadratic in
 // m).  out = [E, max_i |g_i|].  Partials: part[0 .. grid) the block energies
 // (8-byte reduction values), part[grid .. 2 grid) the block maxima of |g|^2.
-template <typename T, int SW, int WY, int NST, int MINB>
+template <typename T, int SW, int WY, int NST, int MINB, int AR>
 __global__ void __launch_bounds__(32 * WY, MINB) energy_grad_strip_kernel(ModelDev md, strip::Weights<T> hw, T muB,
                                                                     const T* __restrict__ m, T* __restrict__ g,
                                                                     T* __restrict__ s, double* part, unsigned* counter,
@@ -367,8 +367,8 @@ __global__ void __launch_bounds__(32 * WY, MINB) energy_grad_strip_kernel(ModelD
   using namespace strip;
   constexpr int TY = SW * WY;
   typedef Dims<TY> DM;
-  typedef PK<T> P;
-  typedef typename P::V VP;
+  typedef typename PA<T, AR>::P P;
+  typedef typename PK<T>::V VP;
   typedef Red<T> RD;
   typedef typename RD::R R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(32 * WY, MINB) energy_grad_strip_kernel(ModelD
     tile_origin(t, ntx, TY, x0, y0);
     SpinsOnSite<T, SW> os;
     VP ax[SW], ay[SW], az[SW];
-    walk<T, SW, DM::SY>(tiles + (size_t)(it % NST) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
+    walk<T, SW, DM::SY, P>(tiles + (size_t)(it % NST) * DM::kTile, wy * SW, lane, ax, ay, az, w, os);
     const int x = x0 + 2 * lane;
     const bool two = x + 1 < L1;
     const bool pair_store = aligned && two;
@@ -593,21 +593,23 @@ bool al16(const void* p) {
 }
 
 // The persistent stencils' variants: (staged tiles, blocks an SM the
-// registers must allow).  The per-site arithmetic is the same in both; the
-// block partition, and so the order of the energy's sum, follows the grid.
-template <typename T, int NST, int MINB>
+// registers must allow, FP32 pair arithmetic: PA).  The per-site arithmetic
+// is the same in all; the block partition, and so the order of the energy's
+// sum, follows the grid.
+template <typename T, int NST, int MINB, int AR0>
 void energy_strip_v(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter, double* out,
                     int* status, cudaStream_t st) {
+  constexpr int AR = sizeof(T) == 4 ? AR0 : 1;  // FP64 pairs are scalar in every form
   constexpr int SW = kStripSW, WY = kStripWY, TY = SW * WY;
   const int ntx = (md.L1 + strip::kTX - 1) / strip::kTX, nty = (md.L2 + TY - 1) / TY;
   const int ntiles = ntx * nty;
   const size_t smem = NST * strip::Dims<TY>::kTile * sizeof(T);
   static int bps_cache = 0;
-  const int bps = strip_bps(energy_grad_strip_kernel<T, SW, WY, NST, MINB>, 32 * WY, smem, bps_cache);
+  const int bps = strip_bps(energy_grad_strip_kernel<T, SW, WY, NST, MINB, AR>, 32 * WY, smem, bps_cache);
   const int grid = std::min(ntiles, kSMs * bps);
   constexpr int kE = 16 / (int)sizeof(T);
   const int aligned = (md.L1 % kE == 0) && al16<T>(m) && al16<T>(g) && al16<T>(s);
-  energy_grad_strip_kernel<T, SW, WY, NST, MINB><<<wgrid(grid), 32 * WY, smem, st>>>(
+  energy_grad_strip_kernel<T, SW, WY, NST, MINB, AR><<<wgrid(grid), 32 * WY, smem, st>>>(
       md, strip::make_weights<T>(md), (T)md.muB, m, g, s, part, counter, out, status, aligned, ntx, ntiles,
       walker_ws());
 }
@@ -645,10 +647,12 @@ template <typename T>
 void launch_energy_grad_strip(const ModelDev& md, const T* m, T* g, T* s, double* part, unsigned* counter,
                               double* out, int* status, cudaStream_t st, int variant) {
   if (variant < 0) variant = std::max(0, stencil_choice(md.L1, md.L2, (int)sizeof(T)));
-  if (variant == 1)
-    energy_strip_v<T, 2, 5>(md, m, g, s, part, counter, out, status, st);
-  else
-    energy_strip_v<T, 3, 1>(md, m, g, s, part, counter, out, status, st);
+  switch (variant) {
+    case 1: energy_strip_v<T, 2, 5, 0>(md, m, g, s, part, counter, out, status, st); break;
+    case 2: energy_strip_v<T, 3, 1, 1>(md, m, g, s, part, counter, out, status, st); break;
+    case 3: energy_strip_v<T, 2, 5, 1>(md, m, g, s, part, counter, out, status, st); break;
+    default: energy_strip_v<T, 3, 1, 0>(md, m, g, s, part, counter, out, status, st); break;
+  }
 }
 
 }  // namespace
@@ -692,13 +696,15 @@ void launch_hvp(const ModelDev& md, const T* m, const T* s, const T* V, size_t l
 
 template <typename T>
 void launch_topo(const ModelDev& md, const T* m, double* part, unsigned* counter, double* out, cudaStream_t st) {
-  if (stencil_choice(md.L1, md.L2, (int)sizeof(T)) == 1)
+  // the charge has no pair walk: variants 1 and 3 share its two-tile layout
+  const int v = stencil_choice(md.L1, md.L2, (int)sizeof(T));
+  if (v == 1 || v == 3)
     topo_strip_v<T, 2, 5>(md, m, part, counter, out, st);
   else
     topo_strip_v<T, 3, 1>(md, m, part, counter, out, st);
 }
 
-int stencil_variant_count() { return 2; }
+int stencil_variant_count() { return 4; }
 int stencil_tuned_variant(int L1, int L2, int esize) { return stencil_choice(L1, L2, esize); }
 void stencil_record_variant(int L1, int L2, int esize, int variant) {
   std::lock_guard<std::mutex> lock(g_stencil_mutex);

@@ -1876,9 +1876,12 @@ void launch_descent_seed(const T* m, const T* v1, double eta_theta, double sign,
 
 // Saddle / minimum test and the per-step output vector.
 // last: the final test of a run (no step follows it, so none is counted)
+// indexed: out6 is the first row of a trace; the record goes to the row of
+// the outer steps taken so far (dst->pad[1], at most rows - 1), so a captured
+// step writes each replay's record to its own row.
 __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
                                    double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst,
-                                   int ascent, int last, size_t ws) {
+                                   int ascent, int last, int indexed, size_t ws) {
   eg_out = wofs(eg_out, ws);
   fmax = wofs(fmax, ws);
   lam = wofs(lam, ws);
@@ -1892,6 +1895,7 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
     return;
   }
   const double E = eg_out[0], gmax = eg_out[1];
+  if (out6 && indexed > 0) out6 += 6 * (size_t)min(max(dst->pad[1], 0), indexed - 1);
   bool conv;
   if (ascent) {
     // lambda_1 < 0 < lambda_2 with the curvature threshold tau_lambda:
@@ -1924,9 +1928,9 @@ __global__ void saddle_test_kernel(const double* eg_out, const double* fmax, con
 
 void launch_saddle_test(const double* eg_out, const double* fmax, const double* lam, const double* gdot,
                         double tau_F, double tau_lambda, double* out6, int* status_out, DevState* dst, int ascent,
-                        int last, cudaStream_t st) {
+                        int last, int indexed, cudaStream_t st) {
   saddle_test_kernel<<<wgrid(1), 32, 0, st>>>(eg_out, fmax, lam, gdot, tau_F, tau_lambda, out6, status_out, dst, ascent,
-                                       last, walker_ws());
+                                       last, indexed, walker_ws());
 }
 
 #define INST(T)                                                                                                   \

@@ -14,8 +14,9 @@
 // staged rows the strip needs, reading each row once as three aligned column
 // pairs per component and forming the two odd pairs, and adds the row into
 // the accumulators of the (up to five) strip sites it is a neighbour of.  In
-// FP32 every add and FMA of the walk is one packed f32x2 instruction for two
-// sites; FP64 takes the same path with scalar pairs.  The row of a site
+// FP32 every add and FMA of the walk is either one packed f32x2 instruction
+// for two sites or two scalar ones with the same per-lane rounding (PA; the
+// launchers time both); FP64 takes the same path with scalar pairs.  The row of a site
 // itself is handed to an on-site hook (the -s v and -2K v_z terms of the HVP,
 // the spins of the energy kernel) before its own stencil terms, so every
 // site's sum runs in the same order whatever the strip length or the number
@@ -86,6 +87,37 @@ struct PK<double> {
   }
 };
 
+// Scalar arithmetic on FP32 column pairs: per lane the same round-to-nearest
+// add, sub, mul and fused multiply-add as PK<float> (the intrinsics are never
+// contracted or reassociated), issued as two scalar instructions, so a walk
+// gives bit-identical sums with either form.
+struct PKs {
+  typedef float2 V;
+  static __device__ __forceinline__ V bc(float s) { return make_float2(s, s); }
+  static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V add(V a, V b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V mul(V a, V b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) {
+    return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+  }
+};
+
+// Pair arithmetic of a walk, AR: 1 packed f32x2 instructions, 0 scalar
+// pairs; FP64 pairs are always scalar.  Measured on GB300 the scalar form is
+// the faster one for the HVP at large lattices: the odd column pairs a
+// packed instruction needs as aligned register pairs cost moves that scalar
+// operands do not (the compiler's float2 intrinsics behave like the inline
+// PTX).
+template <typename T, int AR>
+struct PA {
+  typedef PK<T> P;
+};
+template <>
+struct PA<float, 0> {
+  typedef PKs P;
+};
+
 // One staged row as seen from the column pair (x, x + 1): x[c + 2] holds the
 // columns (x + c, x + 1 + c), c = -2 .. 2, of the x component (y, z alike).
 template <typename T>
@@ -130,10 +162,9 @@ struct WP {
 };
 
 // Adds to (hx, hy, hz) the contribution of a row at offset d2 (= row - site).
-template <typename T, int D2>
+template <typename T, int D2, class P = PK<T>>
 __device__ __forceinline__ void add_row(const RowP<T>& r, typename PK<T>::V& hx, typename PK<T>::V& hy,
                                         typename PK<T>::V& hz, const WP<T>& w) {
-  typedef PK<T> P;
 #define XC(c) r.x[(c) + 2]
 #define YC(c) r.y[(c) + 2]
 #define ZC(c) r.z[(c) + 2]
@@ -195,25 +226,25 @@ __device__ __forceinline__ void add_row(const RowP<T>& r, typename PK<T>::V& hx,
 
 // Row RR of the walk (the strip's sites are rows 2 .. SW + 1) meets strip
 // site S at offset d2 = RR - 2 - S; the site's own row first goes to the hook.
-template <typename T, int SW, int RR, int S, class F>
+template <typename T, int SW, int RR, int S, class P, class F>
 __device__ __forceinline__ void scatter(const RowP<T>& r, typename PK<T>::V (&ax)[SW], typename PK<T>::V (&ay)[SW],
                                         typename PK<T>::V (&az)[SW], const WP<T>& w, F& f) {
   constexpr int D2 = RR - 2 - S;
   if constexpr (S >= 0 && S < SW && D2 >= -2 && D2 <= 2) {
     if constexpr (D2 == 0) f.template center<S>(r, ax[S], ay[S], az[S]);
-    add_row<T, D2>(r, ax[S], ay[S], az[S], w);
+    add_row<T, D2, P>(r, ax[S], ay[S], az[S], w);
   }
 }
 
-template <typename T, int SW, int RR, class F>
+template <typename T, int SW, int RR, class P, class F>
 __device__ __forceinline__ void scatter_row(const RowP<T>& r, typename PK<T>::V (&ax)[SW],
                                             typename PK<T>::V (&ay)[SW], typename PK<T>::V (&az)[SW],
                                             const WP<T>& w, F& f) {
-  scatter<T, SW, RR, RR - 4>(r, ax, ay, az, w, f);
-  scatter<T, SW, RR, RR - 3>(r, ax, ay, az, w, f);
-  scatter<T, SW, RR, RR - 2>(r, ax, ay, az, w, f);
-  scatter<T, SW, RR, RR - 1>(r, ax, ay, az, w, f);
-  scatter<T, SW, RR, RR>(r, ax, ay, az, w, f);
+  scatter<T, SW, RR, RR - 4, P>(r, ax, ay, az, w, f);
+  scatter<T, SW, RR, RR - 3, P>(r, ax, ay, az, w, f);
+  scatter<T, SW, RR, RR - 2, P>(r, ax, ay, az, w, f);
+  scatter<T, SW, RR, RR - 1, P>(r, ax, ay, az, w, f);
+  scatter<T, SW, RR, RR, P>(r, ax, ay, az, w, f);
 }
 
 // Reads the three aligned column pairs (x - 2, x - 1), (x, x + 1),
@@ -233,38 +264,39 @@ __device__ __forceinline__ void read_pairs(const T* p, typename PK<T>::V (&o)[5]
 
 // Walk of rows 0 .. RR of a strip starting at staged row row0 (the staged
 // tile has SY rows per component plane).
-template <typename T, int SW, int SY, int RR>
+template <typename T, int SW, int SY, int RR, class P>
 struct SWalk {
   template <class F>
   static __device__ __forceinline__ void run(const T* __restrict__ tile, int row0, int lane,
                                              typename PK<T>::V (&ax)[SW], typename PK<T>::V (&ay)[SW],
                                              typename PK<T>::V (&az)[SW], const WP<T>& w, F& f) {
-    SWalk<T, SW, SY, RR - 1>::run(tile, row0, lane, ax, ay, az, w, f);
+    SWalk<T, SW, SY, RR - 1, P>::run(tile, row0, lane, ax, ay, az, w, f);
     RowP<T> r;
     // staged column of x - 2 is 2 lane + kPadL - 2
     const T* p = tile + (size_t)(row0 + RR) * kSX + 2 * lane + kPadL - 2;
     read_pairs<T>(p, r.x);
     read_pairs<T>(p + (size_t)kSX * SY, r.y);
     read_pairs<T>(p + 2 * (size_t)kSX * SY, r.z);
-    scatter_row<T, SW, RR>(r, ax, ay, az, w, f);
+    scatter_row<T, SW, RR, P>(r, ax, ay, az, w, f);
   }
 };
-template <typename T, int SW, int SY>
-struct SWalk<T, SW, SY, -1> {
+template <typename T, int SW, int SY, class P>
+struct SWalk<T, SW, SY, -1, P> {
   template <class F>
   static __device__ __forceinline__ void run(const T*, int, int, typename PK<T>::V (&)[SW],
                                              typename PK<T>::V (&)[SW], typename PK<T>::V (&)[SW], const WP<T>&,
                                              F&) {}
 };
 
-// The full walk of one strip: accumulators set to zero, rows 0 .. SW + 3.
-template <typename T, int SW, int SY, class F>
+// The full walk of one strip: accumulators set to zero, rows 0 .. SW + 3;
+// P: the pair arithmetic (PA).
+template <typename T, int SW, int SY, class P = PK<T>, class F>
 __device__ __forceinline__ void walk(const T* __restrict__ tile, int row0, int lane, typename PK<T>::V (&ax)[SW],
                                      typename PK<T>::V (&ay)[SW], typename PK<T>::V (&az)[SW], const WP<T>& w,
                                      F& f) {
 #pragma unroll
   for (int k = 0; k < SW; ++k) ax[k] = ay[k] = az[k] = PK<T>::bc((T)0);
-  SWalk<T, SW, SY, SW + 3>::run(tile, row0, lane, ax, ay, az, w, f);
+  SWalk<T, SW, SY, SW + 3, P>::run(tile, row0, lane, ax, ay, az, w, f);
 }
 
 // ---- asynchronous global -> shared copies (cp.async; 16-byte copies bypass L1)

@@ -74,3 +74,70 @@ def test_descent_minima_and_charges(oracle_run, gpu_run):
     for mm in (gpu_run["mp"], gpu_run["mm"]):
         g, _ = spin.riemann_grad(M, mm)
         assert mmf.max_torque(g) <= P.tau_F * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("dtype,L,extra", [
+    (torch.float64, 32, dict()),
+    (torch.float32, 64, dict(k=2, block=2, krylov_steps=20, reorth=1)),
+])
+def test_graph_replay_matches_plain_launches(monkeypatch, dtype, L, extra):
+    """The outer loop replays a captured step as a CUDA graph, the records
+    indexed on the device; launching every kernel one by one (MOTO_GRAPHS=0)
+    must give the same trajectory bit for bit, ascent and descent."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    if extra.get("reorth") == 1:
+        extra = dict(extra, reorth=mo.MOTO_REORTH_SELECTIVE)
+    M = workload_model(1, L, L)
+    m0 = inputs.add_noise(inputs.skyrmion(L, L, 4.0), 0.01, inputs.workload_seed(1, 7))
+    nv = extra.get("block", 1)
+    V0 = np.stack([inputs.gaussian_field(inputs.workload_seed(1, 30 + j), L, L) for j in range(nv)])
+    runs = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("MOTO_GRAPHS", graphs)
+        ctx = context(M, dtype, max_steps=25, descent_max_steps=40, **extra)
+        m = to_dev(m0, dtype)
+        V = to_dev(V0, dtype).contiguous()
+        rc, steps, trace = ctx.ascend(m, V, check_every=7)
+        rc2, mp, mm, out = ctx.descend(m, V[0].contiguous())
+        runs.append(dict(rc=rc, steps=steps, trace=to_np(trace), m=to_np(m), V=to_np(V), mp=to_np(mp),
+                         mm=to_np(mm), out=to_np(out)))
+        ctx.close()
+    a, b = runs
+    assert a["steps"] == b["steps"] and a["rc"] == b["rc"] and a["steps"] >= 3
+    assert np.isfinite(a["trace"]).all()
+    for key in ("trace", "m", "V", "mp", "mm", "out"):
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+def test_repeated_mmf_step_replays_bit_identically(monkeypatch):
+    """moto_mmf_step called again with the same arguments replays a captured
+    CUDA graph of the step; the states, records and status words must equal
+    those of the kernel-by-kernel launches (MOTO_GRAPHS=0) bit for bit, also
+    across a change of parameters between calls."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    L = 64
+    M = workload_model(1, L, L)
+    m0 = inputs.add_noise(inputs.skyrmion(L, L, 4.0), 0.01, inputs.workload_seed(1, 9))
+    V0 = np.stack([inputs.gaussian_field(inputs.workload_seed(1, 40 + j), L, L) for j in range(2)])
+    runs = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("MOTO_GRAPHS", graphs)
+        ctx = context(M, torch.float32, k=2, block=2, krylov_steps=16)
+        m = to_dev(m0, torch.float32)
+        V = to_dev(V0, torch.float32).contiguous()
+        out = torch.empty(6, dtype=torch.float64, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        p2 = mo.make_params(**{f: getattr(ctx.params, f) for f, _ in ctx.params._fields_})
+        p2.reorth = mo.MOTO_REORTH_SELECTIVE
+        recs = []
+        for t in range(10):
+            mo.moto_mmf_step(ctx.handle, m, ctx.params if t < 6 else p2, V, out, status)
+            recs.append(np.concatenate([to_np(out), to_np(status)]))
+        runs.append(dict(recs=np.stack(recs), m=to_np(m), V=to_np(V)))
+        ctx.close()
+    a, b = runs
+    assert np.isfinite(a["recs"]).all()
+    for key in ("recs", "m", "V"):
+        np.testing.assert_array_equal(a[key], b[key], err_msg=key)
