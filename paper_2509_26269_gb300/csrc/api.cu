@@ -1364,22 +1364,69 @@ int run_llg(moto_ctx* c, T* m, const moto_params* p, int check_every, int* steps
   state_kernel<<<wgrid(1), 32, 0, st>>>(c->st, 1, walker_ws());
   DevState h;
   memset(&h, 0, sizeof(h));
-  for (long t = 0; t <= nmax; ++t) {
-    P_energy_grad<T>(c, c->md, m, g0, nullptr, c->part, c->counter, D + kEG, &c->st->status, false, st);
+  // one Heun step (the last evaluates the stopping test only); like the
+  // optimiser's loop, step 0 runs launch by launch and the update step is
+  // then captured on a private stream and replayed
+  auto heun = [&](bool last, cudaStream_t s) {
+    P_energy_grad<T>(c, c->md, m, g0, nullptr, c->part, c->counter, D + kEG, &c->st->status, false, s);
     P_saddle_test(c, D + kEG, D + kFmax, D + kTheta, D + kMmfDots, p->tau_F, p->tau_lambda, D + kTmp, nullptr,
-                  c->st, 0, t == nmax ? 1 : 0, 0, st);
-    if (t < nmax) {
-      P_llg_predict<T>(c, m, g0, mp, p->llg_alpha, p->llg_dt, N, gate, kGateDone, st);
-      P_energy_grad<T>(c, c->md, mp, g1, nullptr, c->part, c->counter, D + kTmp + 2, &c->st->status, false, st);
-      P_llg_correct<T>(c, m, g0, mp, g1, p->llg_alpha, p->llg_dt, N, gate, kGateDone, st);
+                  c->st, 0, last ? 1 : 0, 0, s);
+    if (!last) {
+      P_llg_predict<T>(c, m, g0, mp, p->llg_alpha, p->llg_dt, N, gate, kGateDone, s);
+      P_energy_grad<T>(c, c->md, mp, g1, nullptr, c->part, c->counter, D + kTmp + 2, &c->st->status, false, s);
+      P_llg_correct<T>(c, m, g0, mp, g1, p->llg_alpha, p->llg_dt, N, gate, kGateDone, s);
     }
-    if (cudaGetLastError() != cudaSuccess) return MOTO_ERR_CUDA;
-    if ((t + 1) % check_every == 0 || t == nmax) {
-      int rc = read_state(c, &h, st);
-      if (rc) return rc;
+  };
+  cudaStream_t run = st, cs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (nmax > 1 && !c->prof_ev && step_graphable(c, p, false) &&
+      cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess) {
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess && cudaEventRecord(ev, st) == cudaSuccess &&
+        cudaStreamWaitEvent(cs, ev, 0) == cudaSuccess)
+      run = cs;
+  }
+  int rc = MOTO_OK;
+  for (long t = 0; t <= nmax; ++t) {
+    const bool last = t == nmax;
+    if (!last && t == 1 && run == cs) {
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        heun(false, cs);
+        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          graph = nullptr;
+          exec = nullptr;
+        }
+      }
+      cudaGetLastError();  // a failed capture falls back to plain launches
+    }
+    if (!last && exec) {
+      if (cudaGraphLaunch(exec, cs) != cudaSuccess) {
+        rc = MOTO_ERR_CUDA;
+        break;
+      }
+    } else {
+      heun(last, run);
+    }
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = MOTO_ERR_CUDA;
+      break;
+    }
+    if ((t + 1) % check_every == 0 || last) {
+      rc = read_state(c, &h, run);
+      if (rc) break;
       if (h.converged || status_code(h)) break;
     }
   }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) {
+    if (ev && cudaEventRecord(ev, cs) == cudaSuccess) cudaStreamWaitEvent(st, ev, 0);
+    cudaStreamDestroy(cs);
+  }
+  if (ev) cudaEventDestroy(ev);
+  if (rc) return rc;
   if (steps_out) *steps_out = h.pad[1];
   int sc = status_code(h);
   if (sc) return sc;

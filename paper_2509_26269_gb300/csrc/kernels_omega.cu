@@ -47,10 +47,35 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
   if (st->gate & (kGateKrylov | kGateDone)) return;
   __shared__ double Bn[MOTO_MAX_K][MOTO_MAX_K];
   __shared__ double M[MOTO_MAX_BASIS * MOTO_MAX_K];  // [k][r][c], k < j
+  // the operands, staged in one round trip: block rows j - 1 and j of the
+  // estimates (columns 0 .. (j + 1) b) and the blocks of T the recurrence
+  // reads, Td[k] = T(k, k) for k <= j and Tl[k] = T(k + 1, k) for k < j
+  __shared__ double Os[2 * MOTO_MAX_K][MOTO_MAX_BASIS];
+  // (j + 1) b <= MOTO_MAX_BASIS, so (j + 1) b^2 <= MOTO_MAX_BASIS MOTO_MAX_K
+  __shared__ double Td[MOTO_MAX_BASIS * MOTO_MAX_K];
+  __shared__ double Tl[MOTO_MAX_BASIS * MOTO_MAX_K];
   __shared__ double nu_s, wmax[32];
   const int bb = b * b, t = threadIdx.x;
   if (t < bb) Bn[t / b][t % b] = Rn[t];
+  const int ncol = (j + 1) * b;
+  for (int e = t; e < 2 * b * ncol; e += blockDim.x) {
+    const int rr = e / ncol, cc = e - rr * ncol;  // rr < b: block row j - 1
+    const int grow = (j - 1) * b + rr;
+    Os[rr][cc] = grow >= 0 ? Om[(size_t)grow * kLdO + cc] : 0.0;
+  }
+  for (int e = t; e < (2 * j + 1) * bb; e += blockDim.x) {
+    const int kb = e / bb, q = e - kb * bb, r = q / b, c = q - r * b;
+    if (kb <= j)
+      Td[kb * bb + q] = tblk(T, ldT, b, kb, kb, r, c);
+    else
+      Tl[(kb - j - 1) * bb + q] = tblk(T, ldT, b, kb - j, kb - j - 1, r, c);
+  }
   __syncthreads();
+  // staged views: W_{j,x} row r at Os[b + r][x], W_{j-1,x} row r at Os[r][x]
+#define OMJ(r, col) Os[b + (r)][col]
+#define OMJ1(r, col) Os[(r)][col]
+#define TD(k, r, c) Td[(k) * bb + (r) * b + (c)]
+#define TL(k, r, c) Tl[(k) * bb + (r) * b + (c)]
   if (t == 0) {
     double dmin = 1e300;
     for (int r = 0; r < b; ++r) dmin = fmin(dmin, Bn[r][r]);
@@ -63,20 +88,23 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
     double a = 0.0;
     for (int q = 0; q < b; ++q) {
       // W_{j,k+1} B_{k+1}   (W_{j,j} = I)
-      const double wjk1 = (k + 1 == j) ? (r == q ? 1.0 : 0.0) : Om[(size_t)(j * b + r) * kLdO + (k + 1) * b + q];
-      a += wjk1 * tblk(T, ldT, b, k + 1, k, q, c);
+      const double wjk1 = (k + 1 == j) ? (r == q ? 1.0 : 0.0) : OMJ(r, (k + 1) * b + q);
+      a += wjk1 * TL(k, q, c);
       // W_{j,k} A_k - A_j W_{j,k}
-      a += Om[(size_t)(j * b + r) * kLdO + k * b + q] * tblk(T, ldT, b, k, k, q, c);
-      a -= tblk(T, ldT, b, j, j, r, q) * Om[(size_t)(j * b + q) * kLdO + k * b + c];
+      a += OMJ(r, k * b + q) * TD(k, q, c);
+      a -= TD(j, r, q) * OMJ(q, k * b + c);
       // W_{j,k-1} B_k^T
-      if (k > 0) a += Om[(size_t)(j * b + r) * kLdO + (k - 1) * b + q] * tblk(T, ldT, b, k, k - 1, c, q);
+      if (k > 0) a += OMJ(r, (k - 1) * b + q) * TL(k - 1, c, q);
       // - B_j W_{j-1,k}   (W_{j-1,j-1} = I)
-      const double wj1k =
-          (k == j - 1) ? (q == c ? 1.0 : 0.0) : Om[(size_t)((j - 1) * b + q) * kLdO + k * b + c];
-      a -= tblk(T, ldT, b, j, j - 1, r, q) * wj1k;
+      const double wj1k = (k == j - 1) ? (q == c ? 1.0 : 0.0) : OMJ1(q, k * b + c);
+      a -= TL(j - 1, r, q) * wj1k;
     }
     M[e] = a;
   }
+#undef OMJ
+#undef OMJ1
+#undef TD
+#undef TL
   __syncthreads();
   const double nu = nu_s;
   double mx = 0.0;

@@ -211,7 +211,31 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const T* __restrict__
         acc[c][0] = acc[c][1] = acc[c][2] = (T)0;
       }
     }
-    for (int r = 0; r < nx; ++r) {
+    // four fields' loads in flight before their products (a thread holds one
+    // site, so with a single field in flight a long combination such as the
+    // Ritz vectors of 96 basis fields keeps too few bytes moving to cover the
+    // memory latency); the products are added in field order either way
+    int r = 0;
+    for (; r + 4 <= nx; r += 4) {
+      T xv[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T* xr = X + (size_t)(r + u) * ldx;
+        xv[u][0] = __ldg(xr + i);
+        xv[u][1] = __ldg(xr + N + i);
+        xv[u][2] = __ldg(xr + 2 * (size_t)N + i);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < NY; ++c) {
+          const T w = Cs[(r + u) * NY + c];
+          acc[c][0] += xv[u][0] * w;
+          acc[c][1] += xv[u][1] * w;
+          acc[c][2] += xv[u][2] * w;
+        }
+    }
+    for (; r < nx; ++r) {
       const T* xr = X + (size_t)r * ldx;
       const T x0 = __ldg(xr + i), x1 = __ldg(xr + N + i), x2 = __ldg(xr + 2 * (size_t)N + i);
 #pragma unroll

@@ -57,3 +57,28 @@ def test_llg_descent_reaches_the_oracle_minima():
         g, _ = spin.riemann_grad(M, to_np(x))
         assert mmf.max_torque(g) <= 1e-3 * (1 + 1e-9)
     ctx.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_llg_graph_replay_matches_plain_launches(monkeypatch, dtype):
+    """The Heun steps are replayed as a captured CUDA graph after the first;
+    launching every kernel (MOTO_GRAPHS=0) must give the same end states,
+    energies, charges and step counts bit for bit."""
+    require_gpu()
+    L1, L2 = 24, 20
+    M = Model(L1, L2, **FULL)
+    m = inputs.add_noise(inputs.skyrmion(L1, L2, 3.5), 0.05, 21)
+    v = spin.project(m, inputs.gaussian_field(22, L1, L2))
+    v /= np.sqrt(np.sum(v * v))
+    res = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("MOTO_GRAPHS", graphs)
+        ctx = context(M, dtype, descent=1, llg_alpha=1.0, llg_dt=0.01, llg_time=0.6, tau_F=1e-12)
+        rc, mp, mm, out = ctx.descend(to_dev(m, dtype), to_dev(v, dtype))
+        res.append((rc, to_np(mp), to_np(mm), to_np(out)))
+        ctx.close()
+    (rc_a, mp_a, mm_a, o_a), (rc_b, mp_b, mm_b, o_b) = res
+    assert rc_a == rc_b and int(o_a[4]) == int(o_a[5]) == 60
+    np.testing.assert_array_equal(mp_a, mp_b)
+    np.testing.assert_array_equal(mm_a, mm_b)
+    np.testing.assert_array_equal(o_a, o_b)
