@@ -19,7 +19,11 @@
 //
 // The estimates live in an MOTO_MAX_BASIS x MOTO_MAX_BASIS FP64 matrix Om
 // (block (i, k) at rows i b .., columns k b ..); the decision is the gate bit
-// kGateNoReorth, which the full-pass launches of the step test.
+// kGateNoReorth, which the full-pass launches of the step test.  The
+// recurrence itself runs in FP32: its values are order-of-magnitude bounds
+// compared with sqrt(eps) (>= 1e-8), far inside FP32's range, and on GB300
+// a chain of dependent FP64 operations costs ~100 cycles a link against a
+// few for FP32.
 #include "internal.h"
 
 namespace moto {
@@ -45,30 +49,35 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
   rlog = wofs(rlog, ws);
   st = wofs(st, ws);
   if (st->gate & (kGateKrylov | kGateDone)) return;
-  __shared__ double Bn[MOTO_MAX_K][MOTO_MAX_K];
-  __shared__ double M[MOTO_MAX_BASIS * MOTO_MAX_K];  // [k][r][c], k < j
+  __shared__ float Bn[MOTO_MAX_K][MOTO_MAX_K];
+  __shared__ float binv[MOTO_MAX_K];  // 1 / B_{j+1}(r, r), +inf where not positive
+  __shared__ float M[MOTO_MAX_BASIS * MOTO_MAX_K];  // [k][r][c], k < j
   // the operands, staged in one round trip: block rows j - 1 and j of the
   // estimates (columns 0 .. (j + 1) b) and the blocks of T the recurrence
   // reads, Td[k] = T(k, k) for k <= j and Tl[k] = T(k + 1, k) for k < j
-  __shared__ double Os[2 * MOTO_MAX_K][MOTO_MAX_BASIS];
+  __shared__ float Os[2 * MOTO_MAX_K][MOTO_MAX_BASIS];
   // (j + 1) b <= MOTO_MAX_BASIS, so (j + 1) b^2 <= MOTO_MAX_BASIS MOTO_MAX_K
-  __shared__ double Td[MOTO_MAX_BASIS * MOTO_MAX_K];
-  __shared__ double Tl[MOTO_MAX_BASIS * MOTO_MAX_K];
-  __shared__ double nu_s, wmax[32];
+  __shared__ float Td[MOTO_MAX_BASIS * MOTO_MAX_K];
+  __shared__ float Tl[MOTO_MAX_BASIS * MOTO_MAX_K];
+  __shared__ float nu_s, wmax[32];
   const int bb = b * b, t = threadIdx.x;
-  if (t < bb) Bn[t / b][t % b] = Rn[t];
+  if (t < bb) Bn[t / b][t % b] = (float)Rn[t];
+  if (t < b) {
+    const double d = Rn[t * b + t];
+    binv[t] = d > 0.0 ? (float)(1.0 / d) : __int_as_float(0x7f800000);
+  }
   const int ncol = (j + 1) * b;
   for (int e = t; e < 2 * b * ncol; e += blockDim.x) {
     const int rr = e / ncol, cc = e - rr * ncol;  // rr < b: block row j - 1
     const int grow = (j - 1) * b + rr;
-    Os[rr][cc] = grow >= 0 ? Om[(size_t)grow * kLdO + cc] : 0.0;
+    Os[rr][cc] = grow >= 0 ? (float)Om[(size_t)grow * kLdO + cc] : 0.f;
   }
   for (int e = t; e < (2 * j + 1) * bb; e += blockDim.x) {
     const int kb = e / bb, q = e - kb * bb, r = q / b, c = q - r * b;
     if (kb <= j)
-      Td[kb * bb + q] = tblk(T, ldT, b, kb, kb, r, c);
+      Td[kb * bb + q] = (float)tblk(T, ldT, b, kb, kb, r, c);
     else
-      Tl[(kb - j - 1) * bb + q] = tblk(T, ldT, b, kb - j, kb - j - 1, r, c);
+      Tl[(kb - j - 1) * bb + q] = (float)tblk(T, ldT, b, kb - j, kb - j - 1, r, c);
   }
   __syncthreads();
   // staged views: W_{j,x} row r at Os[b + r][x], W_{j-1,x} row r at Os[r][x]
@@ -77,18 +86,18 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
 #define TD(k, r, c) Td[(k) * bb + (r) * b + (c)]
 #define TL(k, r, c) Tl[(k) * bb + (r) * b + (c)]
   if (t == 0) {
-    double dmin = 1e300;
-    for (int r = 0; r < b; ++r) dmin = fmin(dmin, Bn[r][r]);
-    const double tn = fmax(st->tnorm, 1e-300);
-    nu_s = dmin > 0.0 ? eps * tn / dmin : 1e300;
+    float dmin = __int_as_float(0x7f800000);
+    for (int r = 0; r < b; ++r) dmin = fminf(dmin, Bn[r][r]);
+    const float tn = (float)fmax(st->tnorm, 1e-30);
+    nu_s = dmin > 0.f ? (float)eps * tn / dmin : __int_as_float(0x7f800000);
   }
   // right-hand sides
   for (int e = t; e < j * bb; e += blockDim.x) {
     const int k = e / bb, r = (e % bb) / b, c = e % b;
-    double a = 0.0;
+    float a = 0.f;
     for (int q = 0; q < b; ++q) {
       // W_{j,k+1} B_{k+1}   (W_{j,j} = I)
-      const double wjk1 = (k + 1 == j) ? (r == q ? 1.0 : 0.0) : OMJ(r, (k + 1) * b + q);
+      const float wjk1 = (k + 1 == j) ? (r == q ? 1.f : 0.f) : OMJ(r, (k + 1) * b + q);
       a += wjk1 * TL(k, q, c);
       // W_{j,k} A_k - A_j W_{j,k}
       a += OMJ(r, k * b + q) * TD(k, q, c);
@@ -96,7 +105,7 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
       // W_{j,k-1} B_k^T
       if (k > 0) a += OMJ(r, (k - 1) * b + q) * TL(k - 1, c, q);
       // - B_j W_{j-1,k}   (W_{j-1,j-1} = I)
-      const double wj1k = (k == j - 1) ? (q == c ? 1.0 : 0.0) : OMJ1(q, k * b + c);
+      const float wj1k = (k == j - 1) ? (q == c ? 1.f : 0.f) : OMJ1(q, k * b + c);
       a -= TL(j - 1, r, q) * wj1k;
     }
     M[e] = a;
@@ -106,35 +115,36 @@ __global__ void __launch_bounds__(1024) omega_estimate_kernel(int b, int j, cons
 #undef TD
 #undef TL
   __syncthreads();
-  const double nu = nu_s;
-  double mx = 0.0;
+  const float nu = nu_s;
+  float mx = 0.f;
   // B_{j+1}^T X = M, B upper triangular: forward substitution down each column
   for (int e = t; e < j * b; e += blockDim.x) {
     const int k = e / b, c = e % b;
-    double x[MOTO_MAX_K];
+    float x[MOTO_MAX_K];
     for (int r = 0; r < b; ++r) {
-      double a = M[k * bb + r * b + c];
+      float a = M[k * bb + r * b + c];
       for (int q = 0; q < r; ++q) a -= Bn[q][r] * x[q];
-      x[r] = (Bn[r][r] > 0.0) ? a / Bn[r][r] : 1e300;
+      x[r] = a * binv[r];
     }
     for (int r = 0; r < b; ++r) {
-      const double v = x[r] + copysign(nu, x[r]);
-      Om[(size_t)((j + 1) * b + r) * kLdO + k * b + c] = v;
-      mx = fmax(mx, fabs(v));
+      const float v = x[r] + copysignf(nu, x[r]);
+      Om[(size_t)((j + 1) * b + r) * kLdO + k * b + c] = (double)v;
+      mx = fmaxf(mx, fabsf(v));
     }
   }
   for (int e = t; e < bb; e += blockDim.x)
-    Om[(size_t)((j + 1) * b + e / b) * kLdO + j * b + e % b] = nu;
-  // block maximum, then the decision
+    Om[(size_t)((j + 1) * b + e / b) * kLdO + j * b + e % b] = (double)nu;
+  // block maximum, then the decision (a factor without a positive diagonal,
+  // nu = inf, always asks for the pass)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((t & 31) == 0) wmax[t >> 5] = mx;
   __syncthreads();
   if (t == 0) {
-    double m2 = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, wmax[w]);
+    float m2 = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmaxf(m2, wmax[w]);
     const bool forced = st->pad[3] != 0;
-    const bool need = forced || !(m2 <= sqrt(eps));
+    const bool need = forced || !(nu < __int_as_float(0x7f800000)) || !(m2 <= (float)sqrt(eps));
     st->pad[5] = forced ? 1 : 0;
     rlog[j] = need ? 1.0 : 0.0;  // for the launch profiler: did step j take the full pass
     if (need)

@@ -4,6 +4,8 @@
 // (Cholesky QR factors, Jacobi eigensolver, L-BFGS two-loop in coefficient
 // space) that run in a single block.
 #include <float.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -211,31 +213,7 @@ __global__ void __launch_bounds__(kThreads) combine_kernel(const T* __restrict__
         acc[c][0] = acc[c][1] = acc[c][2] = (T)0;
       }
     }
-    // four fields' loads in flight before their products (a thread holds one
-    // site, so with a single field in flight a long combination such as the
-    // Ritz vectors of 96 basis fields keeps too few bytes moving to cover the
-    // memory latency); the products are added in field order either way
-    int r = 0;
-    for (; r + 4 <= nx; r += 4) {
-      T xv[4][3];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const T* xr = X + (size_t)(r + u) * ldx;
-        xv[u][0] = __ldg(xr + i);
-        xv[u][1] = __ldg(xr + N + i);
-        xv[u][2] = __ldg(xr + 2 * (size_t)N + i);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int c = 0; c < NY; ++c) {
-          const T w = Cs[(r + u) * NY + c];
-          acc[c][0] += xv[u][0] * w;
-          acc[c][1] += xv[u][1] * w;
-          acc[c][2] += xv[u][2] * w;
-        }
-    }
-    for (; r < nx; ++r) {
+    for (int r = 0; r < nx; ++r) {
       const T* xr = X + (size_t)r * ldx;
       const T x0 = __ldg(xr + i), x1 = __ldg(xr + N + i), x2 = __ldg(xr + 2 * (size_t)N + i);
 #pragma unroll
@@ -284,10 +262,144 @@ static int stream_grid(size_t sites) {
   return stream_grid(sites, sizeof(T) == 4 ? 4 : 1);
 }
 
+// Long FP32 combinations out = X C (nx >= 16 fields into ny <= 8, no Y term,
+// no projection: the Ritz vectors of a block Lanczos basis).  Such a
+// combination reads nx fields at once; a thread of combine_kernel keeps one
+// field's loads in registers at a time, too few bytes in flight to cover the
+// memory latency.  Here each thread owns quads of 4 consecutive elements of
+// the flattened fields and copies its quad of 4 fields at a time into its
+// own slots of a shared-memory ring with 16-byte cp.async (kCombRing groups,
+// two in flight while one is used), so the bytes in flight do not cost
+// registers.  Only the issuing thread reads its slots, so cp.async.wait_group
+// is the only synchronisation.  Each output element is the same FMA chain
+// over the fields in order as in combine_kernel, so the results are
+// bit-identical.  (thread, group) steps run through one pipeline across the
+// thread's quads.  Slots are field-major, thread-minor: a warp's 16-byte
+// reads are conflict-free.
+constexpr int kCombRing = 3;
+constexpr int kCombThreads = 192;  // 40 KB of static shared memory a block
+
+__device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gsrc)
+               : "memory");
+}
+
+template <int NY>
+__global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float* __restrict__ X, size_t ldx, int nx,
+                                                                    const int* nx_dev, const double* __restrict__ C,
+                                                                    int ny, double sigma, float* out, size_t ldo,
+                                                                    size_t n, const int* gate, int mask, size_t ws) {
+  X = wofs(X, ws);
+  nx_dev = wofs(nx_dev, ws);
+  C = wofs(C, ws);
+  out = wofs(out, ws);
+  gate = wofs(gate, ws);
+  if (gate && (*gate & mask)) return;
+  if (nx_dev) nx = min(*nx_dev, nx);
+  __shared__ float Cs[MOTO_MAX_BASIS * NY];
+  __shared__ __align__(16) float4 ring[kCombRing * 4 * kCombThreads];
+  for (int idx = threadIdx.x; idx < nx * NY; idx += blockDim.x) {
+    const int r = idx / NY, c = idx - r * NY;
+    Cs[idx] = c < ny ? (float)(sigma * C[r * ny + c]) : 0.f;
+  }
+  __syncthreads();
+  const size_t nq = (n + 3) / 4;
+  const int G = nx > 4 ? (nx + 3) / 4 : 1;  // groups of 4 fields (nx = 0: the outputs are zero)
+  const size_t tq = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t qstride = (size_t)gridDim.x * blockDim.x;
+  // the thread's quads: tq, tq + qstride, ...; step s = (quad index i, group g)
+  const size_t nmine = tq < nq ? (nq - 1 - tq) / qstride + 1 : 0;
+  const size_t nsteps = nmine * (size_t)G;
+  auto issue = [&](size_t step) {
+    if (step < nsteps) {
+      const size_t i = step / G;
+      const int g = (int)(step - i * G);
+      const size_t e0 = 4 * (tq + i * qstride);
+      const int slot = (int)(step % kCombRing);
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int r = 4 * g + f;
+        if (r < nx) cp_async16_cg(&ring[(slot * 4 + f) * kCombThreads + threadIdx.x], X + (size_t)r * ldx + e0);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");  // empty groups keep the count uniform
+  };
+#pragma unroll
+  for (int k = 0; k < kCombRing - 1; ++k) issue(k);
+  float acc[NY][4];
+  for (size_t step = 0; step < nsteps; ++step) {
+    issue(step + kCombRing - 1);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kCombRing - 1) : "memory");
+    const size_t i = step / G;
+    const int g = (int)(step - i * G);
+    if (g == 0) {
+#pragma unroll
+      for (int c = 0; c < NY; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
+    }
+    const int slot = (int)(step % kCombRing);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const int r = 4 * g + f;
+      if (r < nx) {
+        const float4 x = ring[(slot * 4 + f) * kCombThreads + threadIdx.x];
+#pragma unroll
+        for (int c = 0; c < NY; ++c) {
+          const float w = Cs[r * NY + c];
+          acc[c][0] = fmaf(x.x, w, acc[c][0]);
+          acc[c][1] = fmaf(x.y, w, acc[c][1]);
+          acc[c][2] = fmaf(x.z, w, acc[c][2]);
+          acc[c][3] = fmaf(x.w, w, acc[c][3]);
+        }
+      }
+    }
+    if (g == G - 1) {
+      const size_t e0 = 4 * (tq + i * qstride);
+      if (e0 + 4 <= n) {
+#pragma unroll
+        for (int c = 0; c < NY; ++c)
+          if (c < ny)
+            *reinterpret_cast<float4*>(out + (size_t)c * ldo + e0) =
+                make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NY; ++c)
+          if (c < ny)
+            for (int u = 0; u < 4 && e0 + u < n; ++u) out[(size_t)c * ldo + e0 + u] = acc[c][u];
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 template <typename T>
 void launch_combine(const T* X, size_t ldx, int nx, const int* nx_dev, const double* C, int ny, const T* Y,
                     size_t ldy, double beta, double sigma, T* out, size_t ldo, const T* m, int N, const int* gate,
                     int mask, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    // long combinations: the cp.async ring (needs 16-byte aligned fields:
+    // the quads of the last field may read up to 3 elements past 3N, inside
+    // its padding, and those elements are never stored)
+    const size_t n = 3 * (size_t)N;
+    const bool al = ((uintptr_t)X % 16 == 0) && ((uintptr_t)out % 16 == 0) && ldx % 4 == 0 && ldo % 4 == 0 &&
+                    ldx >= (n + 3) / 4 * 4 && walker_ws() % 16 == 0;
+    static const bool ring_on = [] {
+      const char* e = getenv("MOTO_COMBINE_RING");  // "0": always combine_kernel (a diagnostic switch)
+      return !(e && strcmp(e, "0") == 0);
+    }();
+    if (ring_on && nx >= 16 && !Y && !m && beta == 0.0 && al) {
+      const size_t nq = (n + 3) / 4;
+      const size_t want = (nq + kCombThreads - 1) / kCombThreads;
+      const int g = (int)std::min<size_t>(want, (size_t)kSMs * 4);  // one wave: 4 blocks an SM by registers
+      if (ny <= 4)
+        combine_long_kernel<4><<<wgrid(g), kCombThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, sigma, out, ldo, n, gate,
+                                                                mask, walker_ws());
+      else
+        combine_long_kernel<8><<<wgrid(g), kCombThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, sigma, out, ldo, n, gate,
+                                                                mask, walker_ws());
+      return;
+    }
+  }
   const int g = stream_grid<T>(N);
   if (ny <= 1)
     combine_kernel<T, 1><<<wgrid(g), kThreads, 0, st>>>(X, ldx, nx, nx_dev, C, ny, Y, ldy, (T)beta, (T)sigma, out, ldo, m,

@@ -184,3 +184,39 @@ def test_lowest_modes_after_a_converged_ascent():
     assert int(to_np(info1)[0]) == 60
     ctx.close()
     fresh.close()
+
+
+def test_ritz_combination_ring_is_bit_identical():
+    """The Ritz vectors of a 96-field basis go through the cp.async-ring
+    combination; the plain combination kernel (MOTO_COMBINE_RING=0, read when
+    the library loads, so it runs in a child process) must give the same
+    eigenpairs bit for bit."""
+    require_gpu()
+    import subprocess
+    import sys
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, ".")
+sys.path.insert(0, "tests")
+import inputs
+from gpu_util import context, to_dev, to_np, workload_model
+L = 256
+M = workload_model(4, L, L)
+m = inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, 3))
+V0 = np.stack([inputs.gaussian_field(inputs.workload_seed(4, 40), L, L, offset=j * 3 * L * L) for j in range(8)])
+ctx = context(M, torch.float32, k=8, block=8, krylov_steps=12)
+lam, V, info = ctx.lowest_modes(to_dev(m, torch.float32), to_dev(V0, torch.float32))
+np.save(sys.argv[1], np.concatenate([to_np(lam)[:8], to_np(V).ravel()]))
+'''
+    import os
+    import tempfile
+    outs = []
+    with tempfile.TemporaryDirectory() as d:
+        for flag in ("1", "0"):
+            f = os.path.join(d, f"r{flag}.npy")
+            env = dict(os.environ, MOTO_COMBINE_RING=flag)
+            root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+            subprocess.run([sys.executable, "-c", code, f], check=True, env=env, cwd=root)
+            outs.append(np.load(f))
+    assert np.isfinite(outs[0]).all()
+    np.testing.assert_array_equal(outs[0], outs[1])
