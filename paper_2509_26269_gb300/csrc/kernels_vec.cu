@@ -608,122 +608,6 @@ __global__ void __launch_bounds__(kThreads, 2) chol2_gram_kernel(const T* __rest
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// FP32 second Cholesky Gram through a per-thread cp.async ring: the fields of
-// the thread's element pairs (8 bytes of each of the nx <= 8 fields a stage)
-// go straight to the thread's own slots of a kChol2Ring-stage ring in shared
-// memory, three stages in flight while one is used, so the bytes in flight
-// do not compete with the 36 Gram accumulators for registers (the register
-// double buffer of chol2_gram_kernel caps it at two blocks an SM).  t = X P
-// and the Gram are the same FMA chains as in chol2_gram_kernel; the pairs a
-// thread owns, and so the order of the sums, follow this kernel's grid.
-constexpr int kChol2Ring = 4;
-constexpr int kChol2Threads = 160;  // 40 KB of ring a block
-
-__global__ void __launch_bounds__(kChol2Threads) chol2_gram_ring_kernel(const float* __restrict__ X, size_t ldx,
-                                                                        int nx, const double* __restrict__ P,
-                                                                        size_t n, double* out, double* part,
-                                                                        unsigned* counter, const int* gate, int mask,
-                                                                        size_t ws) {
-  X = wofs(X, ws);
-  P = wofs(P, ws);
-  out = wofs(out, ws);
-  part = wofs(part, ws);
-  counter = wofs(counter, ws);
-  gate = wofs(gate, ws);
-  if (gate && (*gate & mask)) return;
-  __shared__ __align__(16) float Ps[64];
-  __shared__ double red[kChol2Threads / 32][kUpdSelf];
-  __shared__ __align__(8) float2 ring[kChol2Ring * 8 * kChol2Threads];
-  stage_tri(Ps, P, nx);
-  __syncthreads();
-  float sacc[kUpdSelf];
-#pragma unroll
-  for (int q = 0; q < kUpdSelf; ++q) sacc[q] = 0.f;
-  const size_t np = (n + 1) / 2;
-  const size_t tv = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  const size_t nmine = tv < np ? (np - 1 - tv) / stride + 1 : 0;
-  auto issue = [&](size_t i) {
-    if (i < nmine) {
-      const size_t e = 2 * (tv + i * stride);
-      const int slot = (int)(i % kChol2Ring);
-      // the tail pair of an odd n also copies the element past n (inside
-      // the field's padding: ldx >= n + 1); it is replaced by zero below
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-        if (r < nx)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
-                           (uint32_t)__cvta_generic_to_shared(&ring[(slot * 8 + r) * kChol2Threads + threadIdx.x])),
-                       "l"(X + (size_t)r * ldx + e)
-                       : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-#pragma unroll
-  for (int k = 0; k < kChol2Ring - 1; ++k) issue(k);
-  for (size_t i = 0; i < nmine; ++i) {
-    issue(i + kChol2Ring - 1);
-    asm volatile("cp.async.wait_group %0;" ::"n"(kChol2Ring - 1) : "memory");
-    const int slot = (int)(i % kChol2Ring);
-    const bool tail = 2 * (tv + i * stride) + 2 > n;
-    float2 x[8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      x[r] = make_float2(0.f, 0.f);
-      if (r < nx) {
-        x[r] = ring[(slot * 8 + r) * kChol2Threads + threadIdx.x];
-        if (tail) x[r].y = 0.f;
-      }
-    }
-    float2 t[8];
-    tri_mul2(x, Ps, t);
-    int q = 0;
-#pragma unroll
-    for (int c1 = 0; c1 < 8; ++c1)
-#pragma unroll
-      for (int c2 = c1; c2 < 8; ++c2, ++q) sacc[q] = fmaf(t[c1].y, t[c2].y, fmaf(t[c1].x, t[c2].x, sacc[q]));
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  // warp butterflies in FP32, block and grid sums in two-float arithmetic
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < kUpdSelf; ++q) {
-    float v = sacc[q];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    sacc[q] = v;
-  }
-  F2(*rred)[kUpdSelf] = reinterpret_cast<F2(*)[kUpdSelf]>(red);
-#pragma unroll
-  for (int q = 0; q < kUpdSelf; ++q)
-    if (lane == (q & 31)) rred[wid][q] = f2_of(sacc[q]);
-  __syncthreads();
-  if (threadIdx.x < kUpdSelf) {
-    F2 acc = rred[0][threadIdx.x];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) acc = radd(acc, rred[w][threadIdx.x]);
-    reinterpret_cast<F2*>(part)[(size_t)blockIdx.x * kUpdSelf + threadIdx.x] = acc;
-  }
-  if (!grid_last_block(counter)) return;
-  __syncthreads();
-  __shared__ double tot[kUpdSelf];
-  grid_sum_f2(reinterpret_cast<const F2*>(part), gridDim.x, kUpdSelf, tot, reinterpret_cast<F2*>(red));
-  __syncthreads();
-  if (threadIdx.x < kUpdSelf) {
-    const double acc = tot[threadIdx.x];
-    int c1 = 0, rem = threadIdx.x;
-    while (rem >= 8 - c1) {
-      rem -= 8 - c1;
-      ++c1;
-    }
-    const int c2 = c1 + rem;
-    if (c2 < nx) {
-      out[c1 * nx + c2] = acc;
-      out[c2 * nx + c1] = acc;
-    }
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-}
-
 // Site-based: a thread loads all its fields first (24 per site), then forms
 // t and Q per component.  PAIR (FP32, N even): two adjacent sites per thread
 // with 8-byte loads and packed FMAs.
@@ -835,26 +719,6 @@ bool launch_chol2(const T* X, size_t ldx, int nx, const double* P1, const double
     // FP64 arithmetic is slow on GB300, so FP64 blocks take 8 KB
     const size_t per_block = sizeof(T) == 4 ? 65536 : 8192;
     size_t g = (nx * n * sizeof(T) + per_block - 1) / per_block;
-    if constexpr (sizeof(T) == 4) {
-      // one wave of as many ring blocks an SM as fit (at most 6: the partials
-      // buffer holds kSMs x 8 x 32 entries), queried once
-      static int bps = 0;
-      if (bps == 0) {
-        cudaFuncSetAttribute(chol2_gram_ring_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, chol2_gram_ring_kernel, kChol2Threads, 0) !=
-                cudaSuccess ||
-            bps < 1)
-          bps = 1;
-        bps = std::min(bps, 6);
-      }
-      if (ldx >= n + 1 || n % 2 == 0) {
-        const size_t cap = (size_t)kSMs * bps;
-        g = std::max<size_t>(1, std::min(g, cap));
-        chol2_gram_ring_kernel<<<wgrid((int)g), kChol2Threads, 0, st>>>(X, ldx, nx, P1, n, S2, part, counter, gate,
-                                                                        mask, walker_ws());
-        return true;
-      }
-    }
     const size_t cap = (size_t)kSMs * 2;  // one wave at two blocks per SM
     if (g > cap) g = cap;
     if (g < 1) g = 1;
