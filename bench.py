@@ -547,7 +547,8 @@ def run_probe(args):
     of the step three times on the workload's state at the bench's lattice
     (the autotuner off, the variant forced), for single-kernel captures
     (`ncu -k <kernel> -s 1 -c 1`).  hvp: 8-vector tangent HVPs of the bench's
-    seeded start block; stencil: energy + gradient + s."""
+    seeded start block; stencil: energy + gradient + s; ritz: one block
+    Lanczos solve (for its Ritz-vector combination, launched once)."""
     os.environ["MOTO_AUTOTUNE"] = "0"
     import torch
     import paper_2509_26269_gb300 as mo
@@ -557,7 +558,12 @@ def run_probe(args):
                   k=K_MODES, block=BLOCK, krylov_steps=STEPS)
     m = torch.from_numpy(inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, 0))).to(
         "cuda", torch.float32)
-    if args.probe == "hvp":
+    if args.probe == "ritz":
+        # one block Lanczos solve of the step (its Ritz vectors: the long
+        # combination of the 96 basis fields)
+        V0 = torch.from_numpy(start_block(BLOCK, inputs.workload_seed(4, 0) + 17)).to("cuda", torch.float32)
+        ctx.lowest_modes(m, V0, reorth=mo.MOTO_REORTH_SELECTIVE)
+    elif args.probe == "hvp":
         mo.moto_set_hvp_variant(ctx.handle, args.variant)
         _, _, s = ctx.energy_grad(m)
         V = torch.from_numpy(start_block(BLOCK, inputs.workload_seed(4, 0) + 17)).to("cuda", torch.float32)
@@ -585,7 +591,7 @@ def main():
     ap.add_argument("--saddle-steps", type=int, default=3000, help="ascent step cap of the saddles/s leg")
     ap.add_argument("--lattice", type=int, default=2048,
                     help="lattice side; values other than 2048 are small cases for profiler captures")
-    ap.add_argument("--probe", choices=["hvp", "stencil"], default=None,
+    ap.add_argument("--probe", choices=["hvp", "stencil", "ritz"], default=None,
                     help="profiling aid: launch one kernel family three times and exit (no timing)")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant forced by --probe")
     args = ap.parse_args()

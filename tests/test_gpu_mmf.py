@@ -141,3 +141,38 @@ def test_repeated_mmf_step_replays_bit_identically(monkeypatch):
     assert np.isfinite(a["recs"]).all()
     for key in ("recs", "m", "V"):
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
+
+
+def test_step_graph_follows_a_change_of_model(monkeypatch):
+    """A captured moto_mmf_step graph bakes in the model; moto_set_pairs must
+    discard it, so steps after the switch to a pair-list Hamiltonian equal
+    those of a context that launched every kernel (bit for bit), and differ
+    from the shell model's."""
+    require_gpu()
+    import paper_2509_26269_gb300 as mo
+    L = 64
+    M = workload_model(1, L, L)
+    pl = inputs.random_pairs(41, reach=3, n_offsets=12)
+    m0 = inputs.add_noise(inputs.skyrmion(L, L, 4.0), 0.01, inputs.workload_seed(1, 11))
+    V0 = np.stack([inputs.gaussian_field(inputs.workload_seed(1, 50 + j), L, L) for j in range(2)])
+    runs = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("MOTO_GRAPHS", graphs)
+        ctx = context(M, torch.float32, k=2, block=2, krylov_steps=16)
+        m = to_dev(m0, torch.float32)
+        V = to_dev(V0, torch.float32).contiguous()
+        out = torch.empty(6, dtype=torch.float64, device="cuda")
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        recs = []
+        for t in range(6):
+            if t == 3:
+                ctx.set_pairs(pl)
+            mo.moto_mmf_step(ctx.handle, m, ctx.params, V, out, status)
+            recs.append(to_np(out).copy())
+        runs.append(dict(recs=np.stack(recs), m=to_np(m)))
+        ctx.close()
+    a, b = runs
+    np.testing.assert_array_equal(a["recs"], b["recs"])
+    np.testing.assert_array_equal(a["m"], b["m"])
+    # the energy of step 3 is the pair model's, not a continuation of the shells'
+    assert abs(a["recs"][3, 0] - a["recs"][2, 0]) > 1e-3 * abs(a["recs"][2, 0])
