@@ -276,7 +276,8 @@ static int stream_grid(size_t sites) {
 // bit-identical.  (thread, group) steps run through one pipeline across the
 // thread's quads.  Slots are field-major, thread-minor: a warp's 16-byte
 // reads are conflict-free.
-constexpr int kCombRing = 4;
+constexpr int kCombRing = 4;  // a power of two (slot = step & (kCombRing - 1))
+static_assert((kCombRing & (kCombRing - 1)) == 0, "ring size");
 constexpr int kCombThreads = 160;  // 40 KB of static shared memory a block
 
 __device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* gsrc) {
@@ -311,16 +312,22 @@ __global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float*
   // the thread's quads: tq, tq + qstride, ...; step s = (quad index i, group g)
   const size_t nmine = tq < nq ? (nq - 1 - tq) / qstride + 1 : 0;
   const size_t nsteps = nmine * (size_t)G;
+  // the issue position runs kCombRing - 1 steps ahead of the consume
+  // position; both walk (quad, group) with counters (no divisions)
+  size_t iq = 0;  // issue: quad index and group
+  int ig = 0;
   auto issue = [&](size_t step) {
     if (step < nsteps) {
-      const size_t i = step / G;
-      const int g = (int)(step - i * G);
-      const size_t e0 = 4 * (tq + i * qstride);
-      const int slot = (int)(step % kCombRing);
+      const size_t e0 = 4 * (tq + iq * qstride);
+      const int slot = (int)(step & (kCombRing - 1));
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const int r = 4 * g + f;
+        const int r = 4 * ig + f;
         if (r < nx) cp_async16_cg(&ring[(slot * 4 + f) * kCombThreads + threadIdx.x], X + (size_t)r * ldx + e0);
+      }
+      if (++ig == G) {
+        ig = 0;
+        ++iq;
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");  // empty groups keep the count uniform
@@ -328,16 +335,16 @@ __global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float*
 #pragma unroll
   for (int k = 0; k < kCombRing - 1; ++k) issue(k);
   float acc[NY][4];
+  size_t cq = 0;  // consume: quad index and group
+  int g = 0;
   for (size_t step = 0; step < nsteps; ++step) {
     issue(step + kCombRing - 1);
     asm volatile("cp.async.wait_group %0;" ::"n"(kCombRing - 1) : "memory");
-    const size_t i = step / G;
-    const int g = (int)(step - i * G);
     if (g == 0) {
 #pragma unroll
       for (int c = 0; c < NY; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
     }
-    const int slot = (int)(step % kCombRing);
+    const int slot = (int)(step & (kCombRing - 1));
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const int r = 4 * g + f;
@@ -354,7 +361,7 @@ __global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float*
       }
     }
     if (g == G - 1) {
-      const size_t e0 = 4 * (tq + i * qstride);
+      const size_t e0 = 4 * (tq + cq * qstride);
       if (e0 + 4 <= n) {
 #pragma unroll
         for (int c = 0; c < NY; ++c)
@@ -367,6 +374,10 @@ __global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float*
           if (c < ny)
             for (int u = 0; u < 4 && e0 + u < n; ++u) out[(size_t)c * ldo + e0 + u] = acc[c][u];
       }
+    }
+    if (++g == G) {
+      g = 0;
+      ++cq;
     }
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
