@@ -548,7 +548,8 @@ def run_probe(args):
     (the autotuner off, the variant forced), for single-kernel captures
     (`ncu -k <kernel> -s 1 -c 1`).  hvp: 8-vector tangent HVPs of the bench's
     seeded start block; stencil: energy + gradient + s; ritz: one block
-    Lanczos solve (for its Ritz-vector combination, launched once)."""
+    Lanczos solve (for its Ritz-vector combination, launched once); l1: the
+    explorer's pairwise L1 distances of a population of 24."""
     os.environ["MOTO_AUTOTUNE"] = "0"
     import torch
     import paper_2509_26269_gb300 as mo
@@ -558,7 +559,15 @@ def run_probe(args):
                   k=K_MODES, block=BLOCK, krylov_steps=STEPS)
     m = torch.from_numpy(inputs.add_noise(inputs.biskyrmion(L, L, 8.0), 0.01, inputs.workload_seed(4, 0))).to(
         "cuda", torch.float32)
-    if args.probe == "ritz":
+    if args.probe == "l1":
+        # the explorer's pairwise L1 distances of a population of 24
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(4000)
+        pop = m[None] + 0.2 * torch.randn((24, 3, L, L), generator=gen, device="cuda", dtype=torch.float32)
+        Dpop = torch.empty((24, 24), device="cuda", dtype=torch.float64)
+        for _ in range(3):
+            mo.moto_pairwise_l1(ctx.handle, pop, 3 * L * L, 24, Dpop)
+    elif args.probe == "ritz":
         # one block Lanczos solve of the step (its Ritz vectors: the long
         # combination of the 96 basis fields)
         V0 = torch.from_numpy(start_block(BLOCK, inputs.workload_seed(4, 0) + 17)).to("cuda", torch.float32)
@@ -591,7 +600,7 @@ def main():
     ap.add_argument("--saddle-steps", type=int, default=3000, help="ascent step cap of the saddles/s leg")
     ap.add_argument("--lattice", type=int, default=2048,
                     help="lattice side; values other than 2048 are small cases for profiler captures")
-    ap.add_argument("--probe", choices=["hvp", "stencil", "ritz"], default=None,
+    ap.add_argument("--probe", choices=["hvp", "stencil", "ritz", "l1"], default=None,
                     help="profiling aid: launch one kernel family three times and exit (no timing)")
     ap.add_argument("--variant", type=int, default=0, help="kernel variant forced by --probe")
     args = ap.parse_args()

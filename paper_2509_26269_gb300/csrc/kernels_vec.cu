@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float*
   gate = wofs(gate, ws);
   if (gate && (*gate & mask)) return;
   if (nx_dev) nx = min(*nx_dev, nx);
-  __shared__ float Cs[MOTO_MAX_BASIS * NY];
+  __shared__ __align__(16) float Cs[MOTO_MAX_BASIS * NY];  // row r: the NY weights of field r
   __shared__ __align__(16) float4 ring[kCombRing * 4 * kCombThreads];
   for (int idx = threadIdx.x; idx < nx * NY; idx += blockDim.x) {
     const int r = idx / NY, c = idx - r * NY;
@@ -345,20 +345,34 @@ __global__ void __launch_bounds__(kCombThreads) combine_long_kernel(const float*
       for (int c = 0; c < NY; ++c) acc[c][0] = acc[c][1] = acc[c][2] = acc[c][3] = 0.f;
     }
     const int slot = (int)(step & (kCombRing - 1));
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
+    // a field's NY weights in NY / 4 16-byte loads; full groups skip the
+    // per-field test
+    auto field = [&](int f) {
       const int r = 4 * g + f;
-      if (r < nx) {
-        const float4 x = ring[(slot * 4 + f) * kCombThreads + threadIdx.x];
+      const float4 x = ring[(slot * 4 + f) * kCombThreads + threadIdx.x];
+      float w[NY];
 #pragma unroll
-        for (int c = 0; c < NY; ++c) {
-          const float w = Cs[r * NY + c];
-          acc[c][0] = fmaf(x.x, w, acc[c][0]);
-          acc[c][1] = fmaf(x.y, w, acc[c][1]);
-          acc[c][2] = fmaf(x.z, w, acc[c][2]);
-          acc[c][3] = fmaf(x.w, w, acc[c][3]);
-        }
+      for (int c4 = 0; c4 < NY; c4 += 4) {
+        const float4 w4 = *reinterpret_cast<const float4*>(&Cs[r * NY + c4]);
+        w[c4] = w4.x;
+        w[c4 + 1] = w4.y;
+        w[c4 + 2] = w4.z;
+        w[c4 + 3] = w4.w;
       }
+#pragma unroll
+      for (int c = 0; c < NY; ++c) {
+        acc[c][0] = fmaf(x.x, w[c], acc[c][0]);
+        acc[c][1] = fmaf(x.y, w[c], acc[c][1]);
+        acc[c][2] = fmaf(x.z, w[c], acc[c][2]);
+        acc[c][3] = fmaf(x.w, w[c], acc[c][3]);
+      }
+    };
+    if (4 * g + 4 <= nx) {
+#pragma unroll
+      for (int f = 0; f < 4; ++f) field(f);
+    } else {
+      for (int f = 0; f < 4; ++f)
+        if (4 * g + f < nx) field(f);
     }
     if (g == G - 1) {
       const size_t e0 = 4 * (tq + cq * qstride);
