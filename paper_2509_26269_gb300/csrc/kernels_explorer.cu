@@ -4,9 +4,7 @@
 // diversity objective is built from.
 //
 // Pairwise L1: a block streams tiles of kTE elements of every candidate
-// through shared memory, staged element-major (the 4 nb candidates of one
-// element contiguous), so a thread reads its two groups of four candidates
-// with two 16-byte loads; thread (block pair, slice) owns the 4 x 4 distances
+// through shared memory; thread (block pair, slice) owns the 4 x 4 distances
 // between candidates 4i .. 4i+3 and 4j .. 4j+3 (i <= j) and adds |x_a - x_b|
 // over every nslice-th element of a tile, so each staged value feeds four
 // distances.  FP32 sums are promoted to FP64 every kFlushT tiles; slices,
@@ -19,6 +17,7 @@ namespace moto {
 
 namespace {
 constexpr int kTE = 128;      // elements per staged tile
+constexpr int kSX = kTE + 1;  // staged row stride: rows of one column fall in different banks
 constexpr int kFlushT = 32;   // tiles between FP32 -> FP64 promotions
 constexpr int kPThreads = 256;
 // staged values per thread per tile: populations of up to 24 / up to 64
@@ -66,31 +65,13 @@ __global__ void __launch_bounds__(kThreads) perturb_kernel(const T* __restrict__
   }
 }
 
-// four consecutive staged values (16-byte aligned: rows of 4 nb values, groups
-// of four) in 16-byte loads
-__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  v[0] = a.x;
-  v[1] = a.y;
-  v[2] = a.z;
-  v[3] = a.w;
-}
-__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
-  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = a.x;
-  v[1] = a.y;
-  v[2] = b.x;
-  v[3] = b.y;
-}
-
 template <typename T, int kPrefetch>
 __global__ void __launch_bounds__(kPThreads) pairwise_l1_kernel(const T* __restrict__ X, size_t ldx, int P,
                                                                 size_t n, double* part, unsigned* counter,
                                                                 double* D) {
   extern __shared__ __align__(16) unsigned char ex_raw[];
-  T* Xs = reinterpret_cast<T*>(ex_raw);  // [kTE][4 nb]: element-major
+  T* Xs = reinterpret_cast<T*>(ex_raw);  // [4 nb][kSX]
   const int nb = (P + 3) / 4, nbp = nb * (nb + 1) / 2;
-  const int P4 = 4 * nb;
   const int nsl = blockDim.x / nbp;
   const int tid = threadIdx.x, bp = tid % nbp, slice = tid / nbp;
   const bool active = slice < nsl;
@@ -137,17 +118,19 @@ __global__ void __launch_bounds__(kPThreads) pairwise_l1_kernel(const T* __restr
       const int idx = tid + u * kPThreads;
       if (idx < total) {
         const int a = idx / kTE, e = idx - a * kTE;
-        Xs[e * P4 + a] = nxt[u];
+        Xs[a * kSX + e] = nxt[u];
       }
     }
     __syncthreads();
     if (t + gridDim.x < ntiles) fetch(t + gridDim.x);
     if (active) {
-#pragma unroll 4
       for (int e = slice; e < kTE; e += nsl) {
         T xa[4], xb[4];
-        load4(Xs + e * P4 + 4 * bi, xa);
-        load4(Xs + e * P4 + 4 * bj, xb);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          xa[r] = Xs[(4 * bi + r) * kSX + e];
+          xb[r] = Xs[(4 * bj + r) * kSX + e];
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -226,7 +209,7 @@ bool launch_pairwise_l1(const T* X, size_t ldx, int P, size_t n, double* part, s
   if (P < 2 || P > MOTO_MAX_POP) return false;
   const int nb = (P + 3) / 4, nbp = nb * (nb + 1) / 2, nent = nbp * 16;
   const int nsl = kPThreads / nbp;
-  size_t smem = (size_t)4 * nb * kTE * sizeof(T);
+  size_t smem = (size_t)4 * nb * kSX * sizeof(T);
   smem = std::max(smem, ((size_t)nsl * nent) * sizeof(double));
   smem = std::max(smem, (size_t)nent * sizeof(double));
   static bool attr = false;
