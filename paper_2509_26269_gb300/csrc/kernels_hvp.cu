@@ -94,7 +94,14 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
       }
     }
   }
-  stage_tile<T, DM::SY>(tiles, V, N, L1, L2, x0, y0, vec16);
+  // interior tiles: the copies' source offsets once for all vectors
+  TileCopies<T, DM::SY, 32 * WY> tc;
+  if (vec16) {
+    tc.init(N, L1, x0, y0);
+    tc.stage(tiles, V);
+  } else {
+    stage_tile<T, DM::SY>(tiles, V, N, L1, L2, x0, y0, false);
+  }
   const int x = x0 + 2 * lane;  // the thread's columns x, x + 1
   const bool pair_store = aligned && x + 1 < L1;
   HvpOnSite<T, SW, P> os;
@@ -104,8 +111,11 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
     T* tile = tiles + (size_t)(j & 1) * DM::kTile;
     T* hv = HV + (size_t)j * ldhv;
     if (j + 1 < nvec) {
-      stage_tile<T, DM::SY>(tiles + (size_t)((j + 1) & 1) * DM::kTile, V + (size_t)(j + 1) * ldv, N, L1, L2, x0,
-                            y0, vec16);
+      T* nt = tiles + (size_t)((j + 1) & 1) * DM::kTile;
+      if (vec16)
+        tc.stage(nt, V + (size_t)(j + 1) * ldv);
+      else
+        stage_tile<T, DM::SY>(nt, V + (size_t)(j + 1) * ldv, N, L1, L2, x0, y0, false);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();

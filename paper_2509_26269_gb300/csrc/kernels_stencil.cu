@@ -235,23 +235,28 @@ __device__ __forceinline__ void tile_origin(int t, int ntx, int ty_sites, int& x
 
 // Tile ring of the persistent kernels: tile t + i grid is staged in buffer
 // (it + i) % NST, so NST - 1 tiles are in flight while one is used.
-template <typename T, int TY>
+// tc: the 16-byte copies' offsets relative to a tile's origin, computed once
+// per block (interior tiles add the origin's offset to the field pointer)
+template <typename T, int TY, class TC>
 __device__ __forceinline__ void stage_one(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int t, int buf,
-                                          int aligned) {
+                                          int aligned, const TC& tc) {
   int x0, y0;
   tile_origin(t, ntx, TY, x0, y0);
-  strip::stage_tile<T, strip::Dims<TY>::SY>(tiles + (size_t)buf * strip::Dims<TY>::kTile, m, N, L1, L2, x0, y0,
-                                            aligned && strip::tile_inside<TY>(x0, y0, L1, L2));
+  T* dst = tiles + (size_t)buf * strip::Dims<TY>::kTile;
+  if (aligned && strip::tile_inside<TY>(x0, y0, L1, L2))
+    tc.stage(dst, m + (size_t)(y0 - 2) * L1 + (x0 - strip::kPadL));
+  else
+    strip::stage_tile<T, strip::Dims<TY>::SY>(dst, m, N, L1, L2, x0, y0, false);
 }
 
 // the first NST - 1 tiles of the block
-template <int NST, typename T, int TY>
+template <int NST, typename T, int TY, class TC>
 __device__ __forceinline__ void stage_prologue(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int ntiles,
-                                               int t0, int aligned) {
+                                               int t0, int aligned, const TC& tc) {
 #pragma unroll
   for (int i = 0; i < NST - 1; ++i) {
     const int t = t0 + i * (int)gridDim.x;
-    if (t < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, t, i, aligned);
+    if (t < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, t, i, aligned, tc);
   }
 }
 
@@ -259,12 +264,12 @@ __device__ __forceinline__ void stage_prologue(T* tiles, const T* m, size_t N, i
 // ahead (its buffer was released by the barrier at the end of the previous
 // iteration), then wait until tile t has landed: the copy groups issued after
 // it may stay pending.
-template <int NST, typename T, int TY>
+template <int NST, typename T, int TY, class TC>
 __device__ __forceinline__ void stage_next(T* tiles, const T* m, size_t N, int L1, int L2, int ntx, int ntiles, int t,
-                                           int it, int aligned) {
+                                           int it, int aligned, const TC& tc) {
   static_assert(NST >= 2 && NST <= 3, "two or three staged tiles");
   const int ahead = t + (NST - 1) * (int)gridDim.x;
-  if (ahead < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, ahead, (it + NST - 1) % NST, aligned);
+  if (ahead < ntiles) stage_one<T, TY>(tiles, m, N, L1, L2, ntx, ahead, (it + NST - 1) % NST, aligned, tc);
   const int later = (ntiles - 1 - t) / (int)gridDim.x;  // tiles of this block after t
   const int pend = later < NST - 1 ? later : NST - 1;
   if (pend >= 2)
@@ -384,9 +389,11 @@ __global__ void __launch_bounds__(32 * WY, MINB) energy_grad_strip_kernel(ModelD
   T gmax = (T)0;
   bool bad = false;
   int t = blockIdx.x, x0, y0;
-  stage_prologue<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
+  TileCopies<T, DM::SY, 32 * WY> tc;
+  tc.init(N, L1, kPadL, 2);  // offsets relative to a tile's origin
+  stage_prologue<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned, tc);
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    stage_next<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
+    stage_next<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned, tc);
     __syncthreads();
     tile_origin(t, ntx, TY, x0, y0);
     SpinsOnSite<T, SW> os;
@@ -497,9 +504,11 @@ __global__ void __launch_bounds__(32 * WY, MINB) topo_strip_kernel(ModelDev md, 
   const size_t N = md.N;
   R acc = RD::of((T)0);
   int t = blockIdx.x, x0, y0;
-  stage_prologue<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned);
+  TileCopies<T, DM::SY, 32 * WY> tc;
+  tc.init(N, L1, kPadL, 2);  // offsets relative to a tile's origin
+  stage_prologue<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, aligned, tc);
   for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
-    stage_next<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned);
+    stage_next<NST, T, TY>(tiles, m, N, L1, L2, ntx, ntiles, t, it, aligned, tc);
     __syncthreads();
     tile_origin(t, ntx, TY, x0, y0);
     const T* tile = tiles + (size_t)(it % NST) * DM::kTile;

@@ -369,6 +369,40 @@ __device__ __forceinline__ void stage_tile(T* tile, const T* __restrict__ v, siz
   cp_async_commit();
 }
 
+// The 16-byte copies of a staged tile whose rows lie inside the lattice
+// (tile_inside), precomputed per thread: copy k of a thread is chunk
+// idx = threadIdx.x + k B of the [3][SY][kSX] tile (destination idx kE
+// elements in), its source offset relative to the field pointer kept in 32
+// bits (3 N < 2^32: moto_create caps N at 2^30).  A block that stages the
+// same tile of several fields (the HVP's vectors) computes the offsets once
+// instead of two divisions and the address arithmetic per copy and field.
+template <typename T, int SY, int B>
+struct TileCopies {
+  static constexpr int kE = 16 / (int)sizeof(T);
+  static constexpr int kCh = kSX / kE;
+  static constexpr int kTotal = 3 * SY * kCh;
+  static constexpr int kN = (kTotal + B - 1) / B;
+  uint32_t off[kN];
+  __device__ __forceinline__ void init(size_t N, int L1, int x0, int y0) {
+#pragma unroll
+    for (int k = 0; k < kN; ++k) {
+      const int idx = threadIdx.x + k * B;
+      const int comp = idx / (SY * kCh), rem = idx - comp * (SY * kCh);
+      const int ly = rem / kCh, ch = rem - ly * kCh;
+      off[k] = (uint32_t)((size_t)comp * N + (size_t)(y0 - 2 + ly) * L1 + (x0 - kPadL) + ch * kE);
+    }
+  }
+  // starts the copies of the tile of field v; commits one group
+  __device__ __forceinline__ void stage(T* tile, const T* __restrict__ v) const {
+#pragma unroll
+    for (int k = 0; k < kN; ++k) {
+      const int idx = threadIdx.x + k * B;
+      if (k + 1 < kN || idx < kTotal) cp_async16(tile + (size_t)idx * kE, v + off[k]);
+    }
+    cp_async_commit();
+  }
+};
+
 // Whether a tile at (x0, y0) stages with 16-byte copies.
 template <int TY>
 __device__ __forceinline__ bool tile_inside(int x0, int y0, int L1, int L2) {
