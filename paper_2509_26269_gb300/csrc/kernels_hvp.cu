@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
   typedef typename PK<T>::V VP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][SY][kSX]
-  T* ms = tiles + 2 * DM::kTile;               // [4][TY][kTX]: m_x, m_y, m_z, s (MREG: then a third tile)
+  T* ms = tiles + 2 * DM::kTile;               // [4][TY][kTX]: m_x, m_y, m_z, s
   const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
   const int L1 = md.L1, L2 = md.L2;
@@ -107,26 +107,31 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
   HvpOnSite<T, SW, P> os;
   os.twoK = P::bc(hw.twoK);
   VP mr[MREG ? SW : 1][3];
-  auto stage_vec = [&](T* dst, int j) {
-    if (vec16)
-      tc.stage(dst, V + (size_t)j * ldv);
-    else
-      stage_tile<T, DM::SY>(dst, V + (size_t)j * ldv, N, L1, L2, x0, y0, false);
-  };
-  auto load_ms = [&]() {
+  for (int j = 0; j < nvec; ++j) {
+    T* tile = tiles + (size_t)(j & 1) * DM::kTile;
+    T* hv = HV + (size_t)j * ldhv;
+    if (j + 1 < nvec) {
+      T* nt = tiles + (size_t)((j + 1) & 1) * DM::kTile;
+      if (vec16)
+        tc.stage(nt, V + (size_t)(j + 1) * ldv);
+      else
+        stage_tile<T, DM::SY>(nt, V + (size_t)(j + 1) * ldv, N, L1, L2, x0, y0, false);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    if (j == 0) {
 #pragma unroll
-    for (int k = 0; k < SW; ++k) {
-      const int mi = (wy * SW + k) * kTX + 2 * lane;
-      os.nsi[k] = P::mul(*reinterpret_cast<const VP*>(ms + 3 * TY * kTX + mi), P::bc((T)-1));
-      if constexpr (MREG) {
+      for (int k = 0; k < SW; ++k) {
+        const int mi = (wy * SW + k) * kTX + 2 * lane;
+        os.nsi[k] = P::mul(*reinterpret_cast<const VP*>(ms + 3 * TY * kTX + mi), P::bc((T)-1));
+        if constexpr (MREG) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mr[k][c] = *reinterpret_cast<const VP*>(ms + c * TY * kTX + mi);
+          for (int c = 0; c < 3; ++c) mr[k][c] = *reinterpret_cast<const VP*>(ms + c * TY * kTX + mi);
+        }
       }
     }
-  };
-  // the walk of vector j from its staged tile, projected and stored
-  auto apply = [&](const T* tile, int j) {
-    T* hv = HV + (size_t)j * ldhv;
     VP ax[SW], ay[SW], az[SW];
     walk<T, SW, DM::SY, P>(tile, wy * SW, lane, ax, ay, az, w, os);
     if (x < L1) {
@@ -168,42 +173,9 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
         }
       }
     }
-  };
-  if constexpr (MREG) {
-    // three tile buffers, the third the m, s area once m and s are in
-    // registers: vector j + 2 is staged right after the barrier that ends
-    // every warp's reads of vector j - 1 (its buffer), so one barrier a
-    // vector and two vectors' copies in flight
-    T* buf[3] = {tiles, tiles + DM::kTile, ms};
-    if (nvec > 1) stage_vec(buf[1], 1);
-    for (int j = 0; j < nvec; ++j) {
-      if (j + 1 < nvec)
-        cp_async_wait<1>();
-      else
-        cp_async_wait<0>();
-      __syncthreads();
-      if (j == 0) {
-        load_ms();
-        __syncthreads();  // the m, s area is a tile buffer from here on
-      }
-      if (j + 2 < nvec) stage_vec(buf[(j + 2) % 3], j + 2);
-      apply(buf[j % 3], j);
-    }
-  } else {
-    for (int j = 0; j < nvec; ++j) {
-      if (j + 1 < nvec) {
-        stage_vec(tiles + (size_t)((j + 1) & 1) * DM::kTile, j + 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      __syncthreads();
-      if (j == 0) load_ms();
-      apply(tiles + (size_t)(j & 1) * DM::kTile, j);
-      // every warp is done with this buffer before the copy issued in the
-      // next iteration (for vector j + 2) overwrites it
-      __syncthreads();
-    }
+    // every warp is done with this buffer before the copy issued in the next
+    // iteration (for vector j + 2) overwrites it
+    __syncthreads();
   }
 }
 
@@ -223,10 +195,7 @@ void hvp_launch_v(const ModelDev& md, const Weights<T>& hw, const T* m, const T*
   constexpr int AR = sizeof(T) == 4 ? AR0 : 1;  // FP64 pairs are scalar in every form
   constexpr int TY = SW * WY;
   const dim3 grid((md.L1 + kTX - 1) / kTX, (md.L2 + TY - 1) / TY);
-  // MREG: the m, s area doubles as a third tile buffer
-  constexpr size_t kMs = 4 * (size_t)TY * kTX;
-  constexpr size_t kArea = MREG ? (Dims<TY>::kTile > kMs ? Dims<TY>::kTile : kMs) : kMs;
-  const size_t smem = (2 * Dims<TY>::kTile + kArea) * sizeof(T);
+  const size_t smem = (2 * Dims<TY>::kTile + 4 * (size_t)TY * kTX) * sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(hvp_strip_kernel<T, SW, WY, MREG, AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
