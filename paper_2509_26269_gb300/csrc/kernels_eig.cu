@@ -88,101 +88,80 @@ __global__ void __launch_bounds__(256) tridiag_eig_kernel(const double* __restri
   __syncthreads();
 
   // ---- 1. tridiagonalisation (precision R) -------------------------------------
-  // Two block barriers a reflector: the partial sums of squares of the next
-  // column below the diagonal are taken, one per warp, while the current
-  // update writes that column (double-buffered: a warp may write the next
-  // reflector's partial while a slower one still reads the current); every
-  // thread then forms the reflector from them (the same operations in the
-  // same order everywhere), with its first entry v0 kept in registers and
-  // written to A only after the update, when no thread reads it.
   if (band > 1) {
-    __shared__ R pnorm[2][32];
-    if (wp == 0) {  // column 0 below the diagonal
-      R sq = 0;
-      for (int r = 1 + ln; r < n; r += 32) {
-        const R a = A[r * kLdA];
-        sq += a * a;
-      }
-      sq = warp_sum_r(sq);
-      if (ln == 0) {
-        pnorm[0][0] = sq;
-        for (int w = 1; w < nw; ++w) pnorm[0][w] = 0;
-      }
-    }
-    __syncthreads();
     for (int j = 0; j + 2 < n; ++j) {
-      const int m0 = j + 1, par = j & 1;
-      R norm2 = 0;
-      for (int w = 0; w < nw; ++w) norm2 += pnorm[par][w];
-      const R x0 = A[m0 * kLdA + j];
-      R b = 0, alpha = x0, v0 = x0;
-      if (!(norm2 - x0 * x0 <= (R)1e-30 * (norm2 + (R)1e-30))) {
-        alpha = -copysign(sqrt(norm2), x0);
-        v0 = x0 - alpha;
-        const R vtv = v0 * v0 + (norm2 - x0 * x0);
-        b = (R)2 / vtv;
-      }
-      if (tid == 0) {
-        e[j] = (double)alpha;
-        beta[j] = b;
-      }
-      // the entry of column j in row c (v0 in row m0)
-      auto vj = [&](int c) -> R { return c == m0 ? v0 : A[c * kLdA + j]; };
-      R part = 0;  // lane 0: sum of squares of column m0 below the diagonal, this warp's rows
-      if (b != (R)0) {
-        // p = b A22 v: two threads a row (adjacent lanes, alternate columns),
-        // four partial sums each
-        for (int idx = tid; idx < 2 * (n - m0); idx += nth) {
-          const int r = m0 + (idx >> 1), h = idx & 1;
-          R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-          int c2 = m0 + h;
-          for (; c2 + 6 < n; c2 += 8) {
-            a0 += A[r * kLdA + c2] * vj(c2);
-            a1 += A[r * kLdA + c2 + 2] * A[(c2 + 2) * kLdA + j];
-            a2 += A[r * kLdA + c2 + 4] * A[(c2 + 4) * kLdA + j];
-            a3 += A[r * kLdA + c2 + 6] * A[(c2 + 6) * kLdA + j];
-          }
-          for (; c2 < n; c2 += 2) a0 += A[r * kLdA + c2] * vj(c2);
-          R a = (a0 + a1) + (a2 + a3);
-          a += __shfl_xor_sync(3u << (ln & 30), a, 1);
-          if (h == 0) pv[r] = b * a;
+      const int m0 = j + 1;
+      if (wp == 0) {  // reflector of column j below the diagonal
+        R s = 0;
+        for (int r = m0 + ln; r < n; r += 32) {
+          const R a = A[r * kLdA + j];
+          s += a * a;
         }
+        const R norm2 = warp_sum_r(s);
+        if (ln == 0) {
+          const R x0 = A[m0 * kLdA + j];
+          if (norm2 - x0 * x0 <= (R)1e-30 * (norm2 + (R)1e-30)) {
+            sh_beta = 0;
+            sh_alpha = x0;
+          } else {
+            const R alpha = -copysign(sqrt(norm2), x0);
+            const R v0 = x0 - alpha;
+            const R vtv = v0 * v0 + (norm2 - x0 * x0);
+            sh_alpha = alpha;
+            sh_beta = (R)2 / vtv;
+            A[m0 * kLdA + j] = v0;
+          }
+          e[j] = (double)sh_alpha;
+          beta[j] = sh_beta;
+        }
+      }
+      __syncthreads();
+      const R b = sh_beta;
+      if (b == (R)0) {
         __syncthreads();
-        // K = b v^T p / 2, summed by every warp in the same order; the update
-        // A22 -= v w^T + w v^T with w = p - K v formed on the fly
-        R q = 0;
-        for (int r = m0 + ln; r < n; r += 32) q += vj(r) * pv[r];
-        const R K = (R)0.5 * b * warp_sum_r(q);
-        // the lane's column terms (at most three columns) do not depend on the row
-        R vcol[3], wcol[3];
+        continue;
+      }
+      // p = b A22 v: two threads a row (adjacent lanes, alternate columns),
+      // four partial sums each
+      for (int idx = tid; idx < 2 * (n - m0); idx += nth) {
+        const int r = m0 + (idx >> 1), h = idx & 1;
+        R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int c2 = m0 + h;
+        for (; c2 + 6 < n; c2 += 8) {
+          a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
+          a1 += A[r * kLdA + c2 + 2] * A[(c2 + 2) * kLdA + j];
+          a2 += A[r * kLdA + c2 + 4] * A[(c2 + 4) * kLdA + j];
+          a3 += A[r * kLdA + c2 + 6] * A[(c2 + 6) * kLdA + j];
+        }
+        for (; c2 < n; c2 += 2) a0 += A[r * kLdA + c2] * A[c2 * kLdA + j];
+        R a = (a0 + a1) + (a2 + a3);
+        a += __shfl_xor_sync(3u << (ln & 30), a, 1);
+        if (h == 0) pv[r] = b * a;
+      }
+      __syncthreads();
+      // K = b v^T p / 2, summed by every warp in the same order; the update
+      // A22 -= v w^T + w v^T with w = p - K v formed on the fly
+      R q = 0;
+      for (int r = m0 + ln; r < n; r += 32) q += A[r * kLdA + j] * pv[r];
+      const R K = (R)0.5 * b * warp_sum_r(q);
+      // the lane's column terms (at most three columns) do not depend on the row
+      R vcol[3], wcol[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int c2 = m0 + ln + 32 * u;
+        vcol[u] = c2 < n ? A[c2 * kLdA + j] : (R)0;
+        wcol[u] = c2 < n ? pv[c2] - K * vcol[u] : (R)0;
+      }
+#pragma unroll 2
+      for (int r = m0 + wp; r < n; r += nw) {
+        const R vr_ = A[r * kLdA + j];
+        const R wr = pv[r] - K * vr_;
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
           const int c2 = m0 + ln + 32 * u;
-          vcol[u] = c2 < n ? vj(c2) : (R)0;
-          wcol[u] = c2 < n ? pv[c2] - K * vcol[u] : (R)0;
+          if (c2 < n) A[r * kLdA + c2] -= vr_ * wcol[u] + wr * vcol[u];
         }
-#pragma unroll 2
-        for (int r = m0 + wp; r < n; r += nw) {
-          const R vr_ = vj(r);
-          const R wr = pv[r] - K * vr_;
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            const int c2 = m0 + ln + 32 * u;
-            if (c2 < n) {
-              const R upd = A[r * kLdA + c2] - (vr_ * wcol[u] + wr * vcol[u]);
-              A[r * kLdA + c2] = upd;
-              if (u == 0 && ln == 0 && r > m0) part += upd * upd;  // column m0, rows below m0
-            }
-          }
-        }
-        if (tid == 0) A[m0 * kLdA + j] = v0;  // the reflector's first entry, for the back-transformation
-      } else {
-        // nothing to annihilate: column m0 is unchanged
-        if (ln == 0)
-          for (int r = m0 + wp; r < n; r += nw)
-            if (r > m0) part += A[r * kLdA + m0] * A[r * kLdA + m0];
       }
-      if (ln == 0) pnorm[par ^ 1][wp] = part;
       __syncthreads();
     }
     if (tid == 0) {
