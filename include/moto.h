@@ -405,9 +405,9 @@ int moto_hvp_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
 int moto_set_hvp_variant(moto_ctx* ctx, int variant);
 /* The same for the energy / gradient stencil of moto_energy_grad and the
  * solvers (variants: staged tiles and blocks an SM, FP32 pair arithmetic
- * packed or scalar; g and s are bit-identical
- * across them, the energy's sum follows each variant's grid), timed by
- * moto_create and recorded for (L1, L2, precision).  moto_topo_charge uses
+ * packed or scalar; g and s are bit-identical across them, the energy's sum
+ * follows each variant's grid), timed by moto_create and recorded for (L1,
+ * L2, precision).  moto_topo_charge uses
  * the recorded variant's layout.  The pair-list model and the FP64-arithmetic
  * energy use their own kernels. */
 int moto_stencil_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
