@@ -407,9 +407,8 @@ int moto_set_hvp_variant(moto_ctx* ctx, int variant);
  * solvers (variants: staged tiles and blocks an SM, FP32 pair arithmetic
  * packed or scalar; g and s are bit-identical across them, the energy's sum
  * follows each variant's grid), timed by moto_create and recorded for (L1,
- * L2, precision).  moto_topo_charge uses
- * the recorded variant's layout.  The pair-list model and the FP64-arithmetic
- * energy use their own kernels. */
+ * L2, precision).  moto_topo_charge uses the recorded variant's layout.  The
+ * pair-list model and the FP64-arithmetic energy use their own kernels. */
 int moto_stencil_tuning(const moto_ctx* ctx, int* variant, float* ms, int cap);
 int moto_set_stencil_variant(moto_ctx* ctx, int variant);
 
