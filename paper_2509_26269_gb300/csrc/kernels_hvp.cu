@@ -13,7 +13,6 @@
 // lattice, precision and vector count by timing (see hvp_variant).
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -180,175 +179,14 @@ __global__ void __launch_bounds__(32 * WY) hvp_strip_kernel(ModelDev md, Weights
   }
 }
 
-// Persistent form of the register-m HVP: a grid of a few blocks an SM walks
-// the lattice's tiles (tile t of block b: t = b, b + grid, ...), so no wave
-// of blocks is left partly empty at the end.  (tile, vector) steps run
-// through one double-buffered pipeline: the step after the last vector of a
-// tile stages the next tile's first vector, and the next tile's m and s are
-// staged during its predecessor's second vector (m and s are then in
-// registers).  Each site's arithmetic is that of hvp_strip_kernel, so the
-// results are the same bit for bit.  Needs nvec >= 2 (the launcher runs
-// single vectors through hvp_strip_kernel).
-template <typename T, int SW, int WY, int AR>
-__global__ void __launch_bounds__(32 * WY) hvp_strip_persistent_kernel(ModelDev md, Weights<T> hw,
-                                                                       const T* __restrict__ m,
-                                                                       const T* __restrict__ s,
-                                                                       const T* __restrict__ V, size_t ldv,
-                                                                       T* __restrict__ HV, size_t ldhv, int nvec,
-                                                                       int aligned, int ntx, int ntiles,
-                                                                       const int* gate, int mask, size_t ws) {
-  m = wofs(m, ws);
-  s = wofs(s, ws);
-  V = wofs(V, ws);
-  HV = wofs(HV, ws);
-  gate = wofs(gate, ws);
-  if (gate && (*gate & mask)) return;
-  constexpr int TY = SW * WY;
-  typedef Dims<TY> DM;
-  typedef typename PA<T, AR>::P P;
-  typedef typename PK<T>::V VP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* tiles = reinterpret_cast<T*>(smem_raw);  // [2][3][SY][kSX]
-  T* ms = tiles + 2 * DM::kTile;               // [4][TY][kTX]: m_x, m_y, m_z, s
-  const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-  const int L1 = md.L1, L2 = md.L2;
-  const size_t N = md.N;
-  const WP<T> w(hw);
-  TileCopies<T, DM::SY, 32 * WY> tc;
-  tc.init(N, L1, kPadL, 2);  // offsets relative to a tile's origin
-  auto origin = [&](int t, int& x0, int& y0) {
-    const int ty = t / ntx;
-    x0 = (t - ty * ntx) * kTX;
-    y0 = ty * TY;
-  };
-  auto inside = [&](int x0, int y0) { return aligned && tile_inside<TY>(x0, y0, L1, L2); };
-  // m, s of tile t (no commit: they join the next staged vector's group)
-  auto stage_ms = [&](int t) {
-    int x0, y0;
-    origin(t, x0, y0);
-    if (inside(x0, y0)) {
-      constexpr int kE = 16 / (int)sizeof(T), kCh = kTX / kE;
-      for (int idx = threadIdx.x; idx < 4 * TY * kCh; idx += blockDim.x) {
-        const int comp = idx / (TY * kCh), rem = idx - comp * (TY * kCh);
-        const int ly = rem / kCh, ch = rem - ly * kCh;
-        const size_t g = (size_t)(y0 + ly) * L1 + x0 + ch * kE;
-        const T* src = comp < 3 ? m + (size_t)comp * N + g : s + g;
-        cp_async16(ms + (size_t)comp * TY * kTX + ly * kTX + ch * kE, src);
-      }
-    } else {
-      for (int idx = threadIdx.x; idx < 4 * TY * kTX; idx += blockDim.x) {
-        const int comp = idx / (TY * kTX), rem = idx - comp * (TY * kTX);
-        const int ly = rem / kTX, lx = rem - ly * kTX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        if (gx < L1 && gy < L2) {
-          const size_t g = (size_t)gy * L1 + gx;
-          cp_elem(ms + idx, comp < 3 ? m + (size_t)comp * N + g : s + g);
-        }
-      }
-    }
-  };
-  // vector j of tile t into buffer dst (commits one group)
-  auto stage_vec = [&](T* dst, int t, int j) {
-    int x0, y0;
-    origin(t, x0, y0);
-    const T* v = V + (size_t)j * ldv;
-    if (inside(x0, y0))
-      tc.stage(dst, v + (size_t)(y0 - 2) * L1 + (x0 - kPadL));
-    else
-      stage_tile<T, DM::SY>(dst, v, N, L1, L2, x0, y0, false);
-  };
-  const int t0 = blockIdx.x;
-  if (t0 >= ntiles) return;
-  const int nmine = (ntiles - 1 - t0) / (int)gridDim.x + 1;
-  const int nsteps = nmine * nvec;
-  stage_ms(t0);
-  stage_vec(tiles, t0, 0);
-  HvpOnSite<T, SW, P> os;
-  os.twoK = P::bc(hw.twoK);
-  VP mr[SW][3];
-  int i = 0, j = 0;  // the step's tile (i-th of the block) and vector
-  for (int step = 0; step < nsteps; ++step) {
-    const int t = t0 + i * (int)gridDim.x;
-    // the next step: vector j + 1 of this tile or vector 0 of the next one
-    const bool more = step + 1 < nsteps;
-    if (more) {
-      const int tn = j + 1 < nvec ? t : t + (int)gridDim.x;
-      if (j == 1 && i + 1 < nmine) {
-        // the next tile's m, s: this tile's have been in registers since
-        // vector 0, and the barrier ending vector 0 closed their reads
-        stage_ms(t + (int)gridDim.x);
-      }
-      stage_vec(tiles + (size_t)((step + 1) & 1) * DM::kTile, tn, j + 1 < nvec ? j + 1 : 0);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    int x0, y0;
-    origin(t, x0, y0);
-    if (j == 0) {
-#pragma unroll
-      for (int k = 0; k < SW; ++k) {
-        const int mi = (wy * SW + k) * kTX + 2 * lane;
-        os.nsi[k] = P::mul(*reinterpret_cast<const VP*>(ms + 3 * TY * kTX + mi), P::bc((T)-1));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mr[k][c] = *reinterpret_cast<const VP*>(ms + c * TY * kTX + mi);
-      }
-    }
-    const T* tile = tiles + (size_t)(step & 1) * DM::kTile;
-    T* hv = HV + (size_t)j * ldhv;
-    const int x = x0 + 2 * lane;
-    const bool pair_store = aligned && x + 1 < L1;
-    VP ax[SW], ay[SW], az[SW];
-    walk<T, SW, DM::SY, P>(tile, wy * SW, lane, ax, ay, az, w, os);
-    if (x < L1) {
-#pragma unroll
-      for (int k = 0; k < SW; ++k) {
-        const int y = y0 + wy * SW + k;
-        if (y >= L2) break;
-        const size_t ix = (size_t)y * L1 + x;
-        const VP m0 = mr[k][0], m1 = mr[k][1], m2 = mr[k][2];
-        const VP p = P::fma(m2, az[k], P::fma(m1, ay[k], P::mul(m0, ax[k])));
-        const VP np = P::mul(p, P::bc((T)-1));
-        const VP ox = P::fma(np, m0, ax[k]);
-        const VP oy = P::fma(np, m1, ay[k]);
-        const VP oz = P::fma(np, m2, az[k]);
-        if (pair_store) {
-          *reinterpret_cast<VP*>(hv + ix) = ox;
-          *reinterpret_cast<VP*>(hv + N + ix) = oy;
-          *reinterpret_cast<VP*>(hv + 2 * N + ix) = oz;
-        } else {
-          hv[ix] = ox.x;
-          hv[N + ix] = oy.x;
-          hv[2 * N + ix] = oz.x;
-          if (x + 1 < L1) {
-            hv[ix + 1] = ox.y;
-            hv[N + ix + 1] = oy.y;
-            hv[2 * N + ix + 1] = oz.y;
-          }
-        }
-      }
-    }
-    // every warp is done with this buffer (and, at vector 0, with m and s)
-    // before the copies issued in the next step overwrite them
-    __syncthreads();
-    if (++j == nvec) {
-      j = 0;
-      ++i;
-    }
-  }
-}
-
 namespace {
 
 // The variants the launcher chooses from (all give bit-identical results).
 struct HvpVariant {
   int sw, wy, mreg, ar;
 };
-// mreg 2: the persistent form (hvp_strip_persistent_kernel, m in registers)
 constexpr HvpVariant kHvpVariants[] = {{4, 4, 1, 0}, {4, 4, 0, 0}, {8, 2, 0, 0}, {2, 8, 1, 0},
-                                       {2, 8, 1, 1}, {4, 4, 1, 1}, {4, 4, 0, 1}, {8, 2, 0, 1},
-                                       {4, 4, 2, 0}};
+                                       {2, 8, 1, 1}, {4, 4, 1, 1}, {4, 4, 0, 1}, {8, 2, 0, 1}};
 constexpr int kNumHvpVariants = sizeof(kHvpVariants) / sizeof(kHvpVariants[0]);
 
 template <typename T, int SW, int WY, bool MREG, int AR0>
@@ -367,28 +205,6 @@ void hvp_launch_v(const ModelDev& md, const Weights<T>& hw, const T* m, const T*
                                                                  mask, walker_ws());
 }
 
-template <typename T, int SW, int WY, int AR0>
-void hvp_launch_persistent(const ModelDev& md, const Weights<T>& hw, const T* m, const T* s, const T* V, size_t ldv,
-                           T* HV, size_t ldhv, int nvec, int aligned, const int* gate, int mask, cudaStream_t st) {
-  constexpr int AR = sizeof(T) == 4 ? AR0 : 1;
-  constexpr int TY = SW * WY;
-  const int ntx = (md.L1 + kTX - 1) / kTX, nty = (md.L2 + TY - 1) / TY;
-  const int ntiles = ntx * nty;
-  const size_t smem = (2 * Dims<TY>::kTile + 4 * (size_t)TY * kTX) * sizeof(T);
-  static int bps = 0;
-  if (bps == 0) {
-    cudaFuncSetAttribute(hvp_strip_persistent_kernel<T, SW, WY, AR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, hvp_strip_persistent_kernel<T, SW, WY, AR>, 32 * WY,
-                                                      smem) != cudaSuccess ||
-        bps < 1)
-      bps = 1;
-  }
-  const int grid = std::min(ntiles, kSMs * bps);
-  hvp_strip_persistent_kernel<T, SW, WY, AR><<<wgrid(grid), 32 * WY, smem, st>>>(
-      md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, ntx, ntiles, gate, mask, walker_ws());
-}
-
 template <typename T>
 void hvp_launch_index(int v, const ModelDev& md, const Weights<T>& hw, const T* m, const T* s, const T* V, size_t ldv,
                       T* HV, size_t ldhv, int nvec, int aligned, const int* gate, int mask, cudaStream_t st) {
@@ -400,12 +216,6 @@ void hvp_launch_index(int v, const ModelDev& md, const Weights<T>& hw, const T* 
     case 5: hvp_launch_v<T, 4, 4, true, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
     case 6: hvp_launch_v<T, 4, 4, false, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
     case 7: hvp_launch_v<T, 8, 2, false, 1>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
-    case 8:
-      if (nvec >= 2)
-        hvp_launch_persistent<T, 4, 4, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st);
-      else
-        hvp_launch_v<T, 4, 4, true, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st);
-      break;
     default: hvp_launch_v<T, 4, 4, true, 0>(md, hw, m, s, V, ldv, HV, ldhv, nvec, aligned, gate, mask, st); break;
   }
 }
